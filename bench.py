@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Benchmark: factor-graph ADMM sweep on circle packing, N=1000 disks.
+
+One step = one solve of the N=1000 packing graph (499,500 pair, 3,000 wall
+and 1,000 radius factors; 3,007,000 scalar edges) for 2,000 iterations in
+FP32 (FP64 residuals), the whole sweep in one persistent kernel.  Metric:
+scalar edge-updates per second (edges x iterations / device time), with
+the sweep's effective bandwidth against the measured HBM peak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the serial FP64 oracle (the CPU baseline) on the
+same workload, on bounded samples.  Under torchrun every rank solves its
+own copy (independent problems, weak scaling); the timing is the max over
+ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DISKS = 1000
+ITERS = 2000
+SEED = 1000 * 1 + 0       # config index x 1000 + replicate
+BYTES_PER_EDGE_ITER = 20  # algorithmic: read u, read m|x, write u, write m|x, read m (FP32)
+METRIC = "edge-updates/s"
+UNIT = "scalar edge-updates/s"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_packing_n1000_f32.md")
+SWEEP_SOURCES = ["sweep.cuh", "sweep_launch.cuh", "sweep_f32.cu", "fga_internal.h"]
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1603_02526_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current sweep sources (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    with open(PROFILE_SUMMARY) as fh:
+        for line in fh:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("sweep_source_hash") != sweep_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the serial FP64 oracle on bounded samples of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(problem, iters):
+    from oracle import from_problem
+    g = from_problem(problem)
+    t0 = time.perf_counter()
+    g.iterate(iters)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(problem, iters=200):
+    E = problem.num_edges
+    dt = oracle_sample(problem, iters)
+    return {"value": E * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "serial FP64 oracle, N=%d packing, %d of the %d iterations (%.1f s)" % (
+                N_DISKS, iters, ITERS, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1603_02526_gb300 import inputs
+    p = inputs.packing_problem(N_DISKS, seed=SEED)
+    E = p.num_edges
+    per_step = 20     # oracle iterations per step (about 1 s each on one core)
+    for _ in range(args.warmup):
+        oracle_sample(p, 2)
+    times = [oracle_sample(p, per_step) for _ in range(args.steps)]
+    dt = sum(times)
+    value = E * per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "circle packing N=%d, rho=alpha=1, %d-iteration solve" % (N_DISKS, ITERS),
+                       "sample": "%d oracle iterations per step" % per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "serial FP64 oracle, %d iterations per step, %d steps" % (
+                                 per_step, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1603_02526_gb300 import build, inputs, _lib
+    from paper_1603_02526_gb300.graph import graph_from_problem
+    build.build()
+    stream = torch.cuda.Stream()
+    p = inputs.packing_problem(N_DISKS, seed=SEED)
+    E = p.num_edges
+    g = graph_from_problem(p, "f32", device=local, stream=stream,
+                           options={_lib.FGA_OPT_ZORDER: 1, _lib.FGA_OPT_STORE_M: 0}, init=False)
+    z0_host = torch.from_numpy(p.z0).pin_memory()
+    z_out = torch.empty(p.num_scalar_vars, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def one_step():
+        g.fga_init(z0_host.numpy())
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        r = g.fga_iterate(ITERS, check_every=ITERS)
+        return r
+
+    for _ in range(args.warmup):
+        r = one_step()
+    assert r["iters"] == ITERS, r
+    sampler = ClockSampler(local)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    dev_ms = []
+    for _ in range(args.steps):
+        r = one_step()
+        dev_ms.append(r["ms"])
+    torch.cuda.synchronize()
+    _barrier(ws)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    ms_step = float(np.mean(dev_ms))
+    ms_step_max = _max_over_ranks(ms_step, ws)
+    value = ws * E * ITERS / (ms_step_max * 1e-3)
+
+    # end to end through the C-ABI with host buffers: H2D of the start point,
+    # the solve, D2H of z, every step
+    e2e_t = []
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        g.fga_init(z0_host.numpy())
+        g.fga_iterate(ITERS, check_every=ITERS)
+        g.fga_read_z(z_out.numpy())
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_s = _max_over_ranks(float(np.mean(e2e_t)), ws)
+    e2e = {"value": ws * E * ITERS / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(p.z0.nbytes), "d2h_bytes_per_step": int(z_out.numel() * 8)}
+
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_EDGE_ITER * E * ITERS / (ms_step * 1e-3) / 1e9
+    traffic = _profile_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": BYTES_PER_EDGE_ITER * E * ITERS,
+            "kernel": "k_sweep_persistent<float>"}
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, iters=args.cpu_iters)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "circle packing N=%d in a unit triangle, rho=alpha=1, %d iterations, "
+                                   "FP32 messages / FP64 residuals, fused persistent sweep" % (N_DISKS, ITERS),
+                       "scalar_edges": E, "factors": p.num_factors, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps, "wall_s_timed_region": wall}
+    print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-iters", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * fgadmm.h -- C-ABI of the GB300 factor-graph ADMM library (libfgadmm.so).
+ *
+ * The library runs Algorithm 2 of "Testing fine-grained parallelism for the
+ * ADMM on a factor-graph" (Hao et al., Sec. II): on a factor graph
+ * G = (F, V, E) with per-edge messages x, m, u, n, weights rho, alpha and
+ * per-variable z, one iteration is
+ *     x_(a,da) = Prox_{f_a,rho}(n_(a,da))    for every factor a
+ *     m = x + u                              for every edge
+ *     z_b = sum rho m / sum rho              for every variable b
+ *     u = u + alpha (x - z_b)                for every edge
+ *     n = z_b - u                            for every edge
+ * with Prox_{h,rho}(r) = argmin_s h(s) + rho/2 |s - r|^2 (Eq. PO).
+ *
+ * The call sequence follows the paper's usage description (Sec. III):
+ * build the graph factor by factor (the paper's addNode; here factors are
+ * registered by type and in batches), copy it to the GPU
+ * (CopyGraphFromCPUtoGPU; here fga_finalize), run the update loop
+ * (fga_iterate) and read the solution from z (Sec. II, last paragraph).
+ *
+ * Conventions for every function:
+ *   - The return value is a status code (FGA_OK or a negative FGA_E*).
+ *     On failure a thread-local message is available from fga_last_error().
+ *     Out-parameters are written only on FGA_OK.
+ *   - Every host input array is copied before the call returns; the caller
+ *     keeps ownership.  Output arrays are caller-allocated.  Where a
+ *     function says "host or device", the pointer may be either (the
+ *     library asks the CUDA runtime which it is).
+ *   - A graph object is not thread-safe; calls on one graph must not run
+ *     concurrently.  Different graphs are independent.
+ *   - Vector variables are expanded into scalar components.  A "scalar
+ *     edge" is one component of one (factor, variable) edge; scalar edges
+ *     are numbered in creation order: factor by factor in call order, each
+ *     factor's variables in the order given, each variable's components in
+ *     order (Sec. III storage order).  z is indexed by scalar variable in
+ *     the order variables were added.
+ */
+#ifndef FGADMM_H
+#define FGADMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FGA_OK 0
+#define FGA_EINVAL (-1)     /* bad argument, id out of range, arity mismatch  */
+#define FGA_ENOMEM (-2)     /* host or device allocation failed               */
+#define FGA_ECUDA (-3)      /* a CUDA runtime call failed                     */
+#define FGA_ESTATE (-4)     /* call not allowed in the object's current state */
+#define FGA_ETIMEOUT (-5)   /* a device-side wait ran out of its time limit   */
+#define FGA_ENONFINITE (-6) /* a residual became NaN or infinite              */
+#define FGA_EBUDGET (-7)    /* iteration budget spent before the tolerance    */
+
+/* ---- precision of messages and prox evaluations ------------------------ */
+#define FGA_F32 0           /* FP32 messages; FP64 residuals and readout      */
+#define FGA_F64 1           /* FP64 everywhere                                */
+
+/* ---- factor types (interface numbers) ---------------------------------- */
+/* Each entry: variables (dims) ; params per factor ; definition.           */
+#define FGA_PACK_PAIR 0       /* (c1:2, r1:1, c2:2, r2:1) ; 0 ; indicator of
+                                 |c1-c2| >= r1+r2 (Appendix A, no-collision) */
+#define FGA_PACK_WALL 1       /* (c:2, r:1) ; 4 = Qx,Qy,Vx,Vy ; indicator of
+                                 Q.(c-V) >= r (Appendix A, wall)             */
+#define FGA_PACK_RADIUS_LIN 2 /* (r:1) ; 1 = w ; f = -w r                    */
+#define FGA_PACK_RADIUS_QUAD 3 /* (r:1) ; 0 ; f = -r^2/2 (Appendix A); needs
+                                 rho > 1 on its edge                          */
+#define FGA_SVM_HINGE 4       /* (w:D, b:1) ; D+2 = x[D], y, c ;
+                                 f = c max(0, 1 - y (w.x + b))               */
+#define FGA_SVM_L2 5          /* (w:any) ; 1 = lambda ; f = lambda/2 |w|^2
+                                 (Appendix C, minimal norm two)               */
+#define FGA_MPC_DYN 6         /* (x:n, u:m, x':n) ; n*n + n*m = A (row-major),
+                                 B (row-major) ; indicator of x' = A x + B u
+                                 (Appendix B, linearised dynamics)            */
+#define FGA_MPC_QUAD 7        /* (any vars) ; one q per scalar component ;
+                                 f = 1/2 sum q_k v_k^2 (Appendix B, cost)     */
+#define FGA_MPC_BOX 8         /* (any vars) ; 2 = lo, hi ; indicator of
+                                 lo <= v <= hi                                */
+#define FGA_FIX 9             /* (any vars) ; one value per scalar component ;
+                                 indicator of v = value                       */
+#define FGA_NUM_TYPES 10
+
+/* ---- edge arrays for readout ------------------------------------------- */
+#define FGA_EDGE_X 0
+#define FGA_EDGE_M 1
+#define FGA_EDGE_U 2
+#define FGA_EDGE_N 3
+
+/* ---- options (fga_set_option, before fga_finalize) --------------------- */
+#define FGA_OPT_ZORDER 0      /* 0 = canonical: each z_b sums its edges one by
+                                 one in ascending creation order (bit-exact
+                                 with a serial FP64 loop); 1 = fast:
+                                 deterministic warp / block / hub trees.
+                                 Default: 0 for FGA_F64, 1 for FGA_F32.       */
+#define FGA_OPT_STORE_M 1     /* 1 = keep m per edge so FGA_EDGE_M can be read
+                                 back (default 1 for FGA_F64, 0 for FGA_F32)  */
+#define FGA_OPT_BLOCK 2       /* threads per CTA of the sweep (0 = library
+                                 choice; 64..1024, multiple of 32)           */
+
+typedef struct fga_graph fga_graph; /* opaque, library-owned */
+
+/* Creates an empty graph.  precision: FGA_F32 or FGA_F64.  device: CUDA
+ * device ordinal used by every later call.  cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream) on which all device work of this
+ * graph is ordered.  No device memory is touched until fga_finalize. */
+int fga_graph_create(fga_graph **out, int32_t precision, int32_t device, void *cuda_stream);
+
+/* Replaces the stream used by later calls. */
+int fga_set_stream(fga_graph *g, void *cuda_stream);
+
+/* Sets an FGA_OPT_* option; before fga_finalize only (FGA_ESTATE after). */
+int fga_set_option(fga_graph *g, int32_t option, int64_t value);
+
+/* Adds `count` variables of dimension `dim` (>= 1).  *first_var_id gets
+ * the id of the first one; ids are consecutive.  Before fga_finalize. */
+int fga_add_variables(fga_graph *g, int64_t count, int32_t dim, int64_t *first_var_id);
+
+/* Registers `count` factors of one type (the paper's addNode, by type and
+ * in batches).  var_ids: count * n_vars_per_factor variable ids, row-major
+ * (factor-major).  params: count * params_per_factor values, row-major, or
+ * params_per_factor values shared by all `count` factors when
+ * params_shared != 0 (NULL allowed when params_per_factor == 0).  The
+ * number of params must match the type's definition above, and variable
+ * dimensions must match the type's shape; otherwise FGA_EINVAL.  Scalar
+ * edges are numbered in call order.  *first_factor_id may be NULL. */
+int fga_add_factors(fga_graph *g, int32_t type, int64_t count, int32_t n_vars_per_factor,
+                    const int64_t *var_ids, const double *params, int32_t params_per_factor,
+                    int32_t params_shared, int64_t *first_factor_id);
+
+/* Uniform rho > 0 and alpha > 0 on every edge (default 1, 1).  Before
+ * fga_finalize. */
+int fga_set_rho_alpha(fga_graph *g, double rho, double alpha);
+
+/* Per-scalar-edge rho and alpha (creation order, |E| values each; either
+ * may be NULL to keep the uniform value).  Before fga_finalize.  The two
+ * coordinates of a disk centre (PACK_PAIR, PACK_WALL) must share one rho. */
+int fga_set_edge_rho_alpha(fga_graph *g, const double *rho, const double *alpha);
+
+/* Validates the graph, lays it out for the GPU (type buckets of
+ * edge-major arrays, a variable-major edge index for the z-update) and
+ * copies it to device memory -- the paper's CopyGraphFromCPUtoGPU.  After
+ * this, no variable or factor can be added. */
+int fga_finalize(fga_graph *g);
+
+/* Sizes: scalar edges, scalar variables, factors, variables. */
+int fga_graph_info(const fga_graph *g, int64_t *num_edges, int64_t *num_scalar_vars,
+                   int64_t *num_factors, int64_t *num_vars);
+
+/* Starting point (the paper leaves it open): z = z0 (|Z| values, variable
+ * order; NULL = 0), u = u0 (|E| values, creation order; NULL = 0),
+ * n = z_b - u, x = 0.  Host or device pointers (FP64).  After finalize. */
+int fga_init(fga_graph *g, const double *z0, const double *u0);
+
+typedef struct {
+    int64_t max_iters;          /* iterations to run in this call (>= 0)    */
+    double tol_pri, tol_dual;   /* stop when RMS primal and dual residuals
+                                   are both <= these (0 = never)             */
+    int32_t check_every;        /* residuals are evaluated after every
+                                   check_every-th iteration and after the
+                                   last one (>= 1)                           */
+    int32_t fused;              /* 1 = one persistent kernel for the whole
+                                   call; 0 = one launch per update phase     */
+    int64_t barrier_timeout_ns; /* limit on one grid-wide wait inside the
+                                   persistent kernel (0 = 2e9 ns)            */
+    int32_t fault_skip_block;   /* testing: >= 0 makes that CTA skip its
+                                   first barrier arrival (the wait then runs
+                                   out and FGA_ETIMEOUT is returned); -1 off */
+    int32_t reserved;
+} fga_iter_opts;
+
+typedef struct {
+    int64_t iters;    /* iterations done in this call                      */
+    double r_pri;     /* RMS primal residual sqrt(sum_e (x_e-z_b)^2 / |E|)   */
+    double r_dual;    /* RMS dual residual sqrt(sum_e rho_e^2 (dz_b)^2 / |E|) */
+    int32_t status;   /* FGA_OK, FGA_EBUDGET (tolerances set but not met),
+                         FGA_ETIMEOUT or FGA_ENONFINITE                     */
+    float ms;         /* device time of the call (CUDA events)             */
+} fga_iter_result;
+
+/* Runs Algorithm 2 for up to opts->max_iters iterations on the graph's
+ * stream, stopping at the first checked iteration whose residuals meet both
+ * tolerances.  The state after the call is exactly the state after
+ * result->iters iterations, so calls can be chained (resume) with the same
+ * iterates as one long call.  Synchronises the stream before returning.
+ * Returns result->status as well (FGA_EBUDGET is reported in the result but
+ * the call itself returns FGA_OK). */
+int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result);
+
+/* Residuals of the last checked iteration (NaN before any). */
+int fga_residuals(const fga_graph *g, double *r_pri, double *r_dual);
+
+/* z readout in FP64, variable order, n = number of scalar variables. Host or
+ * device pointer. */
+int fga_read_z(fga_graph *g, double *out, int64_t n);
+
+/* Edge-array readout in FP64, creation order, n = number of scalar edges.
+ * which: FGA_EDGE_X/M/U/N.  FGA_EDGE_M needs FGA_OPT_STORE_M.  Host or
+ * device pointer. */
+int fga_read_edge_state(fga_graph *g, int32_t which, double *out, int64_t n);
+
+/* Frees every host and device resource of the graph. */
+int fga_destroy(fga_graph *g);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char *fga_last_error(void);
+
+/* Library version string. */
+const char *fga_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGADMM_H */

@@ -1,0 +1,1018 @@
+// fga_graph.cpp -- host side of libfgadmm: graph building (the paper's
+// addNode, by type), layout for the GPU and upload (the paper's
+// CopyGraphFromCPUtoGPU), iteration driver, readout, and the C-ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fgadmm.h"
+#include "fga_internal.h"
+
+using namespace fga;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string t_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? FGA_ENOMEM : FGA_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+extern "C" const char *fga_last_error(void) { return t_last_error.c_str(); }
+extern "C" const char *fga_version(void) { return "fgadmm-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n) {
+        release();
+        bytes = n;
+        if (n == 0) return cudaSuccess;
+        return cudaMalloc(&p, n);
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// the graph
+// ---------------------------------------------------------------------------
+struct FactorBatch {
+    int type = 0;
+    int64_t count = 0;
+    int nv = 0;
+    std::vector<int64_t> vars;     // count * nv
+    std::vector<double> params;    // count * np, or np when shared
+    int np = 0;
+    bool shared = false;
+    int64_t edge0 = 0;             // first creation-order edge
+    int arity = 0;
+    std::vector<int> dims;         // nv
+    const double *param(int64_t f) const { return params.data() + (shared ? 0 : f * np); }
+};
+
+struct Bucket {
+    int type = 0;
+    std::vector<int> dims;
+    int np = 0;
+    int arity = 0;
+    std::vector<std::pair<int, int64_t>> members;   // (batch, factor in batch), creation order
+    int64_t ebase = 0, item0 = 0, nitems = 0;
+    bool per_edge = false;
+};
+
+struct fga_graph {
+    int precision = FGA_F64;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int zorder = -1, store_m = -1, block = 0;
+
+    std::vector<int32_t> vdim;
+    std::vector<int64_t> voff;
+    int64_t nz = 0;
+
+    std::vector<FactorBatch> batches;
+    int64_t nfac = 0, ne = 0;
+
+    double rho_u = 1.0, alpha_u = 1.0;
+    std::vector<double> rho_c, alpha_c;   // per edge, creation order (empty = uniform)
+
+    bool finalized = false;
+    bool initialized = false;
+
+    // layout (host)
+    std::vector<Bucket> buckets;
+    std::vector<int64_t> s2c;       // storage -> creation
+    std::vector<int32_t> svar;      // storage order
+    int64_t nitems_f = 0;
+
+    // device
+    DevBuf x[2], m[2], u, rho_e, alpha_e, d_svar, d_pos, pvm, z[2], srho, srho2, row;
+    DevBuf small_vars, witems, hub_np, hub_off, hub_part, hub_ticket;
+    DevBuf res_pri, res_dual, ctl, bar;
+    std::vector<std::unique_ptr<DevBuf>> bucket_bufs;
+    int n_small = 0, n_witems = 0, n_hubs = 0;
+    bool uniform_rho = true, uniform_alpha = true;
+    int grid = 1, blk = 256;
+
+    // state
+    int64_t iters_done = 0;
+    int xpar = 0, zpar = 0;
+    double last_rp = std::numeric_limits<double>::quiet_NaN();
+    double last_rd = std::numeric_limits<double>::quiet_NaN();
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    size_t rsize() const { return precision == FGA_F32 ? sizeof(float) : sizeof(double); }
+};
+
+static int set_device(const fga_graph *g) {
+    CUDA_TRY(cudaSetDevice(g->device));
+    return FGA_OK;
+}
+
+// Expected number of parameters for a factor of `type` with variable
+// dimensions `dims` (-1 if the shape is invalid for the type).
+static int expected_params(int type, const std::vector<int> &dims, int arity) {
+    const int nv = (int)dims.size();
+    switch (type) {
+    case FGA_PACK_PAIR:
+        return (nv == 4 && dims[0] == 2 && dims[1] == 1 && dims[2] == 2 && dims[3] == 1) ? 0 : -1;
+    case FGA_PACK_WALL:
+        return (nv == 2 && dims[0] == 2 && dims[1] == 1) ? 4 : -1;
+    case FGA_PACK_RADIUS_LIN:
+        return (nv == 1 && dims[0] == 1) ? 1 : -1;
+    case FGA_PACK_RADIUS_QUAD:
+        return (nv == 1 && dims[0] == 1) ? 0 : -1;
+    case FGA_SVM_HINGE:
+        return (nv == 2 && dims[1] == 1) ? dims[0] + 2 : -1;
+    case FGA_SVM_L2:
+        return nv == 1 ? 1 : -1;
+    case FGA_MPC_DYN:
+        return (nv == 3 && dims[0] == dims[2] && 2 * dims[0] + dims[1] <= 64) ? dims[0] * dims[0] + dims[0] * dims[1]
+                                                                               : -1;
+    case FGA_MPC_QUAD:
+        return arity;
+    case FGA_MPC_BOX:
+        return 2;
+    case FGA_FIX:
+        return arity;
+    default:
+        return -1;
+    }
+}
+
+static bool is_per_edge(int type) {
+    return type == FGA_PACK_RADIUS_LIN || type == FGA_PACK_RADIUS_QUAD || type == FGA_SVM_L2 ||
+           type == FGA_MPC_QUAD || type == FGA_MPC_BOX || type == FGA_FIX;
+}
+
+// ---------------------------------------------------------------------------
+// C-ABI: building
+// ---------------------------------------------------------------------------
+extern "C" int fga_graph_create(fga_graph **out, int32_t precision, int32_t device, void *cuda_stream) {
+    if (!out) return fail(FGA_EINVAL, "fga_graph_create: out is NULL");
+    if (precision != FGA_F32 && precision != FGA_F64)
+        return fail(FGA_EINVAL, "fga_graph_create: precision must be FGA_F32 or FGA_F64");
+    if (device < 0) return fail(FGA_EINVAL, "fga_graph_create: bad device %d", device);
+    fga_graph *g = new (std::nothrow) fga_graph();
+    if (!g) return fail(FGA_ENOMEM, "fga_graph_create: out of host memory");
+    g->precision = precision;
+    g->device = device;
+    g->stream = (cudaStream_t)cuda_stream;
+    *out = g;
+    return FGA_OK;
+}
+
+extern "C" int fga_set_stream(fga_graph *g, void *cuda_stream) {
+    if (!g) return fail(FGA_EINVAL, "fga_set_stream: NULL graph");
+    g->stream = (cudaStream_t)cuda_stream;
+    return FGA_OK;
+}
+
+extern "C" int fga_set_option(fga_graph *g, int32_t option, int64_t value) {
+    if (!g) return fail(FGA_EINVAL, "fga_set_option: NULL graph");
+    if (g->finalized) return fail(FGA_ESTATE, "fga_set_option: graph already finalized");
+    switch (option) {
+    case FGA_OPT_ZORDER:
+        if (value != 0 && value != 1) return fail(FGA_EINVAL, "FGA_OPT_ZORDER must be 0 or 1");
+        g->zorder = (int)value;
+        return FGA_OK;
+    case FGA_OPT_STORE_M:
+        g->store_m = value ? 1 : 0;
+        return FGA_OK;
+    case FGA_OPT_BLOCK:
+        if (value != 0 && (value < 64 || value > 256 || value % 32))
+            return fail(FGA_EINVAL, "FGA_OPT_BLOCK must be 0 or a multiple of 32 in [64, 256]");
+        g->block = (int)value;
+        return FGA_OK;
+    default:
+        return fail(FGA_EINVAL, "fga_set_option: unknown option %d", option);
+    }
+}
+
+extern "C" int fga_add_variables(fga_graph *g, int64_t count, int32_t dim, int64_t *first_var_id) {
+    if (!g) return fail(FGA_EINVAL, "fga_add_variables: NULL graph");
+    if (g->finalized) return fail(FGA_ESTATE, "fga_add_variables: graph already finalized");
+    if (count < 0 || dim < 1) return fail(FGA_EINVAL, "fga_add_variables: count %lld dim %d", (long long)count, dim);
+    if (g->nz + count * (int64_t)dim > (int64_t)INT32_MAX - 1)
+        return fail(FGA_EINVAL, "fga_add_variables: more than 2^31-2 scalar variables");
+    const int64_t first = (int64_t)g->vdim.size();
+    try {
+        g->vdim.insert(g->vdim.end(), (size_t)count, dim);
+        for (int64_t i = 0; i < count; ++i) {
+            g->voff.push_back(g->nz);
+            g->nz += dim;
+        }
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_add_variables: out of host memory");
+    }
+    if (first_var_id) *first_var_id = first;
+    return FGA_OK;
+}
+
+extern "C" int fga_add_factors(fga_graph *g, int32_t type, int64_t count, int32_t n_vars_per_factor,
+                               const int64_t *var_ids, const double *params, int32_t params_per_factor,
+                               int32_t params_shared, int64_t *first_factor_id) {
+    if (!g) return fail(FGA_EINVAL, "fga_add_factors: NULL graph");
+    if (g->finalized) return fail(FGA_ESTATE, "fga_add_factors: graph already finalized");
+    if (type < 0 || type >= FGA_NUM_TYPES) return fail(FGA_EINVAL, "fga_add_factors: unknown type %d", type);
+    if (count < 0 || n_vars_per_factor < 1 || n_vars_per_factor > 64)
+        return fail(FGA_EINVAL, "fga_add_factors: count %lld, %d variables per factor", (long long)count,
+                    n_vars_per_factor);
+    if (count == 0) {
+        if (first_factor_id) *first_factor_id = g->nfac;
+        return FGA_OK;
+    }
+    if (!var_ids) return fail(FGA_EINVAL, "fga_add_factors: var_ids is NULL");
+    if (params_per_factor < 0 || (params_per_factor > 0 && !params))
+        return fail(FGA_EINVAL, "fga_add_factors: params missing");
+    FactorBatch b;
+    b.type = type;
+    b.count = count;
+    b.nv = n_vars_per_factor;
+    b.np = params_per_factor;
+    b.shared = params_shared != 0;
+    b.edge0 = g->ne;
+    const int64_t nvar = (int64_t)g->vdim.size();
+    // all factors of one call must share one variable shape
+    for (int k = 0; k < b.nv; ++k) {
+        const int64_t v = var_ids[k];
+        if (v < 0 || v >= nvar) return fail(FGA_EINVAL, "fga_add_factors: variable id %lld out of range", (long long)v);
+        b.dims.push_back(g->vdim[v]);
+        b.arity += g->vdim[v];
+    }
+    for (int64_t f = 0; f < count; ++f) {
+        for (int k = 0; k < b.nv; ++k) {
+            const int64_t v = var_ids[f * b.nv + k];
+            if (v < 0 || v >= nvar)
+                return fail(FGA_EINVAL, "fga_add_factors: variable id %lld out of range (factor %lld)",
+                            (long long)v, (long long)f);
+            if (g->vdim[v] != b.dims[k])
+                return fail(FGA_EINVAL, "fga_add_factors: factors of one call must have the same variable shape");
+        }
+    }
+    const int want = expected_params(type, b.dims, b.arity);
+    if (want < 0) return fail(FGA_EINVAL, "fga_add_factors: variable shape does not fit factor type %d", type);
+    if (want != params_per_factor)
+        return fail(FGA_EINVAL, "fga_add_factors: type %d takes %d parameters, got %d", type, want, params_per_factor);
+    if (g->ne + count * (int64_t)b.arity > (int64_t)INT32_MAX - 1)
+        return fail(FGA_EINVAL, "fga_add_factors: more than 2^31-2 scalar edges");
+    try {
+        b.vars.assign(var_ids, var_ids + count * b.nv);
+        const int64_t np_total = b.shared ? b.np : count * b.np;
+        if (np_total) b.params.assign(params, params + np_total);
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_add_factors: out of host memory");
+    }
+    for (double v : b.params)
+        if (!std::isfinite(v)) return fail(FGA_EINVAL, "fga_add_factors: non-finite parameter");
+    if (type == FGA_MPC_BOX) {
+        for (int64_t f = 0; f < (b.shared ? 1 : count); ++f)
+            if (!(b.param(f)[0] <= b.param(f)[1])) return fail(FGA_EINVAL, "fga_add_factors: box with lo > hi");
+    }
+    if (type == FGA_SVM_HINGE) {
+        for (int64_t f = 0; f < (b.shared ? 1 : count); ++f)
+            if (!(b.param(f)[b.dims[0] + 1] >= 0.0)) return fail(FGA_EINVAL, "fga_add_factors: hinge weight c < 0");
+    }
+    if (type == FGA_SVM_L2) {
+        for (int64_t f = 0; f < (b.shared ? 1 : count); ++f)
+            if (!(b.param(f)[0] >= 0.0)) return fail(FGA_EINVAL, "fga_add_factors: lambda < 0");
+    }
+    if (type == FGA_MPC_QUAD) {
+        for (double v : b.params)
+            if (!(v >= 0.0)) return fail(FGA_EINVAL, "fga_add_factors: negative quadratic weight");
+    }
+    const int64_t first = g->nfac;
+    g->ne += count * (int64_t)b.arity;
+    g->nfac += count;
+    try {
+        g->batches.push_back(std::move(b));
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_add_factors: out of host memory");
+    }
+    if (first_factor_id) *first_factor_id = first;
+    return FGA_OK;
+}
+
+extern "C" int fga_set_rho_alpha(fga_graph *g, double rho, double alpha) {
+    if (!g) return fail(FGA_EINVAL, "fga_set_rho_alpha: NULL graph");
+    if (g->finalized) return fail(FGA_ESTATE, "fga_set_rho_alpha: graph already finalized");
+    if (!(rho > 0.0) || !(alpha > 0.0) || !std::isfinite(rho) || !std::isfinite(alpha))
+        return fail(FGA_EINVAL, "fga_set_rho_alpha: rho and alpha must be finite and > 0");
+    g->rho_u = rho;
+    g->alpha_u = alpha;
+    g->rho_c.clear();
+    g->alpha_c.clear();
+    return FGA_OK;
+}
+
+extern "C" int fga_set_edge_rho_alpha(fga_graph *g, const double *rho, const double *alpha) {
+    if (!g) return fail(FGA_EINVAL, "fga_set_edge_rho_alpha: NULL graph");
+    if (g->finalized) return fail(FGA_ESTATE, "fga_set_edge_rho_alpha: graph already finalized");
+    for (int64_t e = 0; e < g->ne; ++e) {
+        if (rho && (!(rho[e] > 0.0) || !std::isfinite(rho[e])))
+            return fail(FGA_EINVAL, "fga_set_edge_rho_alpha: rho[%lld] not finite > 0", (long long)e);
+        if (alpha && (!(alpha[e] > 0.0) || !std::isfinite(alpha[e])))
+            return fail(FGA_EINVAL, "fga_set_edge_rho_alpha: alpha[%lld] not finite > 0", (long long)e);
+    }
+    if (rho) g->rho_c.assign(rho, rho + g->ne);
+    if (alpha) g->alpha_c.assign(alpha, alpha + g->ne);
+    return FGA_OK;
+}
+
+extern "C" int fga_graph_info(const fga_graph *g, int64_t *num_edges, int64_t *num_scalar_vars, int64_t *num_factors,
+                              int64_t *num_vars) {
+    if (!g) return fail(FGA_EINVAL, "fga_graph_info: NULL graph");
+    if (num_edges) *num_edges = g->ne;
+    if (num_scalar_vars) *num_scalar_vars = g->nz;
+    if (num_factors) *num_factors = g->nfac;
+    if (num_vars) *num_vars = (int64_t)g->vdim.size();
+    return FGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// finalize: layout + upload
+// ---------------------------------------------------------------------------
+static double edge_rho_c(const fga_graph *g, int64_t c) { return g->rho_c.empty() ? g->rho_u : g->rho_c[c]; }
+
+// Projector onto {v : M v = 0}, M = [A B -I], in the metric diag(rho):
+// P = I - W M^T (M W M^T)^{-1} M with W = diag(1/rho).  Gauss-Jordan with
+// partial pivoting on the nx x nx matrix M W M^T.
+static bool dyn_projector(int nx, int nu, const double *A, const double *B, const double *rho, std::vector<double> &P) {
+    const int n = 2 * nx + nu;
+    std::vector<double> M((size_t)nx * n, 0.0);
+    for (int i = 0; i < nx; ++i) {
+        for (int j = 0; j < nx; ++j) M[(size_t)i * n + j] = A[i * nx + j];
+        for (int j = 0; j < nu; ++j) M[(size_t)i * n + nx + j] = B[i * nu + j];
+        M[(size_t)i * n + nx + nu + i] = -1.0;
+    }
+    std::vector<double> K((size_t)nx * 2 * nx, 0.0);   // [K | I]
+    for (int i = 0; i < nx; ++i) {
+        for (int k = 0; k < nx; ++k) {
+            double t = 0.0;
+            for (int j = 0; j < n; ++j) t += M[(size_t)i * n + j] * M[(size_t)k * n + j] / rho[j];
+            K[(size_t)i * 2 * nx + k] = t;
+        }
+        K[(size_t)i * 2 * nx + nx + i] = 1.0;
+    }
+    for (int c = 0; c < nx; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < nx; ++r)
+            if (std::fabs(K[(size_t)r * 2 * nx + c]) > std::fabs(K[(size_t)piv * 2 * nx + c])) piv = r;
+        if (!(std::fabs(K[(size_t)piv * 2 * nx + c]) > 0.0)) return false;
+        if (piv != c)
+            for (int j = 0; j < 2 * nx; ++j) std::swap(K[(size_t)c * 2 * nx + j], K[(size_t)piv * 2 * nx + j]);
+        const double d = K[(size_t)c * 2 * nx + c];
+        for (int j = 0; j < 2 * nx; ++j) K[(size_t)c * 2 * nx + j] /= d;
+        for (int r = 0; r < nx; ++r) {
+            if (r == c) continue;
+            const double f = K[(size_t)r * 2 * nx + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < 2 * nx; ++j) K[(size_t)r * 2 * nx + j] -= f * K[(size_t)c * 2 * nx + j];
+        }
+    }
+    // T = K^{-1} M  (nx x n)
+    std::vector<double> T((size_t)nx * n, 0.0);
+    for (int i = 0; i < nx; ++i)
+        for (int j = 0; j < n; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < nx; ++k) t += K[(size_t)i * 2 * nx + nx + k] * M[(size_t)k * n + j];
+            T[(size_t)i * n + j] = t;
+        }
+    P.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < nx; ++k) t += M[(size_t)k * n + i] * T[(size_t)k * n + j];
+            P[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - t / rho[i];
+        }
+    return true;
+}
+
+template <typename R>
+static int upload_vec(DevBuf &buf, const std::vector<R> &v) {
+    CUDA_TRY(buf.alloc(v.size() * sizeof(R)));
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(buf.p, v.data(), v.size() * sizeof(R), cudaMemcpyHostToDevice));
+    return FGA_OK;
+}
+
+template <typename R>
+static int finalize_typed(fga_graph *g, const std::vector<int64_t> &c2s, const std::vector<int32_t> &pos,
+                          const std::vector<int32_t> &rowp, const std::vector<double> &srho_d,
+                          const std::vector<double> &srho2_d) {
+    const int64_t E = g->ne;
+    int rc;
+    // per-edge rho / alpha in storage order (only when not uniform)
+    g->uniform_rho = g->rho_c.empty();
+    g->uniform_alpha = g->alpha_c.empty();
+    if (!g->uniform_rho) {
+        std::vector<R> v((size_t)E);
+        for (int64_t s = 0; s < E; ++s) v[s] = (R)g->rho_c[g->s2c[s]];
+        if ((rc = upload_vec(g->rho_e, v))) return rc;
+    }
+    if (!g->uniform_alpha) {
+        std::vector<R> v((size_t)E);
+        for (int64_t s = 0; s < E; ++s) v[s] = (R)g->alpha_c[g->s2c[s]];
+        if ((rc = upload_vec(g->alpha_e, v))) return rc;
+    }
+    {
+        std::vector<R> v(srho_d.size());
+        for (size_t i = 0; i < v.size(); ++i) v[i] = (R)srho_d[i];
+        if ((rc = upload_vec(g->srho, v))) return rc;
+    }
+    if ((rc = upload_vec(g->srho2, srho2_d))) return rc;
+    if ((rc = upload_vec(g->d_svar, g->svar))) return rc;
+    if ((rc = upload_vec(g->d_pos, pos))) return rc;
+    if ((rc = upload_vec(g->row, rowp))) return rc;
+    const size_t eb = (size_t)std::max<int64_t>(E, 1) * sizeof(R);
+    CUDA_TRY(g->x[0].alloc(eb));
+    CUDA_TRY(g->x[1].alloc(eb));
+    CUDA_TRY(g->u.alloc(eb));
+    CUDA_TRY(g->pvm.alloc(eb));
+    CUDA_TRY(cudaMemset(g->x[0].p, 0, eb));
+    CUDA_TRY(cudaMemset(g->x[1].p, 0, eb));
+    CUDA_TRY(cudaMemset(g->u.p, 0, eb));
+    CUDA_TRY(cudaMemset(g->pvm.p, 0, eb));
+    if (g->store_m) {
+        CUDA_TRY(g->m[0].alloc(eb));
+        CUDA_TRY(g->m[1].alloc(eb));
+        CUDA_TRY(cudaMemset(g->m[0].p, 0, eb));
+        CUDA_TRY(cudaMemset(g->m[1].p, 0, eb));
+    }
+    const size_t zb = (size_t)std::max<int64_t>(g->nz, 1) * sizeof(R);
+    CUDA_TRY(g->z[0].alloc(zb));
+    CUDA_TRY(g->z[1].alloc(zb));
+    CUDA_TRY(cudaMemset(g->z[0].p, 0, zb));
+    CUDA_TRY(cudaMemset(g->z[1].p, 0, zb));
+
+    // per-bucket parameters (SoA) and MPC projection matrices
+    g->bucket_bufs.clear();
+    for (auto &bk : g->buckets) {
+        const int64_t nf = (int64_t)bk.members.size();
+        std::vector<R> prm((size_t)bk.np * nf);
+        for (int64_t f = 0; f < nf; ++f) {
+            const FactorBatch &b = g->batches[bk.members[f].first];
+            const double *p = b.param(bk.members[f].second);
+            for (int j = 0; j < bk.np; ++j) prm[(size_t)j * nf + f] = (R)p[j];
+        }
+        auto pb = std::make_unique<DevBuf>();
+        if ((rc = upload_vec(*pb, prm))) return rc;
+        g->bucket_bufs.push_back(std::move(pb));
+        if (bk.type == FGA_MPC_DYN) {
+            const int nx = bk.dims[0], nu = bk.dims[1], n = bk.arity;
+            std::map<std::vector<double>, int> seen;
+            std::vector<R> mats;
+            std::vector<int32_t> pidx((size_t)nf);
+            std::vector<double> key, rho((size_t)n), P;
+            for (int64_t f = 0; f < nf; ++f) {
+                const FactorBatch &b = g->batches[bk.members[f].first];
+                const int64_t fi = bk.members[f].second;
+                const double *p = b.param(fi);
+                const int64_t c0 = b.edge0 + fi * b.arity;
+                key.assign(p, p + bk.np);
+                for (int k = 0; k < n; ++k) {
+                    rho[k] = edge_rho_c(g, c0 + k);
+                    key.push_back(rho[k]);
+                }
+                auto it = seen.find(key);
+                if (it == seen.end()) {
+                    if (!dyn_projector(nx, nu, p, p + nx * nx, rho.data(), P))
+                        return fail(FGA_EINVAL, "fga_finalize: singular dynamics constraint");
+                    const int id = (int)seen.size();
+                    seen.emplace(key, id);
+                    for (double v : P) mats.push_back((R)v);
+                    pidx[f] = id;
+                } else {
+                    pidx[f] = it->second;
+                }
+            }
+            auto mb = std::make_unique<DevBuf>();
+            if ((rc = upload_vec(*mb, mats))) return rc;
+            g->bucket_bufs.push_back(std::move(mb));
+            auto ib = std::make_unique<DevBuf>();
+            if ((rc = upload_vec(*ib, pidx))) return rc;
+            g->bucket_bufs.push_back(std::move(ib));
+        }
+    }
+    (void)c2s;
+    return FGA_OK;
+}
+
+extern "C" int fga_finalize(fga_graph *g) {
+    if (!g) return fail(FGA_EINVAL, "fga_finalize: NULL graph");
+    if (g->finalized) return fail(FGA_ESTATE, "fga_finalize: graph already finalized");
+    int rc = set_device(g);
+    if (rc) return rc;
+    if (g->zorder < 0) g->zorder = g->precision == FGA_F64 ? 0 : 1;
+    if (g->store_m < 0) g->store_m = g->precision == FGA_F64 ? 1 : 0;
+    const int64_t E = g->ne;
+
+    // rho checks that the prox formulas rely on
+    for (const FactorBatch &b : g->batches) {
+        for (int64_t f = 0; f < b.count; ++f) {
+            const int64_t c0 = b.edge0 + f * b.arity;
+            if ((b.type == FGA_PACK_PAIR || b.type == FGA_PACK_WALL) && edge_rho_c(g, c0) != edge_rho_c(g, c0 + 1))
+                return fail(FGA_EINVAL, "fga_finalize: the two centre coordinates of a disk need one rho");
+            if (b.type == FGA_PACK_PAIR && edge_rho_c(g, c0 + 3) != edge_rho_c(g, c0 + 4))
+                return fail(FGA_EINVAL, "fga_finalize: the two centre coordinates of a disk need one rho");
+            if (b.type == FGA_PACK_RADIUS_QUAD && !(edge_rho_c(g, c0) > 1.0))
+                return fail(FGA_EINVAL, "fga_finalize: the area reward needs rho > 1 on its edge");
+        }
+    }
+
+    // 1. buckets: factors grouped by (type, variable shape), creation order kept
+    g->buckets.clear();
+    for (int bi = 0; bi < (int)g->batches.size(); ++bi) {
+        const FactorBatch &b = g->batches[bi];
+        int found = -1;
+        for (int k = 0; k < (int)g->buckets.size(); ++k)
+            if (g->buckets[k].type == b.type && g->buckets[k].dims == b.dims) found = k;
+        if (found < 0) {
+            if ((int)g->buckets.size() == kMaxBuckets)
+                return fail(FGA_EINVAL, "fga_finalize: more than %d distinct (type, shape) groups", kMaxBuckets);
+            Bucket nb;
+            nb.type = b.type;
+            nb.dims = b.dims;
+            nb.np = b.np;
+            nb.arity = b.arity;
+            nb.per_edge = is_per_edge(b.type);
+            g->buckets.push_back(nb);
+            found = (int)g->buckets.size() - 1;
+        }
+        for (int64_t f = 0; f < b.count; ++f) g->buckets[found].members.emplace_back(bi, f);
+    }
+    // 2. storage order: bucket by bucket, edge-major inside a bucket
+    std::vector<int64_t> c2s;
+    try {
+        g->s2c.assign((size_t)E, 0);
+        g->svar.assign((size_t)E, 0);
+        c2s.assign((size_t)E, 0);
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
+    }
+    int64_t ebase = 0, item = 0;
+    for (Bucket &bk : g->buckets) {
+        const int64_t nf = (int64_t)bk.members.size();
+        bk.ebase = ebase;
+        bk.item0 = item;
+        bk.nitems = bk.per_edge ? nf * bk.arity : nf;
+        for (int64_t f = 0; f < nf; ++f) {
+            const FactorBatch &b = g->batches[bk.members[f].first];
+            const int64_t fi = bk.members[f].second;
+            const int64_t c0 = b.edge0 + fi * b.arity;
+            int k = 0;
+            for (int v = 0; v < b.nv; ++v) {
+                const int64_t var = b.vars[fi * b.nv + v];
+                for (int d = 0; d < b.dims[v]; ++d, ++k) {
+                    const int64_t s = ebase + (int64_t)k * nf + f;
+                    g->s2c[s] = c0 + k;
+                    c2s[c0 + k] = s;
+                    g->svar[s] = (int32_t)(g->voff[var] + d);
+                }
+            }
+        }
+        ebase += nf * bk.arity;
+        item += bk.nitems;
+    }
+    g->nitems_f = item;
+    // 3. variable-major rows, each in ascending creation order
+    const int64_t Z = g->nz;
+    std::vector<int32_t> rowp((size_t)Z + 1, 0), pos((size_t)E, 0), fill((size_t)Z, 0);
+    std::vector<double> srho_d((size_t)Z, 0.0), srho2_d((size_t)Z, 0.0);
+    for (int64_t s = 0; s < E; ++s) rowp[g->svar[s] + 1]++;
+    for (int64_t b = 0; b < Z; ++b) rowp[b + 1] += rowp[b];
+    for (int64_t b = 0; b < Z; ++b) fill[b] = rowp[b];
+    for (int64_t c = 0; c < E; ++c) {
+        const int64_t s = c2s[c];
+        const int32_t b = g->svar[s];
+        pos[s] = fill[b]++;
+        const double r = edge_rho_c(g, c);
+        srho_d[b] += r;        // sequential, ascending creation order
+        srho2_d[b] += r * r;
+    }
+    // 4. fast z-order work lists
+    std::vector<int32_t> small, hub_np, hub_off;
+    std::vector<int4> witems;
+    if (g->zorder == 1) {
+        std::vector<int4> med;
+        int off = 0;
+        for (int64_t b = 0; b < Z; ++b) {
+            const int deg = rowp[b + 1] - rowp[b];
+            if (deg <= kSmallDeg) {
+                small.push_back((int32_t)b);
+            } else if (deg <= kPiece) {
+                med.push_back(make_int4((int)b, rowp[b], deg, -1));
+            } else {
+                const int h = (int)hub_np.size();
+                const int np = (deg + kPiece - 1) / kPiece;
+                hub_np.push_back(np);
+                hub_off.push_back(off);
+                off += np;
+                for (int p = 0; p < np; ++p)
+                    witems.push_back(make_int4((int)b, rowp[b] + p * kPiece, std::min(kPiece, deg - p * kPiece), h));
+            }
+        }
+        witems.insert(witems.end(), med.begin(), med.end());
+        g->n_small = (int)small.size();
+        g->n_witems = (int)witems.size();
+        g->n_hubs = (int)hub_np.size();
+        if ((rc = upload_vec(g->small_vars, small))) return rc;
+        if ((rc = upload_vec(g->witems, witems))) return rc;
+        if ((rc = upload_vec(g->hub_np, hub_np))) return rc;
+        if ((rc = upload_vec(g->hub_off, hub_off))) return rc;
+        CUDA_TRY(g->hub_part.alloc((size_t)std::max(off, 1) * g->rsize()));
+        CUDA_TRY(g->hub_ticket.alloc((size_t)std::max(g->n_hubs, 1) * sizeof(unsigned int)));
+        CUDA_TRY(cudaMemset(g->hub_ticket.p, 0, g->hub_ticket.bytes));
+    }
+    // 5. upload
+    rc = g->precision == FGA_F32 ? finalize_typed<float>(g, c2s, pos, rowp, srho_d, srho2_d)
+                                 : finalize_typed<double>(g, c2s, pos, rowp, srho_d, srho2_d);
+    if (rc) return rc;
+    // 6. launch shape: co-resident CTAs, no more than the work needs
+    int dev_sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
+    g->blk = g->block ? g->block : 256;
+    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk)
+                                            : sweep_max_blocks_per_sm<double>(g->blk);
+    if (bps < 1) return fail(FGA_ECUDA, "fga_finalize: the sweep kernel cannot be resident at %d threads", g->blk);
+    const int64_t full = (int64_t)bps * dev_sms;
+    const int64_t work = std::max<int64_t>(std::max<int64_t>(g->nitems_f, Z), (int64_t)g->n_witems * 32);
+    g->grid = (int)std::max<int64_t>(1, std::min<int64_t>(full, (work + g->blk - 1) / g->blk));
+    CUDA_TRY(g->res_pri.alloc((size_t)g->grid * sizeof(double)));
+    CUDA_TRY(g->res_dual.alloc((size_t)2 * g->grid * sizeof(double)));
+    CUDA_TRY(cudaMemset(g->res_pri.p, 0, g->res_pri.bytes));
+    CUDA_TRY(cudaMemset(g->res_dual.p, 0, g->res_dual.bytes));
+    CUDA_TRY(g->ctl.alloc(sizeof(Ctl)));
+    CUDA_TRY(g->bar.alloc(sizeof(Barrier)));
+    CUDA_TRY(cudaEventCreate(&g->ev0));
+    CUDA_TRY(cudaEventCreate(&g->ev1));
+    CUDA_TRY(cudaDeviceSynchronize());
+    g->finalized = true;
+    return FGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host/device pointer helpers
+// ---------------------------------------------------------------------------
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copies n doubles from a host-or-device pointer into a host vector.
+static int fetch_doubles(const double *src, int64_t n, std::vector<double> &dst, cudaStream_t s) {
+    dst.resize((size_t)n);
+    if (n == 0) return FGA_OK;
+    if (is_device_ptr(src)) {
+        CUDA_TRY(cudaMemcpyAsync(dst.data(), src, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(dst.data(), src, (size_t)n * sizeof(double));
+    }
+    return FGA_OK;
+}
+
+static int deliver_doubles(double *dst, const std::vector<double> &src, cudaStream_t s) {
+    if (src.empty()) return FGA_OK;
+    if (is_device_ptr(dst)) {
+        CUDA_TRY(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(dst, src.data(), src.size() * sizeof(double));
+    }
+    return FGA_OK;
+}
+
+template <typename R>
+static int download(const DevBuf &b, int64_t n, std::vector<R> &out, cudaStream_t s) {
+    out.resize((size_t)n);
+    if (n == 0) return FGA_OK;
+    CUDA_TRY(cudaMemcpyAsync(out.data(), b.p, (size_t)n * sizeof(R), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return FGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// init
+// ---------------------------------------------------------------------------
+template <typename R>
+static int init_typed(fga_graph *g, const std::vector<double> &z0, const std::vector<double> &u0) {
+    cudaStream_t st = g->stream;
+    std::vector<R> zr, ur;
+    if (g->nz) {
+        if (z0.empty()) {
+            CUDA_TRY(cudaMemsetAsync(g->z[0].p, 0, (size_t)g->nz * sizeof(R), st));
+        } else {
+            zr.resize((size_t)g->nz);
+            for (int64_t b = 0; b < g->nz; ++b) zr[b] = (R)z0[b];
+            CUDA_TRY(cudaMemcpyAsync(g->z[0].p, zr.data(), zr.size() * sizeof(R), cudaMemcpyHostToDevice, st));
+        }
+    }
+    if (g->ne) {
+        if (u0.empty()) {
+            CUDA_TRY(cudaMemsetAsync(g->u.p, 0, (size_t)g->ne * sizeof(R), st));
+        } else {
+            ur.resize((size_t)g->ne);
+            for (int64_t s = 0; s < g->ne; ++s) ur[s] = (R)u0[g->s2c[s]];
+            CUDA_TRY(cudaMemcpyAsync(g->u.p, ur.data(), ur.size() * sizeof(R), cudaMemcpyHostToDevice, st));
+        }
+        CUDA_TRY(cudaMemsetAsync(g->x[0].p, 0, (size_t)g->ne * sizeof(R), st));
+        if (g->store_m) CUDA_TRY(cudaMemsetAsync(g->m[0].p, 0, (size_t)g->ne * sizeof(R), st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return FGA_OK;
+}
+
+extern "C" int fga_init(fga_graph *g, const double *z0, const double *u0) {
+    if (!g) return fail(FGA_EINVAL, "fga_init: NULL graph");
+    if (!g->finalized) return fail(FGA_ESTATE, "fga_init: call fga_finalize first");
+    int rc = set_device(g);
+    if (rc) return rc;
+    std::vector<double> zh, uh;
+    if (z0 && (rc = fetch_doubles(z0, g->nz, zh, g->stream))) return rc;
+    if (u0 && (rc = fetch_doubles(u0, g->ne, uh, g->stream))) return rc;
+    for (double v : zh)
+        if (!std::isfinite(v)) return fail(FGA_EINVAL, "fga_init: non-finite z0");
+    for (double v : uh)
+        if (!std::isfinite(v)) return fail(FGA_EINVAL, "fga_init: non-finite u0");
+    rc = g->precision == FGA_F32 ? init_typed<float>(g, zh, uh) : init_typed<double>(g, zh, uh);
+    if (rc) return rc;
+    g->iters_done = 0;
+    g->xpar = 0;
+    g->zpar = 0;
+    g->last_rp = g->last_rd = std::numeric_limits<double>::quiet_NaN();
+    g->initialized = true;
+    return FGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// iterate
+// ---------------------------------------------------------------------------
+template <typename R>
+static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
+    std::memset(&a, 0, sizeof a);
+    a.nb = (int)g->buckets.size();
+    int pb = 0;
+    for (int i = 0; i < a.nb; ++i) {
+        const Bucket &bk = g->buckets[i];
+        BucketDev<R> &d = a.bk[i];
+        d.type = bk.type;
+        d.arity = bk.arity;
+        d.nprm = bk.np;
+        d.per_edge = bk.per_edge ? 1 : 0;
+        for (int k = 0; k < 4; ++k) d.dims[k] = k < (int)bk.dims.size() ? bk.dims[k] : 0;
+        d.nf = (long long)bk.members.size();
+        d.ebase = bk.ebase;
+        d.item0 = bk.item0;
+        d.nitems = bk.nitems;
+        d.prm = g->bucket_bufs[pb++]->as<R>();
+        if (bk.type == FGA_MPC_DYN) {
+            d.pmat = g->bucket_bufs[pb++]->as<R>();
+            d.pidx = g->bucket_bufs[pb++]->as<int>();
+        }
+    }
+    a.nitems_f = g->nitems_f;
+    a.E = g->ne;
+    a.nz = (int)g->nz;
+    a.x[0] = g->x[0].as<R>();
+    a.x[1] = g->x[1].as<R>();
+    a.m[0] = g->store_m ? g->m[0].as<R>() : nullptr;
+    a.m[1] = g->store_m ? g->m[1].as<R>() : nullptr;
+    a.u = g->u.as<R>();
+    a.rho_e = g->uniform_rho ? nullptr : g->rho_e.as<R>();
+    a.alpha_e = g->uniform_alpha ? nullptr : g->alpha_e.as<R>();
+    a.rho_u = (R)g->rho_u;
+    a.alpha_u = (R)g->alpha_u;
+    a.svar = g->d_svar.as<int>();
+    a.pos = g->d_pos.as<int>();
+    a.pvm = g->pvm.as<R>();
+    a.z[0] = g->z[0].as<R>();
+    a.z[1] = g->z[1].as<R>();
+    a.srho = g->srho.as<R>();
+    a.srho2 = g->srho2.as<double>();
+    a.row = g->row.as<int>();
+    a.zorder = g->zorder;
+    a.n_small = g->n_small;
+    a.small_vars = g->small_vars.as<int>();
+    a.n_witems = g->n_witems;
+    a.witems = g->witems.as<int4>();
+    a.hub_npieces = g->hub_np.as<int>();
+    a.hub_off = g->hub_off.as<int>();
+    a.hub_part = g->hub_part.as<R>();
+    a.hub_ticket = g->hub_ticket.as<unsigned int>();
+    a.res_pri = g->res_pri.as<double>();
+    a.res_dual = g->res_dual.as<double>();
+    a.gmax = g->grid;
+    a.ctl = g->ctl.as<Ctl>();
+    a.bar = g->bar.as<Barrier>();
+}
+
+template <typename R>
+static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
+    SweepArgs<R> a;
+    fill_args(g, a);
+    a.k0 = g->iters_done;
+    a.K = o.max_iters;
+    a.check_every = o.check_every;
+    a.tol_pri = o.tol_pri;
+    a.tol_dual = o.tol_dual;
+    a.timeout_ns = o.barrier_timeout_ns > 0 ? o.barrier_timeout_ns : 2000000000LL;
+    a.skip_block = o.fault_skip_block;
+    a.xpar0 = g->xpar;
+    a.zpar0 = g->zpar;
+    cudaStream_t s = g->stream;
+    CUDA_TRY(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), s));
+    CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(Barrier), s));
+    if (g->n_hubs) CUDA_TRY(cudaMemsetAsync(g->hub_ticket.p, 0, g->hub_ticket.bytes, s));
+    CUDA_TRY(cudaEventRecord(g->ev0, s));
+    if (o.fused) {
+        CUDA_TRY(sweep_persistent<R>(a, g->grid, g->blk, s));
+    } else {
+        int xp = g->xpar, zp = g->zpar;
+        for (long long it = 1; it <= a.K; ++it) {
+            const bool pend = it > 1;
+            const bool chk = pend && ((a.k0 + it - 1) % a.check_every == 0);
+            CUDA_TRY(sweep_phase_f<R>(a, pend ? F_U_PROX : F_PROX, xp, zp, chk ? 1 : 0, g->grid, g->blk, s));
+            if (chk) CUDA_TRY(sweep_check<R>(a, it - 1, xp, zp, 0, g->grid, s));
+            xp ^= 1;
+            const bool chkz = ((a.k0 + it) % a.check_every == 0) || it == a.K;
+            CUDA_TRY(sweep_phase_z<R>(a, zp, it, chkz ? 1 : 0, g->grid, g->blk, s));
+            zp ^= 1;
+        }
+        if (a.K > 0) {
+            CUDA_TRY(sweep_phase_f<R>(a, F_U_ONLY, xp, zp, 1, g->grid, g->blk, s));
+            CUDA_TRY(sweep_check<R>(a, a.K, xp, zp, 1, g->grid, s));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(g->ev1, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    Ctl c;
+    Barrier b;
+    CUDA_TRY(cudaMemcpy(&c, g->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&b, g->bar.p, sizeof b, cudaMemcpyDeviceToHost));
+    res.ms = ms;
+    if (b.error) {
+        // the state is undefined after an aborted launch; a new fga_init is needed
+        g->initialized = false;
+        res.iters = 0;
+        res.r_pri = res.r_dual = std::numeric_limits<double>::quiet_NaN();
+        res.status = b.error;
+        return fail(b.error, "fga_iterate: a grid-wide wait timed out (status %d)", b.error);
+    }
+    if (a.K <= 0) {
+        res.iters = 0;
+        res.r_pri = g->last_rp;
+        res.r_dual = g->last_rd;
+        res.status = FGA_OK;
+        return FGA_OK;
+    }
+    if (!c.done) return fail(FGA_ECUDA, "fga_iterate: the sweep ended without reporting");
+    g->iters_done += c.iters;
+    g->xpar = c.xpar;
+    g->zpar = c.zpar;
+    g->last_rp = c.r_pri;
+    g->last_rd = c.r_dual;
+    res.iters = c.iters;
+    res.r_pri = c.r_pri;
+    res.r_dual = c.r_dual;
+    res.status = c.status;
+    if (c.status == FGA_ENONFINITE) return fail(FGA_ENONFINITE, "fga_iterate: residual became non-finite");
+    return FGA_OK;
+}
+
+extern "C" int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result) {
+    if (!g || !opts || !result) return fail(FGA_EINVAL, "fga_iterate: NULL argument");
+    if (!g->finalized || !g->initialized) return fail(FGA_ESTATE, "fga_iterate: call fga_finalize and fga_init first");
+    if (opts->max_iters < 0 || opts->check_every < 1 || opts->tol_pri < 0 || opts->tol_dual < 0)
+        return fail(FGA_EINVAL, "fga_iterate: bad options");
+    if (opts->fault_skip_block >= 0 && !opts->fused)
+        return fail(FGA_EINVAL, "fga_iterate: fault_skip_block needs the fused kernel");
+    int rc = set_device(g);
+    if (rc) return rc;
+    fga_iter_result r;
+    std::memset(&r, 0, sizeof r);
+    rc = g->precision == FGA_F32 ? iterate_typed<float>(g, *opts, r) : iterate_typed<double>(g, *opts, r);
+    *result = r;   // also on timeout / non-finite, so the caller sees the status
+    return rc;
+}
+
+extern "C" int fga_residuals(const fga_graph *g, double *r_pri, double *r_dual) {
+    if (!g) return fail(FGA_EINVAL, "fga_residuals: NULL graph");
+    if (r_pri) *r_pri = g->last_rp;
+    if (r_dual) *r_dual = g->last_rd;
+    return FGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// readout
+// ---------------------------------------------------------------------------
+template <typename R>
+static int read_z_typed(fga_graph *g, double *out) {
+    std::vector<R> zr;
+    int rc = download(g->z[g->zpar], g->nz, zr, g->stream);
+    if (rc) return rc;
+    std::vector<double> zd(zr.begin(), zr.end());
+    return deliver_doubles(out, zd, g->stream);
+}
+
+extern "C" int fga_read_z(fga_graph *g, double *out, int64_t n) {
+    if (!g || (!out && n)) return fail(FGA_EINVAL, "fga_read_z: NULL argument");
+    if (!g->finalized) return fail(FGA_ESTATE, "fga_read_z: graph not finalized");
+    if (n != g->nz) return fail(FGA_EINVAL, "fga_read_z: n = %lld, graph has %lld scalar variables", (long long)n,
+                                (long long)g->nz);
+    int rc = set_device(g);
+    if (rc) return rc;
+    return g->precision == FGA_F32 ? read_z_typed<float>(g, out) : read_z_typed<double>(g, out);
+}
+
+template <typename R>
+static int read_edge_typed(fga_graph *g, int which, double *out) {
+    const int64_t E = g->ne;
+    std::vector<R> v, u, z;
+    int rc;
+    std::vector<double> res((size_t)E);
+    if (which == FGA_EDGE_X || which == FGA_EDGE_M) {
+        const DevBuf &b = which == FGA_EDGE_X ? g->x[g->xpar] : g->m[g->xpar];
+        if ((rc = download(b, E, v, g->stream))) return rc;
+        for (int64_t s = 0; s < E; ++s) res[g->s2c[s]] = (double)v[s];
+    } else if (which == FGA_EDGE_U) {
+        if ((rc = download(g->u, E, u, g->stream))) return rc;
+        for (int64_t s = 0; s < E; ++s) res[g->s2c[s]] = (double)u[s];
+    } else {
+        // n = z_b - u, evaluated in the working precision as the sweep does
+        if ((rc = download(g->u, E, u, g->stream))) return rc;
+        if ((rc = download(g->z[g->zpar], g->nz, z, g->stream))) return rc;
+        for (int64_t s = 0; s < E; ++s) {
+            const R n = z[g->svar[s]] - u[s];
+            res[g->s2c[s]] = (double)n;
+        }
+    }
+    return deliver_doubles(out, res, g->stream);
+}
+
+extern "C" int fga_read_edge_state(fga_graph *g, int32_t which, double *out, int64_t n) {
+    if (!g || (!out && n)) return fail(FGA_EINVAL, "fga_read_edge_state: NULL argument");
+    if (!g->finalized) return fail(FGA_ESTATE, "fga_read_edge_state: graph not finalized");
+    if (which < FGA_EDGE_X || which > FGA_EDGE_N) return fail(FGA_EINVAL, "fga_read_edge_state: bad array %d", which);
+    if (which == FGA_EDGE_M && !g->store_m)
+        return fail(FGA_ESTATE, "fga_read_edge_state: m is not kept (set FGA_OPT_STORE_M before finalize)");
+    if (n != g->ne) return fail(FGA_EINVAL, "fga_read_edge_state: n = %lld, graph has %lld edges", (long long)n,
+                                (long long)g->ne);
+    int rc = set_device(g);
+    if (rc) return rc;
+    return g->precision == FGA_F32 ? read_edge_typed<float>(g, which, out) : read_edge_typed<double>(g, which, out);
+}
+
+extern "C" int fga_destroy(fga_graph *g) {
+    if (!g) return FGA_OK;
+    if (g->finalized) {
+        cudaSetDevice(g->device);
+        cudaStreamSynchronize(g->stream);
+        if (g->ev0) cudaEventDestroy(g->ev0);
+        if (g->ev1) cudaEventDestroy(g->ev1);
+    }
+    delete g;
+    return FGA_OK;
+}

@@ -1,0 +1,125 @@
+// fga_internal.h -- descriptors shared by the host layer and the sweep
+// kernels of libfgadmm (not part of the public C-ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fga {
+
+constexpr int kMaxBuckets = 24;     // distinct (type, variable-shape) groups
+constexpr int kPiece = 2048;        // hub variables are reduced in pieces of this many edges
+constexpr int kSmallDeg = 16;       // fast z-order: thread per variable up to this degree
+
+// Phase-F modes: the x-update of one iteration, preceded (from the second
+// iteration of a call on) by the deferred u- and n-updates of the previous
+// iteration; or the u-update alone at the end of a call.
+enum FMode : int { F_PROX = 0, F_U_PROX = 1, F_U_ONLY = 2 };
+
+// Grid-wide barrier state (device memory, zeroed before every launch).
+struct Barrier {
+    unsigned int count;
+    unsigned int gen;
+    int error;
+    int pad;
+};
+
+// Per-call control block written by the device.
+struct Ctl {
+    long long iters;   // iterations completed in this call
+    double r_pri;      // RMS residuals of the last check
+    double r_dual;
+    int status;        // 0, or a negative FGA_E* code
+    int xpar;          // x/m buffer that holds the state after the call
+    int zpar;          // z buffer that holds the state after the call
+    int done;          // set when the call stopped (unfused launches exit early)
+    int checked;       // at least one residual check happened
+    int pad;
+};
+
+// One bucket = all factors of one type with one variable shape, stored
+// edge-major: scalar edge k of factor f lives at ebase + k * nf + f.
+template <typename R>
+struct BucketDev {
+    int type;
+    int arity;          // scalar edges per factor
+    int nprm;           // parameters per factor (SoA: prm[j * nf + f])
+    int per_edge;       // 1: elementwise prox, one work item per scalar edge
+    int dims[4];        // variable dimensions (types with a fixed shape)
+    long long nf;       // factors
+    long long ebase;    // first storage edge
+    long long item0;    // first phase-F work item
+    long long nitems;   // work items (nf, or nf * arity when per_edge)
+    const R *prm;       // parameters, SoA
+    const R *pmat;      // MPC_DYN: projection matrices, arity x arity each
+    const int *pidx;    // MPC_DYN: matrix index of each factor
+};
+
+template <typename R>
+struct SweepArgs {
+    int nb;
+    BucketDev<R> bk[kMaxBuckets];
+    long long nitems_f;   // phase-F work items over all buckets
+    long long E;          // scalar edges
+    int nz;               // scalar variables
+
+    // per-edge state, storage order
+    R *x[2];
+    R *m[2];              // null when m is not kept
+    R *u;
+    const R *rho_e;       // null: uniform rho_u
+    const R *alpha_e;     // null: uniform alpha_u
+    R rho_u, alpha_u;
+    const int *svar;      // scalar variable of each edge
+    const int *pos;       // slot of each edge in the variable-major array
+    R *pvm;               // rho * m, variable-major (rows in creation order)
+
+    // per-variable state
+    R *z[2];
+    const R *srho;        // sum of rho over the variable's edges
+    const double *srho2;  // sum of rho^2 over the variable's edges
+    const int *row;       // variable-major row pointers [nz + 1]
+
+    // z-update work lists
+    int zorder;           // 0 canonical, 1 fast
+    int n_small;          // fast: variables reduced by one thread
+    const int *small_vars;
+    int n_witems;         // fast: warp work items (var, start, len, hub or -1)
+    const int4 *witems;
+    const int *hub_npieces;
+    const int *hub_off;
+    R *hub_part;
+    unsigned int *hub_ticket;
+
+    // residual partial sums, one per CTA
+    double *res_pri;      // [gmax]
+    double *res_dual;     // [2][gmax]
+    int gmax;
+
+    Ctl *ctl;
+    Barrier *bar;
+    long long k0;         // iterations done before this call
+    long long K;          // iteration budget of this call
+    int check_every;
+    double tol_pri, tol_dual;
+    long long timeout_ns;
+    int skip_block;
+    int xpar0, zpar0;
+};
+
+// Launchers (sweep_f32.cu / sweep_f64.cu).
+template <typename R>
+cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, cudaStream_t s);
+template <typename R>
+cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block,
+                          cudaStream_t s);
+template <typename R>
+cudaError_t sweep_phase_z(const SweepArgs<R> &a, int zp, long long it, int chk, int grid, int block,
+                          cudaStream_t s);
+template <typename R>
+cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int zp, int final_check,
+                        int grid_partials, cudaStream_t s);
+template <typename R>
+int sweep_max_blocks_per_sm(int block);
+
+}  // namespace fga

@@ -1,0 +1,48 @@
+// sweep_launch.cuh -- host launchers of the sweep kernels for one real type.
+// Included once per precision (sweep_f32.cu, sweep_f64.cu).
+#pragma once
+
+#include "sweep.cuh"
+
+namespace fga {
+
+template <typename R>
+cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, cudaStream_t s) {
+    void *args[] = {(void *)&a};
+    // Cooperative launch: the runtime refuses a grid that cannot be
+    // co-resident, so the grid-wide barrier can never wait on a CTA that
+    // was not scheduled.
+    return cudaLaunchCooperativeKernel((const void *)k_sweep_persistent<R>, dim3(grid), dim3(block), args, 0, s);
+}
+
+template <typename R>
+cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block,
+                          cudaStream_t s) {
+    if (mode == F_PROX) k_phase_f<R, F_PROX><<<grid, block, 0, s>>>(a, xp, zp, chk);
+    else if (mode == F_U_PROX) k_phase_f<R, F_U_PROX><<<grid, block, 0, s>>>(a, xp, zp, chk);
+    else k_phase_f<R, F_U_ONLY><<<grid, block, 0, s>>>(a, xp, zp, chk);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t sweep_phase_z(const SweepArgs<R> &a, int zp, long long it, int chk, int grid, int block,
+                          cudaStream_t s) {
+    k_phase_z<R><<<grid, block, 0, s>>>(a, zp, it, chk);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int zp, int final_check,
+                        int grid_partials, cudaStream_t s) {
+    k_check<R><<<1, 32, 0, s>>>(a, it_checked, xp, zp, final_check, grid_partials);
+    return cudaGetLastError();
+}
+
+template <typename R>
+int sweep_max_blocks_per_sm(int block) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_persistent<R>, block, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace fga

@@ -1,0 +1,113 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared entry
+point, and its host-side validation rejects bad input (no GPU needed until
+fga_finalize)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1603_02526_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fga_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    headers = [h for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h")]
+    names = []
+    for h in headers:
+        names += _declared(h)
+    assert "fga_iterate" in names and "fga_finalize" in names
+    for n in names:
+        assert hasattr(lib, n), "libfgadmm.so does not export %s" % n
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.fga_version()
+
+
+def _new(lib, prec=1):
+    g = ctypes.c_void_p()
+    assert lib.fga_graph_create(ctypes.byref(g), prec, 0, None) == 0
+    return g
+
+
+def test_validation_errors(lib):
+    from paper_1603_02526_gb300._lib import FGA_EINVAL, FGA_ESTATE
+    g = _new(lib)
+    first = ctypes.c_int64()
+    assert lib.fga_add_variables(g, 2, 2, ctypes.byref(first)) == 0 and first.value == 0
+    assert lib.fga_add_variables(g, 2, 1, ctypes.byref(first)) == 0 and first.value == 2
+    assert lib.fga_add_variables(g, 1, 0, None) == FGA_EINVAL
+    ids = np.array([[0, 2, 1, 3]], dtype=np.int64)
+    P = ctypes.c_void_p
+    # a valid pair factor
+    assert lib.fga_add_factors(g, 0, 1, 4, P(ids.ctypes.data), None, 0, 0, None) == 0
+    # out-of-range variable id
+    bad = np.array([[0, 2, 1, 9]], dtype=np.int64)
+    assert lib.fga_add_factors(g, 0, 1, 4, P(bad.ctypes.data), None, 0, 0, None) == FGA_EINVAL
+    assert b"out of range" in lib.fga_last_error()
+    # wrong shape for the type (radius on a 2-D variable)
+    one = np.array([[0]], dtype=np.int64)
+    w = np.array([1.0])
+    assert lib.fga_add_factors(g, 2, 1, 1, P(one.ctypes.data), P(w.ctypes.data), 1, 0, None) == FGA_EINVAL
+    # wrong parameter count for a wall
+    wall = np.array([[0, 2]], dtype=np.int64)
+    q = np.array([0.0, 1.0, 0.0])
+    assert lib.fga_add_factors(g, 1, 1, 2, P(wall.ctypes.data), P(q.ctypes.data), 3, 0, None) == FGA_EINVAL
+    # unknown type
+    assert lib.fga_add_factors(g, 42, 1, 1, P(one.ctypes.data), None, 0, 0, None) == FGA_EINVAL
+    # box with lo > hi
+    box = np.array([[2]], dtype=np.int64)
+    lohi = np.array([1.0, -1.0])
+    assert lib.fga_add_factors(g, 8, 1, 1, P(box.ctypes.data), P(lohi.ctypes.data), 2, 0, None) == FGA_EINVAL
+    # rho / alpha must be > 0
+    assert lib.fga_set_rho_alpha(g, 0.0, 1.0) == FGA_EINVAL
+    assert lib.fga_set_rho_alpha(g, 1.0, -1.0) == FGA_EINVAL
+    assert lib.fga_set_rho_alpha(g, 2.0, 1.0) == 0
+    # options: bad values
+    assert lib.fga_set_option(g, 2, 100) == FGA_EINVAL
+    assert lib.fga_set_option(g, 0, 3) == FGA_EINVAL
+    assert lib.fga_set_option(g, 0, 1) == 0
+    # calls that need a finalized / initialised graph
+    out = np.zeros(6)
+    assert lib.fga_read_z(g, P(out.ctypes.data), 6) == FGA_ESTATE
+    assert lib.fga_init(g, None, None) == FGA_ESTATE
+    e, z, f, v = (ctypes.c_int64() for _ in range(4))
+    assert lib.fga_graph_info(g, ctypes.byref(e), ctypes.byref(z), ctypes.byref(f), ctypes.byref(v)) == 0
+    assert (e.value, z.value, f.value, v.value) == (6, 6, 1, 4)
+    assert lib.fga_destroy(g) == 0
+
+
+def test_create_rejects_bad_precision(lib):
+    g = ctypes.c_void_p()
+    assert lib.fga_graph_create(ctypes.byref(g), 7, 0, None) == -1
+    assert lib.fga_graph_create(None, 0, 0, None) == -1
+
+
+def test_binding_counts_match_problem(lib):
+    """The binding registers a packing problem with the counts of Sec. V-A."""
+    from paper_1603_02526_gb300 import inputs
+    from paper_1603_02526_gb300.graph import FactorGraph, _merge_var_blocks
+    p = inputs.packing_problem(20)
+    g = FactorGraph("f32")
+    for c, d in _merge_var_blocks(p.var_blocks):
+        g.fga_add_variables(c, d)
+    for b in p.factor_blocks:
+        g.fga_add_factors(b.ftype, b.var_ids, b.params if b.params.size else None)
+    info = g.fga_graph_info()
+    assert info["num_edges"] == p.num_edges == 1340
+    assert info["num_factors"] == inputs.packing_counts(20)["factors"]
+    assert info["num_vars"] == 40

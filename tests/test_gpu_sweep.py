@@ -1,0 +1,204 @@
+"""GPU parity of the factor-graph sweep against the FP64 oracle (through the
+C-ABI).  FP64 runs use the canonical z-order and must match the oracle to
+1e-10 relative per message (floor 1e-3 of the array scale); in practice
+they agree bit for bit.  FP32 runs use the fast order; their tolerances are
+derived from FP32 rounding (see each test)."""
+import numpy as np
+import pytest
+
+from oracle import from_problem as oracle_from_problem
+from paper_1603_02526_gb300 import inputs
+from paper_1603_02526_gb300 import _lib
+from paper_1603_02526_gb300.graph import graph_from_problem, FactorGraph
+from tests.helpers import assert_messages_match, packing_objective, rel_close_floor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1603_02526_gb300 import build
+    build.build()
+
+
+def _both(problem, iters, precision="f64", fused=True, options=None, **kw):
+    g = graph_from_problem(problem, precision, options=options)
+    rg = g.fga_iterate(iters, fused=fused, **kw)
+    o = oracle_from_problem(problem)
+    ro = o.iterate(iters, **{k: v for k, v in kw.items() if k in ("tol_pri", "tol_dual", "check_every")})
+    return g, o, rg, ro
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_packing_n20_f64_5000_iterations(fused):
+    """Circle packing N=20, rho = alpha = 1, 5000 iterations, FP64."""
+    p = inputs.packing_problem(20)
+    g, o, rg, ro = _both(p, 5000, fused=fused)
+    assert rg["iters"] == ro["iters"] == 5000
+    assert_messages_match(g, o, 1e-10)
+    # the canonical order reproduces the serial sums exactly
+    assert np.array_equal(g.fga_read_z(), o.z())
+    np.testing.assert_allclose([rg["r_pri"], rg["r_dual"]], [ro["r_pri"], ro["r_dual"]], rtol=1e-12)
+
+
+def test_packing_chained_calls_equal_one_call():
+    """Resume: five calls of 1000 iterations reproduce one call of 5000."""
+    p = inputs.packing_problem(20)
+    a = graph_from_problem(p, "f64")
+    a.fga_iterate(5000)
+    b = graph_from_problem(p, "f64")
+    for _ in range(5):
+        b.fga_iterate(1000, check_every=7)
+    for w in range(4):
+        assert np.array_equal(a.fga_read_edge_state(w), b.fga_read_edge_state(w))
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+
+
+def test_packing_n1000_f64_full_size():
+    """The N=1000 graph (3,007,000 scalar edges) at FP64, a few iterations,
+    every message compared."""
+    p = inputs.packing_problem(1000)
+    g, o, rg, ro = _both(p, 3)
+    assert_messages_match(g, o, 1e-10)
+
+
+def test_packing_stop_rule_matches_oracle():
+    p = inputs.packing_problem(3)
+    p.factor_blocks[-1].params[:] = 0.1
+    for ce in (1, 5):
+        g, o, rg, ro = _both(p, 5000, tol_pri=1e-7, tol_dual=1e-7, check_every=ce)
+        assert rg["iters"] == ro["iters"] < 5000
+        assert rg["status"] == 0
+        assert_messages_match(g, o, 1e-10)
+
+
+def test_budget_status():
+    p = inputs.packing_problem(20)
+    g = graph_from_problem(p, "f64")
+    r = g.fga_iterate(10, tol_pri=1e-12, tol_dual=1e-12)
+    assert r["iters"] == 10 and r["status"] == _lib.FGA_EBUDGET
+
+
+def test_fast_order_f64_drift():
+    """The fast (tree) z-order in FP64: reported drift vs the canonical
+    order after 200 iterations of N=20 (non-convex, so differences of one
+    ulp may grow; bound 1e-8 relative with the floor)."""
+    p = inputs.packing_problem(20)
+    g = graph_from_problem(p, "f64", options={_lib.FGA_OPT_ZORDER: 1})
+    g.fga_iterate(200)
+    o = oracle_from_problem(p)
+    o.iterate(200)
+    ok, emax, _ = rel_close_floor(g.fga_read_z(), o.z(), 1e-8)
+    assert ok, emax
+
+
+def test_fig1_readout_in_creation_order():
+    p = inputs.fig1_problem()
+    g, o, rg, ro = _both(p, 25)
+    assert_messages_match(g, o, 1e-10)
+
+
+def test_per_edge_rho_alpha_and_area_reward():
+    """Non-uniform rho/alpha per edge (equal within each disk centre) and
+    the paper's area reward -r^2/2 with rho > 1."""
+    p = inputs.packing_problem(6, reward="quad", rho=1.5)
+    rng = np.random.default_rng(3)
+    o0 = oracle_from_problem(p)
+    E = o0.num_edges
+    ev = o0.edge_var()
+    alpha = 0.5 + rng.random(E)
+    g = FactorGraph("f64")
+    from paper_1603_02526_gb300.graph import _merge_var_blocks
+    for c, d in _merge_var_blocks(p.var_blocks):
+        g.fga_add_variables(c, d)
+    for b in p.factor_blocks:
+        g.fga_add_factors(b.ftype, b.var_ids, b.params if b.params.size else None)
+    # one rho per scalar variable; the two centre coordinates share one
+    rho = (1.2 + rng.random(p.num_scalar_vars))
+    rho[1::3] = rho[0::3]
+    rho_e = rho[ev]
+    g.fga_set_edge_rho_alpha(rho_e, alpha)
+    g.fga_finalize()
+    g.fga_init(p.z0)
+    g.fga_iterate(300)
+    o = oracle_from_problem(p)
+    o.set_rho_alpha(rho_e, alpha)
+    o.init(p.z0)
+    o.iterate(300)
+    assert_messages_match(g, o, 1e-10)
+
+
+def test_f32_packing_n20_objective():
+    """FP32 messages, FP64 residuals: N=20 (converging setting, reward 0.01)
+    run to residual 1e-4 by GPU and oracle; objective -sum r within 1e-4
+    relative of the oracle's."""
+    p = inputs.packing_problem(20)
+    p.factor_blocks[-1].params[:] = 0.01
+    g = graph_from_problem(p, "f32")
+    rg = g.fga_iterate(50000, 1e-4, 1e-4)
+    o = oracle_from_problem(p)
+    ro = o.iterate(50000, 1e-4, 1e-4)
+    assert rg["status"] == 0 and ro["status"] == 0
+    fg, fo = packing_objective(g.fga_read_z()), packing_objective(o.z())
+    assert abs(fg - fo) <= 1e-4 * abs(fo), (fg, fo, rg, ro)
+
+
+def test_f32_n1000_bench_configuration_first_iterations():
+    """The benchmark's launch configuration (N=1000, FP32, fused, fast
+    z-order) against the oracle after 3 iterations, every message.  FP32
+    rounding of O(1) values over a few operations: 2e-5 relative with the
+    floor at 1e-3 of the array scale."""
+    p = inputs.packing_problem(1000)
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1})
+    g.fga_iterate(3)
+    o = oracle_from_problem(p)
+    o.iterate(3)
+    assert_messages_match(g, o, 2e-5)
+
+
+def test_f32_is_deterministic():
+    p = inputs.packing_problem(200)
+    a = graph_from_problem(p, "f32")
+    a.fga_iterate(100)
+    b = graph_from_problem(p, "f32")
+    b.fga_iterate(100)
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+    assert np.array_equal(a.fga_read_edge_state(_lib.FGA_EDGE_U), b.fga_read_edge_state(_lib.FGA_EDGE_U))
+
+
+def test_barrier_time_limit_returns_timeout_and_recovers():
+    """Fault injection: one CTA skips its first barrier arrival; the bounded
+    wait runs out (50 ms) and fga_iterate returns FGA_ETIMEOUT.  The context
+    stays usable: after fga_init the same graph iterates normally."""
+    p = inputs.packing_problem(200)
+    g = graph_from_problem(p, "f32")
+    r = g.fga_iterate(10, barrier_timeout_ns=50_000_000, fault_skip_block=0, raise_on_error=False)
+    assert r["rc"] == _lib.FGA_ETIMEOUT and r["status"] == _lib.FGA_ETIMEOUT
+    with pytest.raises(_lib.FgaError):
+        g.fga_iterate(1)                       # state undefined until re-initialised
+    g.fga_init(p.z0)
+    r = g.fga_iterate(10)
+    assert r["iters"] == 10 and np.isfinite(r["r_pri"])
+
+
+def test_nonfinite_residual_reported():
+    """A start point that overflows FP32 makes the residual non-finite."""
+    p = inputs.packing_problem(5)
+    g = graph_from_problem(p, "f32", init=False)
+    z0 = p.z0.copy()
+    z0[0] = 1e300
+    g.fga_init(z0)
+    r = g.fga_iterate(5, raise_on_error=False)
+    assert r["rc"] == _lib.FGA_ENONFINITE and r["status"] == _lib.FGA_ENONFINITE
+
+
+def test_device_pointer_io():
+    torch = pytest.importorskip("torch")
+    p = inputs.packing_problem(20)
+    g = graph_from_problem(p, "f64", init=False)
+    z0 = torch.tensor(p.z0, dtype=torch.float64, device="cuda")
+    g.fga_init(z0)
+    g.fga_iterate(50)
+    zd = torch.empty(g.num_scalar_vars, dtype=torch.float64, device="cuda")
+    g.fga_read_z(zd)
+    assert np.array_equal(zd.cpu().numpy(), g.fga_read_z())
