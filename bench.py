@@ -291,6 +291,24 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """One warm-up and one solve of --profile-iters iterations (the workload
+    of the benchmark at a length that suits an ncu capture)."""
+    import torch
+    from paper_1603_02526_gb300 import build, inputs, _lib
+    from paper_1603_02526_gb300.graph import graph_from_problem
+    build.build()
+    p = inputs.packing_problem(N_DISKS, seed=SEED)
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_ZORDER: 1, _lib.FGA_OPT_STORE_M: 0})
+    g.fga_iterate(args.profile_iters, check_every=args.profile_iters)
+    g.fga_init(p.z0)
+    r = g.fga_iterate(args.profile_iters, check_every=args.profile_iters)
+    torch.cuda.synchronize()
+    print("profile run: %d iterations, %.3f ms, %.3e edge-updates/s" % (
+        r["iters"], r["ms"], p.num_edges * r["iters"] / (r["ms"] * 1e-3)))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,7 +317,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")
     args = ap.parse_args()
+    if args.profile_iters:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
