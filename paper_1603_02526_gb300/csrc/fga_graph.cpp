@@ -128,6 +128,8 @@ struct fga_graph {
     DevBuf res_pri, res_dual, ctl, bar;
     std::vector<std::unique_ptr<DevBuf>> bucket_bufs;
     int n_small = 0, n_witems = 0, n_hubs = 0;
+    DevBuf chunks, slot_var, ppos, lrow, lslot, lpos, part, prow;
+    int nchunks = 0, smem = 0;
     bool uniform_rho = true, uniform_alpha = true;
     int grid = 1, blk = 256;
 
@@ -425,6 +427,13 @@ static bool dyn_projector(int nx, int nu, const double *A, const double *B, cons
     return true;
 }
 
+// fast z-order layout built by build_chunks
+struct FastLayout {
+    std::vector<ChunkDev> chunks;
+    std::vector<int32_t> slot_var, ppos, lrow, prow;
+    std::vector<uint16_t> lslot, lpos;
+};
+
 template <typename R>
 static int upload_vec(DevBuf &buf, const std::vector<R> &v) {
     CUDA_TRY(buf.alloc(v.size() * sizeof(R)));
@@ -433,9 +442,9 @@ static int upload_vec(DevBuf &buf, const std::vector<R> &v) {
 }
 
 template <typename R>
-static int finalize_typed(fga_graph *g, const std::vector<int64_t> &c2s, const std::vector<int32_t> &pos,
-                          const std::vector<int32_t> &rowp, const std::vector<double> &srho_d,
-                          const std::vector<double> &srho2_d) {
+static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const std::vector<int32_t> &rowp,
+                          const std::vector<double> &srho_d, const std::vector<double> &srho2_d,
+                          const FastLayout &fl) {
     const int64_t E = g->ne;
     int rc;
     // per-edge rho / alpha in storage order (only when not uniform)
@@ -457,18 +466,33 @@ static int finalize_typed(fga_graph *g, const std::vector<int64_t> &c2s, const s
         if ((rc = upload_vec(g->srho, v))) return rc;
     }
     if ((rc = upload_vec(g->srho2, srho2_d))) return rc;
-    if ((rc = upload_vec(g->d_svar, g->svar))) return rc;
-    if ((rc = upload_vec(g->d_pos, pos))) return rc;
-    if ((rc = upload_vec(g->row, rowp))) return rc;
     const size_t eb = (size_t)std::max<int64_t>(E, 1) * sizeof(R);
+    if (g->zorder == 0) {
+        // canonical order: per-edge variable ids and positions in the
+        // creation-ordered variable-major array
+        if ((rc = upload_vec(g->d_svar, g->svar))) return rc;
+        if ((rc = upload_vec(g->d_pos, pos))) return rc;
+        if ((rc = upload_vec(g->row, rowp))) return rc;
+        CUDA_TRY(g->pvm.alloc(eb));
+        CUDA_TRY(cudaMemset(g->pvm.p, 0, eb));
+    } else {
+        if ((rc = upload_vec(g->chunks, fl.chunks))) return rc;
+        if ((rc = upload_vec(g->slot_var, fl.slot_var))) return rc;
+        if ((rc = upload_vec(g->ppos, fl.ppos))) return rc;
+        if ((rc = upload_vec(g->lrow, fl.lrow))) return rc;
+        if ((rc = upload_vec(g->lslot, fl.lslot))) return rc;
+        if ((rc = upload_vec(g->lpos, fl.lpos))) return rc;
+        if ((rc = upload_vec(g->prow, fl.prow))) return rc;
+        const size_t pb = std::max<size_t>(fl.slot_var.size(), 1) * sizeof(R);
+        CUDA_TRY(g->part.alloc(pb));
+        CUDA_TRY(cudaMemset(g->part.p, 0, pb));
+    }
     CUDA_TRY(g->x[0].alloc(eb));
     CUDA_TRY(g->x[1].alloc(eb));
     CUDA_TRY(g->u.alloc(eb));
-    CUDA_TRY(g->pvm.alloc(eb));
     CUDA_TRY(cudaMemset(g->x[0].p, 0, eb));
     CUDA_TRY(cudaMemset(g->x[1].p, 0, eb));
     CUDA_TRY(cudaMemset(g->u.p, 0, eb));
-    CUDA_TRY(cudaMemset(g->pvm.p, 0, eb));
     if (g->store_m) {
         CUDA_TRY(g->m[0].alloc(eb));
         CUDA_TRY(g->m[1].alloc(eb));
@@ -530,7 +554,145 @@ static int finalize_typed(fga_graph *g, const std::vector<int64_t> &c2s, const s
             g->bucket_bufs.push_back(std::move(ib));
         }
     }
-    (void)c2s;
+    return FGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fast z-order layout
+// ---------------------------------------------------------------------------
+// Cuts every bucket into chunks of consecutive work items (at most
+// kChunkItems items, kChunkEdges scalar edges and kChunkSlots distinct scalar
+// variables each), numbers each chunk's variables ("slots") in order of first
+// appearance, and gives every edge its slot and its position in the chunk's
+// slot-sorted buffer.  The per-slot partial sums are laid out variable-major
+// (chunk order inside a row).
+static int build_chunks(fga_graph *g, FastLayout &fl) {
+    const int64_t E = g->ne, Z = g->nz;
+    try {
+        fl.lslot.assign((size_t)E, 0);
+        fl.lpos.assign((size_t)E, 0);
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
+    }
+    std::vector<int32_t> mark((size_t)Z, -1), slot_of((size_t)Z, 0);
+    std::vector<int32_t> cnt;
+    std::vector<int64_t> edges;
+    int chunk_id = 0;
+    for (int bi = 0; bi < (int)g->buckets.size(); ++bi) {
+        const Bucket &bk = g->buckets[bi];
+        const int64_t nf = (int64_t)bk.members.size();
+        if (bk.arity > kChunkEdges) return fail(FGA_EINVAL, "fga_finalize: factor arity %d too large", bk.arity);
+        auto item_edges = [&](int64_t i, std::vector<int64_t> &out) {
+            out.clear();
+            if (bk.per_edge) {
+                out.push_back(bk.ebase + i);
+            } else {
+                for (int k = 0; k < bk.arity; ++k) out.push_back(bk.ebase + (int64_t)k * nf + i);
+            }
+        };
+        std::vector<int64_t> ie;
+        int64_t i = 0;
+        while (i < bk.nitems) {
+            ChunkDev ch;
+            std::memset(&ch, 0, sizeof ch);
+            ch.bucket = bi;
+            ch.f0 = i;
+            ch.sbase = (int)fl.slot_var.size();
+            ch.lrbase = (int)fl.lrow.size();
+            edges.clear();
+            int nslots = 0;
+            while (i < bk.nitems && i - ch.f0 < kChunkItems) {
+                item_edges(i, ie);
+                int fresh = 0;
+                for (int64_t e : ie) {
+                    const int32_t v = g->svar[e];
+                    if (mark[v] != chunk_id) {
+                        // count distinct new variables of this item once
+                        bool dup = false;
+                        for (int64_t e2 : ie) {
+                            if (e2 == e) break;
+                            if (g->svar[e2] == v) { dup = true; break; }
+                        }
+                        if (!dup) ++fresh;
+                    }
+                }
+                if (i == ch.f0 && fresh > kChunkSlots)
+                    return fail(FGA_EINVAL, "fga_finalize: a factor touches more than %d scalar variables",
+                                kChunkSlots);
+                if (i > ch.f0 && ((int64_t)edges.size() + (int64_t)ie.size() > kChunkEdges ||
+                                  nslots + fresh > kChunkSlots))
+                    break;
+                for (int64_t e : ie) {
+                    const int32_t v = g->svar[e];
+                    if (mark[v] != chunk_id) {
+                        mark[v] = chunk_id;
+                        slot_of[v] = nslots++;
+                        fl.slot_var.push_back(v);
+                    }
+                    edges.push_back(e);
+                }
+                ++i;
+            }
+            ch.nitems = (int)(i - ch.f0);
+            ch.nslots = nslots;
+            cnt.assign((size_t)nslots + 1, 0);
+            for (int64_t e : edges) cnt[slot_of[g->svar[e]] + 1]++;
+            for (int k = 0; k < nslots; ++k) cnt[k + 1] += cnt[k];
+            for (int k = 0; k <= nslots; ++k) fl.lrow.push_back(cnt[k]);
+            for (int64_t e : edges) {
+                const int sl = slot_of[g->svar[e]];
+                fl.lslot[e] = (uint16_t)sl;
+                fl.lpos[e] = (uint16_t)(cnt[sl]++);
+            }
+            fl.chunks.push_back(ch);
+            ++chunk_id;
+        }
+    }
+    // variable-major partials: row of variable b = its (chunk, slot) entries in chunk order
+    fl.prow.assign((size_t)Z + 1, 0);
+    for (int32_t v : fl.slot_var) fl.prow[v + 1]++;
+    for (int64_t b = 0; b < Z; ++b) fl.prow[b + 1] += fl.prow[b];
+    std::vector<int32_t> fill(fl.prow.begin(), fl.prow.end() - 1);
+    fl.ppos.resize(fl.slot_var.size());
+    for (size_t k = 0; k < fl.slot_var.size(); ++k) fl.ppos[k] = fill[fl.slot_var[k]]++;
+    g->nchunks = (int)fl.chunks.size();
+    return FGA_OK;
+}
+
+// Work lists of the fast z-update over rows `rowp`: low-degree rows one
+// thread each, others one warp each, hub rows split into kPiece pieces.
+static int build_zlists(fga_graph *g, const std::vector<int32_t> &rowp) {
+    int rc;
+    std::vector<int32_t> small, hub_np, hub_off;
+    std::vector<int4> witems, med;
+    int off = 0;
+    for (int64_t b = 0; b < g->nz; ++b) {
+        const int deg = rowp[b + 1] - rowp[b];
+        if (deg <= kSmallDeg) {
+            small.push_back((int32_t)b);
+        } else if (deg <= kPiece) {
+            med.push_back(make_int4((int)b, rowp[b], deg, -1));
+        } else {
+            const int h = (int)hub_np.size();
+            const int np = (deg + kPiece - 1) / kPiece;
+            hub_np.push_back(np);
+            hub_off.push_back(off);
+            off += np;
+            for (int p = 0; p < np; ++p)
+                witems.push_back(make_int4((int)b, rowp[b] + p * kPiece, std::min(kPiece, deg - p * kPiece), h));
+        }
+    }
+    witems.insert(witems.end(), med.begin(), med.end());
+    g->n_small = (int)small.size();
+    g->n_witems = (int)witems.size();
+    g->n_hubs = (int)hub_np.size();
+    if ((rc = upload_vec(g->small_vars, small))) return rc;
+    if ((rc = upload_vec(g->witems, witems))) return rc;
+    if ((rc = upload_vec(g->hub_np, hub_np))) return rc;
+    if ((rc = upload_vec(g->hub_off, hub_off))) return rc;
+    CUDA_TRY(g->hub_part.alloc((size_t)std::max(off, 1) * g->rsize()));
+    CUDA_TRY(g->hub_ticket.alloc((size_t)std::max(g->n_hubs, 1) * sizeof(unsigned int)));
+    CUDA_TRY(cudaMemset(g->hub_ticket.p, 0, g->hub_ticket.bytes));
     return FGA_OK;
 }
 
@@ -576,6 +738,23 @@ extern "C" int fga_finalize(fga_graph *g) {
             found = (int)g->buckets.size() - 1;
         }
         for (int64_t f = 0; f < b.count; ++f) g->buckets[found].members.emplace_back(bi, f);
+    }
+    // 1b. fast order: inside a bucket, factors that touch nearby variables
+    // are stored together (stable sort by the blocks of the first and last
+    // variable), so that a chunk of consecutive factors touches few variables
+    if (g->zorder == 1) {
+        for (Bucket &bk : g->buckets) {
+            auto key = [&](const std::pair<int, int64_t> &m) {
+                const FactorBatch &b = g->batches[m.first];
+                const int64_t v0 = b.vars[m.second * b.nv], v1 = b.vars[m.second * b.nv + b.nv - 1];
+                const int64_t first = g->voff[v0], last = g->voff[v1] + g->vdim[v1] - 1;
+                return std::make_pair(first / kLocalityBlock, last / kLocalityBlock);
+            };
+            std::stable_sort(bk.members.begin(), bk.members.end(),
+                             [&](const std::pair<int, int64_t> &a, const std::pair<int, int64_t> &b) {
+                                 return key(a) < key(b);
+                             });
+        }
     }
     // 2. storage order: bucket by bucket, edge-major inside a bucket
     std::vector<int64_t> c2s;
@@ -626,53 +805,31 @@ extern "C" int fga_finalize(fga_graph *g) {
         srho_d[b] += r;        // sequential, ascending creation order
         srho2_d[b] += r * r;
     }
-    // 4. fast z-order work lists
-    std::vector<int32_t> small, hub_np, hub_off;
-    std::vector<int4> witems;
+    // 4. fast z-order: chunks, their slots, and the variable-major partials
+    FastLayout fl;
     if (g->zorder == 1) {
-        std::vector<int4> med;
-        int off = 0;
-        for (int64_t b = 0; b < Z; ++b) {
-            const int deg = rowp[b + 1] - rowp[b];
-            if (deg <= kSmallDeg) {
-                small.push_back((int32_t)b);
-            } else if (deg <= kPiece) {
-                med.push_back(make_int4((int)b, rowp[b], deg, -1));
-            } else {
-                const int h = (int)hub_np.size();
-                const int np = (deg + kPiece - 1) / kPiece;
-                hub_np.push_back(np);
-                hub_off.push_back(off);
-                off += np;
-                for (int p = 0; p < np; ++p)
-                    witems.push_back(make_int4((int)b, rowp[b] + p * kPiece, std::min(kPiece, deg - p * kPiece), h));
-            }
-        }
-        witems.insert(witems.end(), med.begin(), med.end());
-        g->n_small = (int)small.size();
-        g->n_witems = (int)witems.size();
-        g->n_hubs = (int)hub_np.size();
-        if ((rc = upload_vec(g->small_vars, small))) return rc;
-        if ((rc = upload_vec(g->witems, witems))) return rc;
-        if ((rc = upload_vec(g->hub_np, hub_np))) return rc;
-        if ((rc = upload_vec(g->hub_off, hub_off))) return rc;
-        CUDA_TRY(g->hub_part.alloc((size_t)std::max(off, 1) * g->rsize()));
-        CUDA_TRY(g->hub_ticket.alloc((size_t)std::max(g->n_hubs, 1) * sizeof(unsigned int)));
-        CUDA_TRY(cudaMemset(g->hub_ticket.p, 0, g->hub_ticket.bytes));
+        if ((rc = build_chunks(g, fl))) return rc;
+        if ((rc = build_zlists(g, fl.prow))) return rc;
     }
     // 5. upload
-    rc = g->precision == FGA_F32 ? finalize_typed<float>(g, c2s, pos, rowp, srho_d, srho2_d)
-                                 : finalize_typed<double>(g, c2s, pos, rowp, srho_d, srho2_d);
+    rc = g->precision == FGA_F32 ? finalize_typed<float>(g, pos, rowp, srho_d, srho2_d, fl)
+                                 : finalize_typed<double>(g, pos, rowp, srho_d, srho2_d, fl);
     if (rc) return rc;
     // 6. launch shape: co-resident CTAs, no more than the work needs
     int dev_sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
     g->blk = g->block ? g->block : 256;
-    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk)
-                                            : sweep_max_blocks_per_sm<double>(g->blk);
+    g->smem = g->zorder == 1 ? (kChunkEdges + kChunkSlots) * (int)g->rsize() : 0;
+    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem)
+                                            : sweep_max_blocks_per_sm<double>(g->blk, g->smem);
     if (bps < 1) return fail(FGA_ECUDA, "fga_finalize: the sweep kernel cannot be resident at %d threads", g->blk);
     const int64_t full = (int64_t)bps * dev_sms;
-    const int64_t work = std::max<int64_t>(std::max<int64_t>(g->nitems_f, Z), (int64_t)g->n_witems * 32);
+    int64_t work;
+    if (g->zorder == 1)
+        work = std::max<int64_t>(std::max<int64_t>((int64_t)g->nchunks * g->blk, g->n_small),
+                                 (int64_t)g->n_witems * 32);
+    else
+        work = std::max<int64_t>(g->nitems_f, Z);
     g->grid = (int)std::max<int64_t>(1, std::min<int64_t>(full, (work + g->blk - 1) / g->blk));
     CUDA_TRY(g->res_pri.alloc((size_t)g->grid * sizeof(double)));
     CUDA_TRY(g->res_dual.alloc((size_t)2 * g->grid * sizeof(double)));
@@ -831,6 +988,15 @@ static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
     a.srho = g->srho.as<R>();
     a.srho2 = g->srho2.as<double>();
     a.row = g->row.as<int>();
+    a.nchunks = g->nchunks;
+    a.chunks = g->chunks.as<ChunkDev>();
+    a.slot_var = g->slot_var.as<int>();
+    a.ppos = g->ppos.as<int>();
+    a.lrow = g->lrow.as<int>();
+    a.lslot = g->lslot.as<unsigned short>();
+    a.lpos = g->lpos.as<unsigned short>();
+    a.part = g->part.as<R>();
+    a.prow = g->prow.as<int>();
     a.zorder = g->zorder;
     a.n_small = g->n_small;
     a.small_vars = g->small_vars.as<int>();
@@ -866,13 +1032,13 @@ static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
     if (g->n_hubs) CUDA_TRY(cudaMemsetAsync(g->hub_ticket.p, 0, g->hub_ticket.bytes, s));
     CUDA_TRY(cudaEventRecord(g->ev0, s));
     if (o.fused) {
-        CUDA_TRY(sweep_persistent<R>(a, g->grid, g->blk, s));
+        CUDA_TRY(sweep_persistent<R>(a, g->grid, g->blk, g->smem, s));
     } else {
         int xp = g->xpar, zp = g->zpar;
         for (long long it = 1; it <= a.K; ++it) {
             const bool pend = it > 1;
             const bool chk = pend && ((a.k0 + it - 1) % a.check_every == 0);
-            CUDA_TRY(sweep_phase_f<R>(a, pend ? F_U_PROX : F_PROX, xp, zp, chk ? 1 : 0, g->grid, g->blk, s));
+            CUDA_TRY(sweep_phase_f<R>(a, pend ? F_U_PROX : F_PROX, xp, zp, chk ? 1 : 0, g->grid, g->blk, g->smem, s));
             if (chk) CUDA_TRY(sweep_check<R>(a, it - 1, xp, zp, 0, g->grid, s));
             xp ^= 1;
             const bool chkz = ((a.k0 + it) % a.check_every == 0) || it == a.K;
@@ -880,7 +1046,7 @@ static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
             zp ^= 1;
         }
         if (a.K > 0) {
-            CUDA_TRY(sweep_phase_f<R>(a, F_U_ONLY, xp, zp, 1, g->grid, g->blk, s));
+            CUDA_TRY(sweep_phase_f<R>(a, F_U_ONLY, xp, zp, 1, g->grid, g->blk, g->smem, s));
             CUDA_TRY(sweep_check<R>(a, a.K, xp, zp, 1, g->grid, s));
         }
     }

@@ -10,6 +10,10 @@ namespace fga {
 constexpr int kMaxBuckets = 24;     // distinct (type, variable-shape) groups
 constexpr int kPiece = 2048;        // hub variables are reduced in pieces of this many edges
 constexpr int kSmallDeg = 16;       // fast z-order: thread per variable up to this degree
+constexpr int kChunkEdges = 8192;   // fast z-order: scalar edges per chunk (shared-memory buffer)
+constexpr int kChunkSlots = 2048;   // fast z-order: distinct scalar variables per chunk
+constexpr int kChunkItems = 1024;   // fast z-order: work items per chunk
+constexpr int kLocalityBlock = 96;  // fast z-order: factors are sorted by (first, last) variable / this
 
 // Phase-F modes: the x-update of one iteration, preceded (from the second
 // iteration of a call on) by the deferred u- and n-updates of the previous
@@ -34,6 +38,19 @@ struct Ctl {
     int zpar;          // z buffer that holds the state after the call
     int done;          // set when the call stopped (unfused launches exit early)
     int checked;       // at least one residual check happened
+    int pad;
+};
+
+// A chunk: consecutive work items of one bucket, processed by one CTA,
+// whose rho*m sums are reduced per touched variable ("slot") in shared
+// memory.
+struct ChunkDev {
+    int bucket;
+    int nitems;
+    long long f0;       // first work item inside the bucket
+    int nslots;
+    int sbase;          // first slot in slot_var / ppos
+    int lrbase;         // first entry of this chunk's slot row pointers in lrow
     int pad;
 };
 
@@ -80,6 +97,17 @@ struct SweepArgs {
     const double *srho2;  // sum of rho^2 over the variable's edges
     const int *row;       // variable-major row pointers [nz + 1]
 
+    // fast z-order: chunks and their per-slot partial sums
+    int nchunks;
+    const ChunkDev *chunks;
+    const int *slot_var;          // scalar variable of every (chunk, slot)
+    const int *ppos;              // position of every (chunk, slot) in part
+    const int *lrow;              // per chunk: nslots + 1 offsets into the chunk buffer
+    const unsigned short *lslot;  // per edge: slot inside its chunk
+    const unsigned short *lpos;   // per edge: position in the chunk buffer (slot-sorted)
+    R *part;                      // per-slot partial sums, variable-major
+    const int *prow;              // variable-major row pointers of part [nz + 1]
+
     // z-update work lists
     int zorder;           // 0 canonical, 1 fast
     int n_small;          // fast: variables reduced by one thread
@@ -107,11 +135,12 @@ struct SweepArgs {
     int xpar0, zpar0;
 };
 
-// Launchers (sweep_f32.cu / sweep_f64.cu).
+// Launchers (sweep_f32.cu / sweep_f64.cu).  `smem` = dynamic shared memory
+// per CTA (the fast order's chunk buffers; 0 in canonical order).
 template <typename R>
-cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, cudaStream_t s);
+cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, int smem, cudaStream_t s);
 template <typename R>
-cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block,
+cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block, int smem,
                           cudaStream_t s);
 template <typename R>
 cudaError_t sweep_phase_z(const SweepArgs<R> &a, int zp, long long it, int chk, int grid, int block,
@@ -120,6 +149,6 @@ template <typename R>
 cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int zp, int final_check,
                         int grid_partials, cudaStream_t s);
 template <typename R>
-int sweep_max_blocks_per_sm(int block);
+int sweep_max_blocks_per_sm(int block, int smem);
 
 }  // namespace fga

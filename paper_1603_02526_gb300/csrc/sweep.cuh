@@ -198,6 +198,11 @@ struct EdgeIO {
     R *xout;        // x of this iteration
     R *mout;        // m of this iteration (may be null)
     const R *zc;    // z after the previous iteration
+    // fast z-order only: the current chunk's z per slot and its rho*m buffer
+    // (shared memory), indexed through lslot / lpos
+    const R *zl;
+    R *pb;
+    int fast;
 };
 
 template <typename R>
@@ -205,12 +210,18 @@ __device__ __forceinline__ R edge_rho(const SweepArgs<R> &a, long long e) {
     return a.rho_e ? a.rho_e[e] : a.rho_u;
 }
 
+// z of the variable at the far end of edge e.
+template <typename R>
+__device__ __forceinline__ R edge_z(const SweepArgs<R> &a, const EdgeIO<R> &io, long long e) {
+    return io.fast ? io.zl[a.lslot[e]] : ldg_l2(io.zc + a.svar[e]);
+}
+
 // Deferred u-update of the previous iteration (when MODE != F_PROX) and the
 // n-update; returns n and leaves the current u in `u`.
 template <typename R, int MODE>
 __device__ __forceinline__ R edge_pre(const SweepArgs<R> &a, const EdgeIO<R> &io, long long e, R &u,
                                       double &pri) {
-    const R z = ldg_l2(io.zc + a.svar[e]);
+    const R z = edge_z(a, io, e);
     u = a.u[e];
     if (MODE != F_PROX) {
         const R al = a.alpha_e ? a.alpha_e[e] : a.alpha_u;
@@ -224,13 +235,17 @@ __device__ __forceinline__ R edge_pre(const SweepArgs<R> &a, const EdgeIO<R> &io
     return z - u;
 }
 
-// m-update and the scatter of rho*m into the variable-major array.
+// m-update, then rho*m either scattered into the variable-major array
+// (canonical order) or parked in the chunk's shared-memory buffer at the
+// edge's slot-sorted position (fast order).
 template <typename R>
 __device__ __forceinline__ void edge_post(const SweepArgs<R> &a, const EdgeIO<R> &io, long long e, R x, R u) {
     io.xout[e] = x;
     const R m = x + u;
     if (io.mout) io.mout[e] = m;
-    a.pvm[a.pos[e]] = edge_rho(a, e) * m;
+    const R p = edge_rho(a, e) * m;
+    if (io.fast) io.pb[a.lpos[e]] = p;
+    else a.pvm[a.pos[e]] = p;
 }
 
 // ---------------------------------------------------------------------------
@@ -313,7 +328,7 @@ __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const Buck
     for (int j = 0; j <= D; ++j) {
         const long long e = B.ebase + j * nf + f;
         const R u = a.u[e];
-        const R n = ldg_l2(io.zc + a.svar[e]) - u;
+        const R n = edge_z(a, io, e) - u;
         R x = n;
         if (active) x = (j < D) ? n + (gy * p[j * nf + f]) / edge_rho(a, e) : n + gy / edge_rho(a, e);
         edge_post(a, io, e, x, u);
@@ -352,7 +367,7 @@ __device__ __forceinline__ void item_mpc_dyn(const SweepArgs<R> &a, const Bucket
             R acc = R(0);
             for (int j = 0; j < A; ++j) {
                 const long long e = B.ebase + j * B.nf + f;
-                acc += __ldg(P + i * A + j) * (ldg_l2(io.zc + a.svar[e]) - a.u[e]);
+                acc += __ldg(P + i * A + j) * (edge_z(a, io, e) - a.u[e]);
             }
             const long long e = B.ebase + i * B.nf + f;
             edge_post(a, io, e, acc, a.u[e]);
@@ -399,11 +414,8 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
 }
 
 template <typename R, int MODE>
-__device__ __forceinline__ void process_item(const SweepArgs<R> &a, const EdgeIO<R> &io, long long it, double &pri) {
-    int b = 0;
-    while (b + 1 < a.nb && it >= a.bk[b + 1].item0) ++b;
-    const BucketDev<R> &B = a.bk[b];
-    const long long li = it - B.item0;
+__device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
+                                                  long long li, double &pri) {
     switch (B.type) {
     case 0: item_pack_pair<R, MODE>(a, B, io, li, pri); break;
     case 1: item_pack_wall<R, MODE>(a, B, io, li, pri); break;
@@ -417,10 +429,53 @@ __device__ __forceinline__ void process_item(const SweepArgs<R> &a, const EdgeIO
 }
 
 template <typename R, int MODE>
-__device__ __forceinline__ void phase_f(const SweepArgs<R> &a, const EdgeIO<R> &io, double &pri) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.nitems_f; it += stride)
-        process_item<R, MODE>(a, io, it, pri);
+__device__ __forceinline__ void process_item(const SweepArgs<R> &a, const EdgeIO<R> &io, long long it, double &pri) {
+    int b = 0;
+    while (b + 1 < a.nb && it >= a.bk[b + 1].item0) ++b;
+    process_in_bucket<R, MODE>(a, a.bk[b], io, it - a.bk[b].item0, pri);
+}
+
+// Canonical order: every work item on its own, rho*m scattered to the
+// variable-major array.  Fast order: CTAs walk their chunks; a chunk's
+// variables ("slots") get their z staged in shared memory, every edge's
+// rho*m lands in shared memory sorted by slot, and each slot's sum over the
+// chunk (edges in slot order, fixed shuffle tree) is written to the
+// variable-major partial array.  Both orders are deterministic.
+template <typename R, int MODE>
+__device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, double &pri) {
+    if (!io.fast) {
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.nitems_f; it += stride)
+            process_item<R, MODE>(a, io, it, pri);
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *pb = reinterpret_cast<R *>(smem_raw);
+    R *zl = pb + kChunkEdges;
+    io.pb = pb;
+    io.zl = zl;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
+        const ChunkDev ch = a.chunks[c];
+        for (int s = threadIdx.x; s < ch.nslots; s += blockDim.x) zl[s] = ldg_l2(io.zc + a.slot_var[ch.sbase + s]);
+        __syncthreads();
+        const BucketDev<R> &B = a.bk[ch.bucket];
+        for (int i = threadIdx.x; i < ch.nitems; i += blockDim.x)
+            process_in_bucket<R, MODE>(a, B, io, ch.f0 + i, pri);
+        __syncthreads();
+        if (MODE != F_U_ONLY) {
+            const int *lr = a.lrow + ch.lrbase;
+            for (int sl = warp; sl < ch.nslots; sl += nwarps) {
+                const int beg = lr[sl], end = lr[sl + 1];
+                R S = R(0);
+                for (int k = beg + lane; k < end; k += 32) S += pb[k];
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+                if (lane == 0) a.part[a.ppos[ch.sbase + sl]] = S;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -431,7 +486,7 @@ __device__ __forceinline__ void z_store(const SweepArgs<R> &a, int b, R S, const
                                         double &dual) {
     const R zold = zo[b];
     R znew = zold;
-    if (a.row[b + 1] > a.row[b]) znew = S / a.srho[b];   // a variable without edges keeps z
+    if (a.srho[b] > R(0)) znew = S / a.srho[b];   // a variable without edges keeps z
     zn[b] = znew;
     if (chk) {
         const double dz = (double)znew - (double)zold;
@@ -452,11 +507,14 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         }
         return;
     }
-    // fast: low-degree variables one thread each ...
+    // fast: sums of the chunk partials, row by row (variable-major)
+    const R *src = a.part;
+    const int *row = a.prow;
+    // low-degree variables one thread each ...
     for (long long i = gtid; i < a.n_small; i += gstride) {
         const int b = a.small_vars[i];
         R S = R(0);
-        for (int k = a.row[b]; k < a.row[b + 1]; ++k) S += ldg_l2(a.pvm + k);
+        for (int k = row[b]; k < row[b + 1]; ++k) S += ldg_l2(src + k);
         z_store(a, b, S, zo, zn, chk, dual);
     }
     // ... the others one warp per item (a whole row, or one piece of a hub
@@ -466,7 +524,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
     for (long long w = wid; w < a.n_witems; w += nw) {
         const int4 wi = a.witems[w];
         R S = R(0);
-        for (int k = lane; k < wi.z; k += 32) S += ldg_l2(a.pvm + wi.y + k);
+        for (int k = lane; k < wi.z; k += 32) S += ldg_l2(src + wi.y + k);
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
         if (wi.w < 0) {
@@ -474,7 +532,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
             continue;
         }
         const int h = wi.w;
-        const int piece = (wi.y - a.row[wi.x]) / kPiece;
+        const int piece = (wi.y - row[wi.x]) / kPiece;
         const int np = a.hub_npieces[h];
         unsigned int ticket = 0;
         if (lane == 0) {
@@ -557,6 +615,9 @@ __device__ __forceinline__ EdgeIO<R> make_io(const SweepArgs<R> &a, int xp, int 
     io.xout = a.x[xp ^ 1];
     io.mout = a.m[xp ^ 1];
     io.zc = a.z[zp];
+    io.zl = nullptr;
+    io.pb = nullptr;
+    io.fast = a.zorder;
     return io;
 }
 
@@ -564,7 +625,7 @@ __device__ __forceinline__ EdgeIO<R> make_io(const SweepArgs<R> &a, int xp, int 
 // the persistent kernel: a whole call in one launch
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_sweep_persistent(const SweepArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> a) {
     unsigned int gen = 0;
     const unsigned int G = gridDim.x;
     bool skip = (a.skip_block == (int)blockIdx.x);

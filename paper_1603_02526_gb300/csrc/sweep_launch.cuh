@@ -7,20 +7,39 @@
 namespace fga {
 
 template <typename R>
-cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, cudaStream_t s) {
+static cudaError_t allow_smem(int smem) {
+    // kernels that take the chunk buffers may need more than the default 48 KB
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_sweep_persistent<R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_U_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)k_phase_f<R, F_U_ONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem);
+}
+
+template <typename R>
+cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, int smem, cudaStream_t s) {
+    cudaError_t e = allow_smem<R>(smem);
+    if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
     // Cooperative launch: the runtime refuses a grid that cannot be
     // co-resident, so the grid-wide barrier can never wait on a CTA that
     // was not scheduled.
-    return cudaLaunchCooperativeKernel((const void *)k_sweep_persistent<R>, dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)k_sweep_persistent<R>, dim3(grid), dim3(block), args,
+                                       (size_t)smem, s);
 }
 
 template <typename R>
-cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block,
+cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block, int smem,
                           cudaStream_t s) {
-    if (mode == F_PROX) k_phase_f<R, F_PROX><<<grid, block, 0, s>>>(a, xp, zp, chk);
-    else if (mode == F_U_PROX) k_phase_f<R, F_U_PROX><<<grid, block, 0, s>>>(a, xp, zp, chk);
-    else k_phase_f<R, F_U_ONLY><<<grid, block, 0, s>>>(a, xp, zp, chk);
+    cudaError_t e = allow_smem<R>(smem);
+    if (e != cudaSuccess) return e;
+    if (mode == F_PROX) k_phase_f<R, F_PROX><<<grid, block, smem, s>>>(a, xp, zp, chk);
+    else if (mode == F_U_PROX) k_phase_f<R, F_U_PROX><<<grid, block, smem, s>>>(a, xp, zp, chk);
+    else k_phase_f<R, F_U_ONLY><<<grid, block, smem, s>>>(a, xp, zp, chk);
     return cudaGetLastError();
 }
 
@@ -39,9 +58,11 @@ cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int
 }
 
 template <typename R>
-int sweep_max_blocks_per_sm(int block) {
+int sweep_max_blocks_per_sm(int block, int smem) {
+    if (allow_smem<R>(smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_persistent<R>, block, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_persistent<R>, block, (size_t)smem) != cudaSuccess)
+        return 0;
     return n;
 }
 
