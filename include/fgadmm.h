@@ -188,6 +188,12 @@ typedef struct {
  * the call itself returns FGA_OK). */
 int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result);
 
+/* Launch configuration chosen at fga_finalize, for reports: info[0] CTAs,
+ * info[1] threads per CTA, info[2] dynamic shared memory per CTA (bytes),
+ * info[3] co-resident CTAs per SM, info[4] work chunks (fast z-order; 0 in
+ * canonical order), info[5] type buckets.  n >= 6. */
+int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n);
+
 /* Residuals of the last checked iteration (NaN before any). */
 int fga_residuals(const fga_graph *g, double *r_pri, double *r_dual);
 

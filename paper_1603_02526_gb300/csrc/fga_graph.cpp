@@ -95,6 +95,7 @@ struct Bucket {
     std::vector<std::pair<int, int64_t>> members;   // (batch, factor in batch), creation order
     int64_t ebase = 0, item0 = 0, nitems = 0;
     bool per_edge = false;
+    bool aos = false;      // factor-major storage of the bucket's edges
 };
 
 struct fga_graph {
@@ -118,7 +119,8 @@ struct fga_graph {
 
     // layout (host)
     std::vector<Bucket> buckets;
-    std::vector<int64_t> s2c;       // storage -> creation
+    std::vector<int64_t> s2c;       // storage -> creation (-1 for alignment padding)
+    int64_t es = 0;                 // storage slots (edges + padding)
     std::vector<int32_t> svar;      // storage order
     int64_t nitems_f = 0;
 
@@ -128,8 +130,8 @@ struct fga_graph {
     DevBuf res_pri, res_dual, ctl, bar;
     std::vector<std::unique_ptr<DevBuf>> bucket_bufs;
     int n_small = 0, n_witems = 0, n_hubs = 0;
-    DevBuf chunks, slot_var, ppos, lrow, lslot, lpos, part, prow;
-    int nchunks = 0, smem = 0;
+    DevBuf chunks, slot_var, ppos, lrow, lidx, part, prow;
+    int nchunks = 0, smem = 0, bps = 0;
     bool uniform_rho = true, uniform_alpha = true;
     int grid = 1, blk = 256;
 
@@ -431,7 +433,7 @@ static bool dyn_projector(int nx, int nu, const double *A, const double *B, cons
 struct FastLayout {
     std::vector<ChunkDev> chunks;
     std::vector<int32_t> slot_var, ppos, lrow, prow;
-    std::vector<uint16_t> lslot, lpos;
+    std::vector<uint32_t> lidx;   // slot | padded buffer position << 16
 };
 
 template <typename R>
@@ -450,14 +452,17 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
     // per-edge rho / alpha in storage order (only when not uniform)
     g->uniform_rho = g->rho_c.empty();
     g->uniform_alpha = g->alpha_c.empty();
+    const int64_t ES = g->es;
     if (!g->uniform_rho) {
-        std::vector<R> v((size_t)E);
-        for (int64_t s = 0; s < E; ++s) v[s] = (R)g->rho_c[g->s2c[s]];
+        std::vector<R> v((size_t)ES, R(1));
+        for (int64_t s = 0; s < ES; ++s)
+            if (g->s2c[s] >= 0) v[s] = (R)g->rho_c[g->s2c[s]];
         if ((rc = upload_vec(g->rho_e, v))) return rc;
     }
     if (!g->uniform_alpha) {
-        std::vector<R> v((size_t)E);
-        for (int64_t s = 0; s < E; ++s) v[s] = (R)g->alpha_c[g->s2c[s]];
+        std::vector<R> v((size_t)ES, R(1));
+        for (int64_t s = 0; s < ES; ++s)
+            if (g->s2c[s] >= 0) v[s] = (R)g->alpha_c[g->s2c[s]];
         if ((rc = upload_vec(g->alpha_e, v))) return rc;
     }
     {
@@ -466,7 +471,9 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         if ((rc = upload_vec(g->srho, v))) return rc;
     }
     if ((rc = upload_vec(g->srho2, srho2_d))) return rc;
-    const size_t eb = (size_t)std::max<int64_t>(E, 1) * sizeof(R);
+    // 64 spare elements: a bulk copy may read up to 16 bytes past the last edge
+    const size_t eb = (size_t)(std::max<int64_t>(ES, 1) + 64) * sizeof(R);
+    (void)E;
     if (g->zorder == 0) {
         // canonical order: per-edge variable ids and positions in the
         // creation-ordered variable-major array
@@ -480,8 +487,7 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         if ((rc = upload_vec(g->slot_var, fl.slot_var))) return rc;
         if ((rc = upload_vec(g->ppos, fl.ppos))) return rc;
         if ((rc = upload_vec(g->lrow, fl.lrow))) return rc;
-        if ((rc = upload_vec(g->lslot, fl.lslot))) return rc;
-        if ((rc = upload_vec(g->lpos, fl.lpos))) return rc;
+        if ((rc = upload_vec(g->lidx, fl.lidx))) return rc;
         if ((rc = upload_vec(g->prow, fl.prow))) return rc;
         const size_t pb = std::max<size_t>(fl.slot_var.size(), 1) * sizeof(R);
         CUDA_TRY(g->part.alloc(pb));
@@ -566,11 +572,10 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
 // appearance, and gives every edge its slot and its position in the chunk's
 // slot-sorted buffer.  The per-slot partial sums are laid out variable-major
 // (chunk order inside a row).
-static int build_chunks(fga_graph *g, FastLayout &fl) {
-    const int64_t E = g->ne, Z = g->nz;
+static int build_chunks(fga_graph *g, FastLayout &fl, int64_t items_per_chunk) {
+    const int64_t Z = g->nz;
     try {
-        fl.lslot.assign((size_t)E, 0);
-        fl.lpos.assign((size_t)E, 0);
+        fl.lidx.assign((size_t)g->es + 64, 0);   // spare tail for bulk copies
     } catch (...) {
         return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
     }
@@ -587,7 +592,8 @@ static int build_chunks(fga_graph *g, FastLayout &fl) {
             if (bk.per_edge) {
                 out.push_back(bk.ebase + i);
             } else {
-                for (int k = 0; k < bk.arity; ++k) out.push_back(bk.ebase + (int64_t)k * nf + i);
+                for (int k = 0; k < bk.arity; ++k)
+                    out.push_back(bk.aos ? bk.ebase + i * bk.arity + k : bk.ebase + (int64_t)k * nf + i);
             }
         };
         std::vector<int64_t> ie;
@@ -601,8 +607,15 @@ static int build_chunks(fga_graph *g, FastLayout &fl) {
             ch.lrbase = (int)fl.lrow.size();
             edges.clear();
             int nslots = 0;
-            while (i < bk.nitems && i - ch.f0 < kChunkItems) {
+            // disk-pair chunks start at even factors (16-byte aligned bulk copies)
+            const int64_t unit = bk.type == FGA_PACK_PAIR ? 2 : 1;
+            while (i < bk.nitems && i - ch.f0 < items_per_chunk) {
                 item_edges(i, ie);
+                if (unit == 2 && i + 1 < bk.nitems) {
+                    std::vector<int64_t> ie2;
+                    item_edges(i + 1, ie2);
+                    ie.insert(ie.end(), ie2.begin(), ie2.end());
+                }
                 int fresh = 0;
                 for (int64_t e : ie) {
                     const int32_t v = g->svar[e];
@@ -631,7 +644,7 @@ static int build_chunks(fga_graph *g, FastLayout &fl) {
                     }
                     edges.push_back(e);
                 }
-                ++i;
+                i += (unit == 2 && i + 1 < bk.nitems) ? 2 : 1;
             }
             ch.nitems = (int)(i - ch.f0);
             ch.nslots = nslots;
@@ -640,9 +653,12 @@ static int build_chunks(fga_graph *g, FastLayout &fl) {
             for (int k = 0; k < nslots; ++k) cnt[k + 1] += cnt[k];
             for (int k = 0; k <= nslots; ++k) fl.lrow.push_back(cnt[k]);
             for (int64_t e : edges) {
+                // segments are padded by one element each (slot sl starts at
+                // cnt[sl] + sl) so that lanes writing to different slots hit
+                // different shared-memory banks
                 const int sl = slot_of[g->svar[e]];
-                fl.lslot[e] = (uint16_t)sl;
-                fl.lpos[e] = (uint16_t)(cnt[sl]++);
+                const uint32_t pos = (uint32_t)(cnt[sl]++ + sl);
+                fl.lidx[e] = (uint32_t)sl | (pos << 16);
             }
             fl.chunks.push_back(ch);
             ++chunk_id;
@@ -734,6 +750,7 @@ extern "C" int fga_finalize(fga_graph *g) {
             nb.np = b.np;
             nb.arity = b.arity;
             nb.per_edge = is_per_edge(b.type);
+            nb.aos = b.type == FGA_PACK_PAIR || b.type == FGA_PACK_WALL || b.type == FGA_MPC_DYN;
             g->buckets.push_back(nb);
             found = (int)g->buckets.size() - 1;
         }
@@ -756,11 +773,15 @@ extern "C" int fga_finalize(fga_graph *g) {
                              });
         }
     }
-    // 2. storage order: bucket by bucket, edge-major inside a bucket
+    // 2. storage order: bucket by bucket (each base a multiple of 4),
+    // factor-major or edge-major inside a bucket
+    int64_t es = 0;
+    for (const Bucket &bk : g->buckets) es = ((es + 3) & ~int64_t(3)) + (int64_t)bk.members.size() * bk.arity;
+    if (es > (int64_t)INT32_MAX - 8) return fail(FGA_EINVAL, "fga_finalize: more than 2^31 edges with padding");
     std::vector<int64_t> c2s;
     try {
-        g->s2c.assign((size_t)E, 0);
-        g->svar.assign((size_t)E, 0);
+        g->s2c.assign((size_t)es, -1);
+        g->svar.assign((size_t)es, 0);
         c2s.assign((size_t)E, 0);
     } catch (...) {
         return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
@@ -768,6 +789,7 @@ extern "C" int fga_finalize(fga_graph *g) {
     int64_t ebase = 0, item = 0;
     for (Bucket &bk : g->buckets) {
         const int64_t nf = (int64_t)bk.members.size();
+        ebase = (ebase + 3) & ~int64_t(3);
         bk.ebase = ebase;
         bk.item0 = item;
         bk.nitems = bk.per_edge ? nf * bk.arity : nf;
@@ -779,7 +801,7 @@ extern "C" int fga_finalize(fga_graph *g) {
             for (int v = 0; v < b.nv; ++v) {
                 const int64_t var = b.vars[fi * b.nv + v];
                 for (int d = 0; d < b.dims[v]; ++d, ++k) {
-                    const int64_t s = ebase + (int64_t)k * nf + f;
+                    const int64_t s = bk.aos ? ebase + f * bk.arity + k : ebase + (int64_t)k * nf + f;
                     g->s2c[s] = c0 + k;
                     c2s[c0 + k] = s;
                     g->svar[s] = (int32_t)(g->voff[var] + d);
@@ -789,12 +811,13 @@ extern "C" int fga_finalize(fga_graph *g) {
         ebase += nf * bk.arity;
         item += bk.nitems;
     }
+    g->es = es;
     g->nitems_f = item;
     // 3. variable-major rows, each in ascending creation order
     const int64_t Z = g->nz;
-    std::vector<int32_t> rowp((size_t)Z + 1, 0), pos((size_t)E, 0), fill((size_t)Z, 0);
+    std::vector<int32_t> rowp((size_t)Z + 1, 0), pos((size_t)es, 0), fill((size_t)Z, 0);
     std::vector<double> srho_d((size_t)Z, 0.0), srho2_d((size_t)Z, 0.0);
-    for (int64_t s = 0; s < E; ++s) rowp[g->svar[s] + 1]++;
+    for (int64_t c = 0; c < E; ++c) rowp[g->svar[c2s[c]] + 1]++;
     for (int64_t b = 0; b < Z; ++b) rowp[b + 1] += rowp[b];
     for (int64_t b = 0; b < Z; ++b) fill[b] = rowp[b];
     for (int64_t c = 0; c < E; ++c) {
@@ -807,8 +830,29 @@ extern "C" int fga_finalize(fga_graph *g) {
     }
     // 4. fast z-order: chunks, their slots, and the variable-major partials
     FastLayout fl;
+    int dev_sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
+    g->blk = g->block ? g->block : 256;
+    g->smem = g->zorder == 1 ? chunk_smem((int)g->rsize()).total : 0;
+    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem)
+                                            : sweep_max_blocks_per_sm<double>(g->blk, g->smem);
+    if (bps < 1) return fail(FGA_ECUDA, "fga_finalize: the sweep kernel cannot be resident at %d threads", g->blk);
+    g->bps = bps;
+    const int64_t full = (int64_t)bps * dev_sms;
     if (g->zorder == 1) {
-        if ((rc = build_chunks(g, fl))) return rc;
+        // about one chunk per resident CTA, so that phase F is balanced: the
+        // smallest chunk size whose chunk count (buckets are cut separately)
+        // does not exceed the resident grid
+        auto count_chunks = [&](int64_t per) {
+            int64_t n = 0;
+            for (const Bucket &bk : g->buckets) n += (bk.nitems + per - 1) / per;
+            return n;
+        };
+        int64_t per = std::max<int64_t>(32, (g->nitems_f + full - 1) / full);
+        per += per & 1;
+        while (per < kChunkItems && count_chunks(per) > full) per += 2 * std::max<int64_t>(1, per / 128);
+        per = std::min<int64_t>(kChunkItems, per);
+        if ((rc = build_chunks(g, fl, per))) return rc;
         if ((rc = build_zlists(g, fl.prow))) return rc;
     }
     // 5. upload
@@ -816,14 +860,6 @@ extern "C" int fga_finalize(fga_graph *g) {
                                  : finalize_typed<double>(g, pos, rowp, srho_d, srho2_d, fl);
     if (rc) return rc;
     // 6. launch shape: co-resident CTAs, no more than the work needs
-    int dev_sms = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
-    g->blk = g->block ? g->block : 256;
-    g->smem = g->zorder == 1 ? (kChunkEdges + kChunkSlots) * (int)g->rsize() : 0;
-    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem)
-                                            : sweep_max_blocks_per_sm<double>(g->blk, g->smem);
-    if (bps < 1) return fail(FGA_ECUDA, "fga_finalize: the sweep kernel cannot be resident at %d threads", g->blk);
-    const int64_t full = (int64_t)bps * dev_sms;
     int64_t work;
     if (g->zorder == 1)
         work = std::max<int64_t>(std::max<int64_t>((int64_t)g->nchunks * g->blk, g->n_small),
@@ -905,16 +941,17 @@ static int init_typed(fga_graph *g, const std::vector<double> &z0, const std::ve
             CUDA_TRY(cudaMemcpyAsync(g->z[0].p, zr.data(), zr.size() * sizeof(R), cudaMemcpyHostToDevice, st));
         }
     }
-    if (g->ne) {
+    if (g->es) {
         if (u0.empty()) {
-            CUDA_TRY(cudaMemsetAsync(g->u.p, 0, (size_t)g->ne * sizeof(R), st));
+            CUDA_TRY(cudaMemsetAsync(g->u.p, 0, (size_t)g->es * sizeof(R), st));
         } else {
-            ur.resize((size_t)g->ne);
-            for (int64_t s = 0; s < g->ne; ++s) ur[s] = (R)u0[g->s2c[s]];
+            ur.assign((size_t)g->es, R(0));
+            for (int64_t s = 0; s < g->es; ++s)
+                if (g->s2c[s] >= 0) ur[s] = (R)u0[g->s2c[s]];
             CUDA_TRY(cudaMemcpyAsync(g->u.p, ur.data(), ur.size() * sizeof(R), cudaMemcpyHostToDevice, st));
         }
-        CUDA_TRY(cudaMemsetAsync(g->x[0].p, 0, (size_t)g->ne * sizeof(R), st));
-        if (g->store_m) CUDA_TRY(cudaMemsetAsync(g->m[0].p, 0, (size_t)g->ne * sizeof(R), st));
+        CUDA_TRY(cudaMemsetAsync(g->x[0].p, 0, (size_t)g->es * sizeof(R), st));
+        if (g->store_m) CUDA_TRY(cudaMemsetAsync(g->m[0].p, 0, (size_t)g->es * sizeof(R), st));
     }
     CUDA_TRY(cudaStreamSynchronize(st));
     return FGA_OK;
@@ -957,18 +994,19 @@ static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
         d.arity = bk.arity;
         d.nprm = bk.np;
         d.per_edge = bk.per_edge ? 1 : 0;
+        d.aos = bk.aos ? 1 : 0;
         for (int k = 0; k < 4; ++k) d.dims[k] = k < (int)bk.dims.size() ? bk.dims[k] : 0;
-        d.nf = (long long)bk.members.size();
-        d.ebase = bk.ebase;
-        d.item0 = bk.item0;
-        d.nitems = bk.nitems;
+        d.nf = (int)bk.members.size();
+        d.ebase = (int)bk.ebase;
+        d.item0 = (int)bk.item0;
+        d.nitems = (int)bk.nitems;
         d.prm = g->bucket_bufs[pb++]->as<R>();
         if (bk.type == FGA_MPC_DYN) {
             d.pmat = g->bucket_bufs[pb++]->as<R>();
             d.pidx = g->bucket_bufs[pb++]->as<int>();
         }
     }
-    a.nitems_f = g->nitems_f;
+    a.nitems_f = (int)g->nitems_f;
     a.E = g->ne;
     a.nz = (int)g->nz;
     a.x[0] = g->x[0].as<R>();
@@ -993,8 +1031,7 @@ static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
     a.slot_var = g->slot_var.as<int>();
     a.ppos = g->ppos.as<int>();
     a.lrow = g->lrow.as<int>();
-    a.lslot = g->lslot.as<unsigned short>();
-    a.lpos = g->lpos.as<unsigned short>();
+    a.lidx = g->lidx.as<unsigned>();
     a.part = g->part.as<R>();
     a.prow = g->prow.as<int>();
     a.zorder = g->zorder;
@@ -1104,6 +1141,18 @@ extern "C" int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_res
     return rc;
 }
 
+extern "C" int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n) {
+    if (!g || !info || n < 6) return fail(FGA_EINVAL, "fga_launch_info: need an array of 6");
+    if (!g->finalized) return fail(FGA_ESTATE, "fga_launch_info: graph not finalized");
+    info[0] = g->grid;
+    info[1] = g->blk;
+    info[2] = g->smem;
+    info[3] = g->bps;
+    info[4] = g->zorder == 1 ? g->nchunks : 0;
+    info[5] = (int64_t)g->buckets.size();
+    return FGA_OK;
+}
+
 extern "C" int fga_residuals(const fga_graph *g, double *r_pri, double *r_dual) {
     if (!g) return fail(FGA_EINVAL, "fga_residuals: NULL graph");
     if (r_pri) *r_pri = g->last_rp;
@@ -1135,22 +1184,25 @@ extern "C" int fga_read_z(fga_graph *g, double *out, int64_t n) {
 
 template <typename R>
 static int read_edge_typed(fga_graph *g, int which, double *out) {
-    const int64_t E = g->ne;
+    const int64_t ES = g->es;
     std::vector<R> v, u, z;
     int rc;
-    std::vector<double> res((size_t)E);
+    std::vector<double> res((size_t)g->ne);
     if (which == FGA_EDGE_X || which == FGA_EDGE_M) {
         const DevBuf &b = which == FGA_EDGE_X ? g->x[g->xpar] : g->m[g->xpar];
-        if ((rc = download(b, E, v, g->stream))) return rc;
-        for (int64_t s = 0; s < E; ++s) res[g->s2c[s]] = (double)v[s];
+        if ((rc = download(b, ES, v, g->stream))) return rc;
+        for (int64_t s = 0; s < ES; ++s)
+            if (g->s2c[s] >= 0) res[g->s2c[s]] = (double)v[s];
     } else if (which == FGA_EDGE_U) {
-        if ((rc = download(g->u, E, u, g->stream))) return rc;
-        for (int64_t s = 0; s < E; ++s) res[g->s2c[s]] = (double)u[s];
+        if ((rc = download(g->u, ES, u, g->stream))) return rc;
+        for (int64_t s = 0; s < ES; ++s)
+            if (g->s2c[s] >= 0) res[g->s2c[s]] = (double)u[s];
     } else {
         // n = z_b - u, evaluated in the working precision as the sweep does
-        if ((rc = download(g->u, E, u, g->stream))) return rc;
+        if ((rc = download(g->u, ES, u, g->stream))) return rc;
         if ((rc = download(g->z[g->zpar], g->nz, z, g->stream))) return rc;
-        for (int64_t s = 0; s < E; ++s) {
+        for (int64_t s = 0; s < ES; ++s) {
+            if (g->s2c[s] < 0) continue;
             const R n = z[g->svar[s]] - u[s];
             res[g->s2c[s]] = (double)n;
         }

@@ -10,10 +10,36 @@ namespace fga {
 constexpr int kMaxBuckets = 24;     // distinct (type, variable-shape) groups
 constexpr int kPiece = 2048;        // hub variables are reduced in pieces of this many edges
 constexpr int kSmallDeg = 16;       // fast z-order: thread per variable up to this degree
-constexpr int kChunkEdges = 8192;   // fast z-order: scalar edges per chunk (shared-memory buffer)
-constexpr int kChunkSlots = 2048;   // fast z-order: distinct scalar variables per chunk
-constexpr int kChunkItems = 1024;   // fast z-order: work items per chunk
+constexpr int kChunkEdges = 6912;   // fast z-order: scalar edges per chunk (shared-memory buffer)
+constexpr int kChunkSlots = 1024;   // fast z-order: distinct scalar variables per chunk
+constexpr int kStagePairs = 128;    // fast z-order: disk pairs per bulk-copy stage
+constexpr int kChunkItems = 2048;   // fast z-order: work items per chunk (upper limit)
 constexpr int kLocalityBlock = 96;  // fast z-order: factors are sorted by (first, last) variable / this
+
+// Shared-memory layout of one CTA in the fast z-order (byte offsets):
+// rho*m buffer (padded slot segments), z per slot, slot row starts, slot
+// destinations, two bulk-copy stages of (u, x, slot/position index) for disk
+// pairs, and the two stage barriers.
+struct ChunkSmem {
+    int pb, zl, lr, pp, st, bar, total;
+    int stage_u, stage_x, stage_i, stage_bytes;   // offsets inside one stage
+};
+inline __host__ __device__ constexpr int align16(int v) { return (v + 15) & ~15; }
+inline __host__ __device__ constexpr ChunkSmem chunk_smem(int rsize) {
+    ChunkSmem l{};
+    l.pb = 0;
+    l.zl = align16(l.pb + (kChunkEdges + kChunkSlots) * rsize);
+    l.lr = align16(l.zl + kChunkSlots * rsize);
+    l.pp = align16(l.lr + (kChunkSlots + 1) * 4);
+    l.st = align16(l.pp + kChunkSlots * 4);
+    l.stage_u = 0;
+    l.stage_x = align16(6 * kStagePairs * rsize);
+    l.stage_i = l.stage_x + align16(6 * kStagePairs * rsize);
+    l.stage_bytes = l.stage_i + align16(6 * kStagePairs * 4);
+    l.bar = align16(l.st + 2 * l.stage_bytes);
+    l.total = l.bar + 16;
+    return l;
+}
 
 // Phase-F modes: the x-update of one iteration, preceded (from the second
 // iteration of a call on) by the deferred u- and n-updates of the previous
@@ -54,19 +80,21 @@ struct ChunkDev {
     int pad;
 };
 
-// One bucket = all factors of one type with one variable shape, stored
-// edge-major: scalar edge k of factor f lives at ebase + k * nf + f.
+// One bucket = all factors of one type with one variable shape.  Scalar
+// edge k of factor f lives at ebase + f * arity + k (factor-major) or at
+// ebase + k * nf + f (edge-major).
 template <typename R>
 struct BucketDev {
     int type;
     int arity;          // scalar edges per factor
     int nprm;           // parameters per factor (SoA: prm[j * nf + f])
     int per_edge;       // 1: elementwise prox, one work item per scalar edge
+    int aos;            // 1: factor-major storage (ebase + f * arity + k)
     int dims[4];        // variable dimensions (types with a fixed shape)
-    long long nf;       // factors
-    long long ebase;    // first storage edge
-    long long item0;    // first phase-F work item
-    long long nitems;   // work items (nf, or nf * arity when per_edge)
+    int nf;             // factors
+    int ebase;          // first storage edge (a multiple of 4)
+    int item0;          // first phase-F work item
+    int nitems;         // work items (nf, or nf * arity when per_edge)
     const R *prm;       // parameters, SoA
     const R *pmat;      // MPC_DYN: projection matrices, arity x arity each
     const int *pidx;    // MPC_DYN: matrix index of each factor
@@ -76,8 +104,8 @@ template <typename R>
 struct SweepArgs {
     int nb;
     BucketDev<R> bk[kMaxBuckets];
-    long long nitems_f;   // phase-F work items over all buckets
-    long long E;          // scalar edges
+    int nitems_f;         // phase-F work items over all buckets
+    long long E;          // scalar edges (for the RMS residuals)
     int nz;               // scalar variables
 
     // per-edge state, storage order
@@ -103,8 +131,8 @@ struct SweepArgs {
     const int *slot_var;          // scalar variable of every (chunk, slot)
     const int *ppos;              // position of every (chunk, slot) in part
     const int *lrow;              // per chunk: nslots + 1 offsets into the chunk buffer
-    const unsigned short *lslot;  // per edge: slot inside its chunk
-    const unsigned short *lpos;   // per edge: position in the chunk buffer (slot-sorted)
+    const unsigned *lidx;         // per edge: slot inside its chunk | position in the
+                                  // chunk buffer (slot-sorted, padded) << 16
     R *part;                      // per-slot partial sums, variable-major
     const int *prow;              // variable-major row pointers of part [nz + 1]
 

@@ -59,6 +59,47 @@ static __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p,
     return old;
 }
 
+// ---- mbarrier + bulk asynchronous copy (global -> shared) --------------------
+static __device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+static __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+static __device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+static __device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+static __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+static __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1-D bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on `bar`.
+static __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+static __device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+static __device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // Grid-wide barrier with a time limit.  One thread per CTA arrives on a
 // counter; the last arrival resets the counter and bumps the generation.
 // Every wait is bounded by timeout_ns (globaltimer) and by a spin count; on
@@ -170,6 +211,45 @@ __device__ __forceinline__ void prox_pack_pair(const R *n, const R *rho, R *x) {
     x[5] = n[5] - tr2;
 }
 
+// FP32 variant of the same projection: the direction and length come from
+// one approximate reciprocal square root, and with a uniform rho every
+// share w_k / W is 1/4.  (FP32 results are compared with the FP64 oracle
+// through tolerances, never bit for bit.)
+__device__ __forceinline__ void prox_pack_pair_f32(const float *n, const float *rho, bool uniform, float *x) {
+    const float dx = n[3] - n[0];
+    const float dy = n[4] - n[1];
+    const float d2 = dx * dx + dy * dy;
+    const float rd = d2 > 0.f ? rsqrtf(d2) : 0.f;
+    const float D = n[2] + n[5] - d2 * rd;
+    if (!(D > 0.f)) {
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] = n[k];
+        return;
+    }
+    float hx = 1.f, hy = 0.f;
+    if (d2 > 0.f) {
+        hx = dx * rd;
+        hy = dy * rd;
+    }
+    float tc1, tr1, tc2, tr2;
+    if (uniform) {
+        tc1 = tr1 = tc2 = tr2 = 0.25f * D;
+    } else {
+        const float wc1 = 1.f / rho[0], wr1 = 1.f / rho[2], wc2 = 1.f / rho[3], wr2 = 1.f / rho[5];
+        const float iW = D / (wc1 + wr1 + wc2 + wr2);
+        tc1 = wc1 * iW;
+        tr1 = wr1 * iW;
+        tc2 = wc2 * iW;
+        tr2 = wr2 * iW;
+    }
+    x[0] = n[0] - tc1 * hx;
+    x[1] = n[1] - tc1 * hy;
+    x[2] = n[2] - tr1;
+    x[3] = n[3] + tc2 * hx;
+    x[4] = n[4] + tc2 * hy;
+    x[5] = n[5] - tr2;
+}
+
 // Appendix A wall: disk (c, r) inside the half-plane Q.(c - V) >= r.
 template <typename R>
 __device__ __forceinline__ void prox_pack_wall(const R *n, const R *rho, R Qx, R Qy, R Vx, R Vy, R *x) {
@@ -190,133 +270,264 @@ __device__ __forceinline__ void prox_pack_wall(const R *n, const R *rho, R Qx, R
 }
 
 // ---------------------------------------------------------------------------
-// per-edge pre/post steps of phase F
+// edge access.  Storage index of scalar edge k of factor f in bucket B:
+// factor-major (B.aos: the factor's edges are adjacent, ebase + f*arity + k)
+// or edge-major (ebase + k*nf + f).  Indices are 32-bit (|E| < 2^31).
 // ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int bedge(const BucketDev<R> &B, int f, int k) {
+    return B.aos ? B.ebase + f * B.arity + k : B.ebase + k * B.nf + f;
+}
+
 template <typename R>
 struct EdgeIO {
     const R *xin;   // x after the previous iteration
     R *xout;        // x of this iteration
     R *mout;        // m of this iteration (may be null)
     const R *zc;    // z after the previous iteration
-    // fast z-order only: the current chunk's z per slot and its rho*m buffer
-    // (shared memory), indexed through lslot / lpos
+    // fast order only: the current chunk's z per slot and its rho*m buffer
+    // (shared memory), addressed through lidx = slot | position << 16
     const R *zl;
     R *pb;
-    int fast;
+    int chk;        // accumulate the primal residual (check iterations only)
 };
 
 template <typename R>
-__device__ __forceinline__ R edge_rho(const SweepArgs<R> &a, long long e) {
+__device__ __forceinline__ R edge_rho(const SweepArgs<R> &a, int e) {
     return a.rho_e ? a.rho_e[e] : a.rho_u;
 }
 
-// z of the variable at the far end of edge e.
-template <typename R>
-__device__ __forceinline__ R edge_z(const SweepArgs<R> &a, const EdgeIO<R> &io, long long e) {
-    return io.fast ? io.zl[a.lslot[e]] : ldg_l2(io.zc + a.svar[e]);
+// z at the far end of edge e; `ix` receives what edge_put needs later.
+template <typename R, bool FAST>
+__device__ __forceinline__ R edge_z(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, unsigned &ix) {
+    if (FAST) {
+        ix = a.lidx[e];
+        return io.zl[ix & 0xffffu];
+    }
+    ix = (unsigned)e;
+    return ldg_l2(io.zc + a.svar[e]);
+}
+
+template <typename R, bool FAST>
+__device__ __forceinline__ void edge_put(const SweepArgs<R> &a, const EdgeIO<R> &io, unsigned ix, R p) {
+    if (FAST) io.pb[ix >> 16] = p;
+    else a.pvm[a.pos[ix]] = p;
 }
 
 // Deferred u-update of the previous iteration (when MODE != F_PROX) and the
-// n-update; returns n and leaves the current u in `u`.
+// n-update, given z and the current u; returns n, updates u.
 template <typename R, int MODE>
-__device__ __forceinline__ R edge_pre(const SweepArgs<R> &a, const EdgeIO<R> &io, long long e, R &u,
-                                      double &pri) {
-    const R z = edge_z(a, io, e);
-    u = a.u[e];
+__device__ __forceinline__ R update_un(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, R z, R xo, R &u,
+                                       double &pri) {
     if (MODE != F_PROX) {
         const R al = a.alpha_e ? a.alpha_e[e] : a.alpha_u;
-        const R xo = io.xin[e];
         const R d = xo - z;
-        const double dd = (double)xo - (double)z;
-        pri += dd * dd;
+        if (io.chk) {
+            const double dd = (double)xo - (double)z;
+            pri += dd * dd;
+        }
         u = u + al * d;
-        a.u[e] = u;
     }
     return z - u;
 }
 
-// m-update, then rho*m either scattered into the variable-major array
-// (canonical order) or parked in the chunk's shared-memory buffer at the
-// edge's slot-sorted position (fast order).
-template <typename R>
-__device__ __forceinline__ void edge_post(const SweepArgs<R> &a, const EdgeIO<R> &io, long long e, R x, R u) {
+// One scalar edge, start of phase F: returns n; u holds the updated u
+// (already stored when MODE != F_PROX).
+template <typename R, int MODE, bool FAST>
+__device__ __forceinline__ R edge_pre(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, R &u, unsigned &ix,
+                                      double &pri) {
+    const R z = edge_z<R, FAST>(a, io, e, ix);
+    u = a.u[e];
+    const R xo = MODE != F_PROX ? io.xin[e] : R(0);
+    const R n = update_un<R, MODE>(a, io, e, z, xo, u, pri);
+    if (MODE != F_PROX) a.u[e] = u;
+    return n;
+}
+
+// One scalar edge, end of phase F: x, m = x + u, rho*m to the z-reduction.
+template <typename R, bool FAST>
+__device__ __forceinline__ void edge_post(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, unsigned ix, R x, R u) {
     io.xout[e] = x;
     const R m = x + u;
     if (io.mout) io.mout[e] = m;
-    const R p = edge_rho(a, e) * m;
-    if (io.fast) io.pb[a.lpos[e]] = p;
-    else a.pvm[a.pos[e]] = p;
+    edge_put<R, FAST>(a, io, ix, edge_rho(a, e) * m);
 }
+
+// 6 consecutive values with three 2-element vector accesses (the pair
+// bucket is factor-major with an even base, so e0 = ebase + 6 f is even).
+template <typename T, typename V2>
+__device__ __forceinline__ void load6(const T *p, T *v) {
+    const V2 *q = reinterpret_cast<const V2 *>(p);
+    #pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const V2 t = q[i];
+        v[2 * i] = t.x;
+        v[2 * i + 1] = t.y;
+    }
+}
+template <typename T, typename V2>
+__device__ __forceinline__ void store6(T *p, const T *v) {
+    V2 *q = reinterpret_cast<V2 *>(p);
+    #pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        V2 t;
+        t.x = v[2 * i];
+        t.y = v[2 * i + 1];
+        q[i] = t;
+    }
+}
+template <typename R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
 
 // ---------------------------------------------------------------------------
 // per-type work items
 // ---------------------------------------------------------------------------
-template <typename R, int MODE>
+template <typename R, int MODE, bool FAST>
 __device__ __forceinline__ void item_pack_pair(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
-                                               long long f, double &pri) {
-    R n[6], u[6], rho[6];
-    long long e[6];
-    #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        e[k] = B.ebase + k * B.nf + f;
-        n[k] = edge_pre<R, MODE>(a, io, e[k], u[k], pri);
-        rho[k] = edge_rho(a, e[k]);
+                                               int f, double &pri) {
+    using V = typename Vec2<R>::T;
+    const int e0 = B.ebase + 6 * f;
+    R u[6], z[6], xo[6], rho[6], n[6];
+    unsigned ix[6];
+    load6<R, V>(a.u + e0, u);
+    if (MODE != F_PROX) load6<R, V>(io.xin + e0, xo);
+    if (FAST) {
+        load6<unsigned, uint2>(a.lidx + e0, ix);
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) z[k] = io.zl[ix[k] & 0xffffu];
+    } else {
+        int sv[6];
+        load6<int, int2>(a.svar + e0, sv);
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            z[k] = ldg_l2(io.zc + sv[k]);
+            ix[k] = (unsigned)(e0 + k);
+        }
     }
+    if (a.rho_e) load6<R, V>(a.rho_e + e0, rho);
+    else {
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) rho[k] = a.rho_u;
+    }
+    #pragma unroll
+    for (int k = 0; k < 6; ++k) n[k] = update_un<R, MODE>(a, io, e0 + k, z[k], xo[k], u[k], pri);
+    if (MODE != F_PROX) store6<R, V>(a.u + e0, u);
     if (MODE == F_U_ONLY) return;
     R x[6];
-    prox_pack_pair(n, rho, x);
+    if constexpr (sizeof(R) == 4) prox_pack_pair_f32(n, rho, a.rho_e == nullptr, x);
+    else prox_pack_pair(n, rho, x);
+    store6<R, V>(io.xout + e0, x);
+    R m[6];
     #pragma unroll
-    for (int k = 0; k < 6; ++k) edge_post(a, io, e[k], x[k], u[k]);
+    for (int k = 0; k < 6; ++k) m[k] = x[k] + u[k];
+    if (io.mout) store6<R, V>(io.mout + e0, m);
+    #pragma unroll
+    for (int k = 0; k < 6; ++k) edge_put<R, FAST>(a, io, ix[k], rho[k] * m[k]);
 }
 
+// The same, with u, x and the slot/position indices read from a bulk-copy
+// stage in shared memory (su, sx, si point at this pair's six entries).
 template <typename R, int MODE>
+__device__ __forceinline__ void item_pack_pair_staged(const SweepArgs<R> &a, const BucketDev<R> &B,
+                                                      const EdgeIO<R> &io, int f, const R *su, const R *sx,
+                                                      const unsigned *si, double &pri) {
+    using V = typename Vec2<R>::T;
+    const int e0 = B.ebase + 6 * f;
+    R u[6], z[6], xo[6], rho[6], n[6];
+    unsigned ix[6];
+    #pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        u[k] = su[k];
+        xo[k] = MODE != F_PROX ? sx[k] : R(0);
+        ix[k] = si[k];
+        z[k] = io.zl[ix[k] & 0xffffu];
+    }
+    if (a.rho_e) load6<R, V>(a.rho_e + e0, rho);
+    else {
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) rho[k] = a.rho_u;
+    }
+    #pragma unroll
+    for (int k = 0; k < 6; ++k) n[k] = update_un<R, MODE>(a, io, e0 + k, z[k], xo[k], u[k], pri);
+    if (MODE != F_PROX) store6<R, V>(a.u + e0, u);
+    if (MODE == F_U_ONLY) return;
+    R x[6];
+    if constexpr (sizeof(R) == 4) prox_pack_pair_f32(n, rho, a.rho_e == nullptr, x);
+    else prox_pack_pair(n, rho, x);
+    store6<R, V>(io.xout + e0, x);
+    R m[6];
+    #pragma unroll
+    for (int k = 0; k < 6; ++k) m[k] = x[k] + u[k];
+    if (io.mout) store6<R, V>(io.mout + e0, m);
+    #pragma unroll
+    for (int k = 0; k < 6; ++k) edge_put<R, true>(a, io, ix[k], rho[k] * m[k]);
+}
+
+// Bounded wait on a stage barrier; false (and the grid's error word set)
+// if the copy did not land within about a second.
+static __device__ __forceinline__ bool stage_wait(unsigned long long *bar, unsigned parity, Barrier *gb) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned spin = 0; spin < (1u << 26); ++spin) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spin & 255u) == 0u && global_ns() - t0 > 1000000000ull) break;
+    }
+    atomicExch(&gb->error, kETimeout);
+    return false;
+}
+
+template <typename R, int MODE, bool FAST>
 __device__ __forceinline__ void item_pack_wall(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
-                                               long long f, double &pri) {
+                                               int f, double &pri) {
     R n[3], u[3], rho[3];
-    long long e[3];
+    unsigned ix[3];
+    int e[3];
     #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        e[k] = B.ebase + k * B.nf + f;
-        n[k] = edge_pre<R, MODE>(a, io, e[k], u[k], pri);
+        e[k] = bedge(B, f, k);
+        n[k] = edge_pre<R, MODE, FAST>(a, io, e[k], u[k], ix[k], pri);
         rho[k] = edge_rho(a, e[k]);
     }
     if (MODE == F_U_ONLY) return;
     const R *p = B.prm;
-    const long long nf = B.nf;
+    const int nf = B.nf;
     R x[3];
     prox_pack_wall(n, rho, p[f], p[nf + f], p[2 * nf + f], p[3 * nf + f], x);
     #pragma unroll
-    for (int k = 0; k < 3; ++k) edge_post(a, io, e[k], x[k], u[k]);
+    for (int k = 0; k < 3; ++k) edge_post<R, FAST>(a, io, e[k], ix[k], x[k], u[k]);
 }
 
 // Hinge c max(0, 1 - y (w.x + b)) on (w in R^D, b): two passes over the
 // factor's edges (the first computes the margin, the second writes x).
-template <typename R, int MODE>
+template <typename R, int MODE, bool FAST>
 __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
-                                               long long f, double &pri) {
+                                               int f, double &pri) {
     const int D = B.arity - 1;
-    const long long nf = B.nf;
+    const int nf = B.nf;
     const R *p = B.prm;
     R dot = R(0), s = R(0), nb = R(0), rb = R(1);
     for (int j = 0; j < D; ++j) {
-        const long long e = B.ebase + j * nf + f;
+        const int e = bedge(B, f, j);
         R u;
-        const R n = edge_pre<R, MODE>(a, io, e, u, pri);
+        unsigned ix;
+        const R n = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
         const R xi = p[j * nf + f];
         dot += n * xi;
         s += (xi * xi) / edge_rho(a, e);
     }
     {
-        const long long e = B.ebase + (long long)D * nf + f;
+        const int e = bedge(B, f, D);
         R u;
-        nb = edge_pre<R, MODE>(a, io, e, u, pri);
+        unsigned ix;
+        nb = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
         rb = edge_rho(a, e);
     }
     if (MODE == F_U_ONLY) return;
     dot += nb;
     s += R(1) / rb;
-    const R y = p[(long long)D * nf + f];
-    const R c = p[(long long)(D + 1) * nf + f];
+    const R y = p[D * nf + f];
+    const R c = p[(D + 1) * nf + f];
     const R t = R(1) - y * dot;
     const bool active = t > R(0);
     R gy = R(0);
@@ -326,12 +537,13 @@ __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const Buck
         gy = gam * y;
     }
     for (int j = 0; j <= D; ++j) {
-        const long long e = B.ebase + j * nf + f;
+        const int e = bedge(B, f, j);
         const R u = a.u[e];
-        const R n = edge_z(a, io, e) - u;
+        unsigned ix;
+        const R n = edge_z<R, FAST>(a, io, e, ix) - u;
         R x = n;
         if (active) x = (j < D) ? n + (gy * p[j * nf + f]) / edge_rho(a, e) : n + gy / edge_rho(a, e);
-        edge_post(a, io, e, x, u);
+        edge_post<R, FAST>(a, io, e, ix, x, u);
     }
 }
 
@@ -339,13 +551,14 @@ __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const Buck
 // {x' = A x + B u}, precomputed per distinct (A, B, rho).  AC = compile-time
 // arity (n kept in registers), or 0 for any arity (n re-formed from u and z
 // for each output row).
-template <typename R, int MODE, int AC>
+template <typename R, int MODE, bool FAST, int AC>
 __device__ __forceinline__ void item_mpc_dyn(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
-                                             long long f, double &pri) {
+                                             int f, double &pri) {
     if constexpr (AC > 0) {
         R n[AC], u[AC];
+        unsigned ix[AC];
         #pragma unroll
-        for (int k = 0; k < AC; ++k) n[k] = edge_pre<R, MODE>(a, io, B.ebase + k * B.nf + f, u[k], pri);
+        for (int k = 0; k < AC; ++k) n[k] = edge_pre<R, MODE, FAST>(a, io, bedge(B, f, k), u[k], ix[k], pri);
         if (MODE == F_U_ONLY) return;
         const R *P = B.pmat + (long long)B.pidx[f] * AC * AC;
         #pragma unroll 2
@@ -353,37 +566,42 @@ __device__ __forceinline__ void item_mpc_dyn(const SweepArgs<R> &a, const Bucket
             R acc = R(0);
             #pragma unroll
             for (int j = 0; j < AC; ++j) acc += __ldg(P + i * AC + j) * n[j];
-            edge_post(a, io, B.ebase + i * B.nf + f, acc, u[i]);
+            edge_post<R, FAST>(a, io, bedge(B, f, i), ix[i], acc, u[i]);
         }
     } else {
         const int A = B.arity;
         for (int k = 0; k < A; ++k) {
             R u;
-            edge_pre<R, MODE>(a, io, B.ebase + k * B.nf + f, u, pri);
+            unsigned ix;
+            edge_pre<R, MODE, FAST>(a, io, bedge(B, f, k), u, ix, pri);
         }
         if (MODE == F_U_ONLY) return;
         const R *P = B.pmat + (long long)B.pidx[f] * A * A;
         for (int i = 0; i < A; ++i) {
             R acc = R(0);
+            unsigned ix;
             for (int j = 0; j < A; ++j) {
-                const long long e = B.ebase + j * B.nf + f;
-                acc += __ldg(P + i * A + j) * (edge_z(a, io, e) - a.u[e]);
+                const int e = bedge(B, f, j);
+                acc += __ldg(P + i * A + j) * (edge_z<R, FAST>(a, io, e, ix) - a.u[e]);
             }
-            const long long e = B.ebase + i * B.nf + f;
-            edge_post(a, io, e, acc, a.u[e]);
+            const int e = bedge(B, f, i);
+            edge_z<R, FAST>(a, io, e, ix);
+            edge_post<R, FAST>(a, io, e, ix, acc, a.u[e]);
         }
     }
 }
 
-// Elementwise types: one work item per scalar edge; li = k * nf + f.
-template <typename R, int MODE>
+// Elementwise types: one work item per scalar edge, edge-major storage
+// (li = k * nf + f).
+template <typename R, int MODE, bool FAST>
 __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
-                                                 long long li, double &pri) {
-    const long long e = B.ebase + li;
+                                                 int li, double &pri) {
+    const int e = B.ebase + li;
     R u;
-    const R n = edge_pre<R, MODE>(a, io, e, u, pri);
+    unsigned ix;
+    const R n = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
     if (MODE == F_U_ONLY) return;
-    const long long f = li % B.nf;
+    const int f = li % B.nf;
     const R rho = edge_rho(a, e);
     R x;
     switch (B.type) {
@@ -410,71 +628,141 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
         x = B.prm[li];
         break;
     }
-    edge_post(a, io, e, x, u);
+    edge_post<R, FAST>(a, io, e, ix, x, u);
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool FAST>
 __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
-                                                  long long li, double &pri) {
+                                                  int li, double &pri) {
     switch (B.type) {
-    case 0: item_pack_pair<R, MODE>(a, B, io, li, pri); break;
-    case 1: item_pack_wall<R, MODE>(a, B, io, li, pri); break;
-    case 4: item_svm_hinge<R, MODE>(a, B, io, li, pri); break;
+    case 0: item_pack_pair<R, MODE, FAST>(a, B, io, li, pri); break;
+    case 1: item_pack_wall<R, MODE, FAST>(a, B, io, li, pri); break;
+    case 4: item_svm_hinge<R, MODE, FAST>(a, B, io, li, pri); break;
     case 6:
-        if (B.arity == 28) item_mpc_dyn<R, MODE, 28>(a, B, io, li, pri);
-        else item_mpc_dyn<R, MODE, 0>(a, B, io, li, pri);
+        if (B.arity == 28) item_mpc_dyn<R, MODE, FAST, 28>(a, B, io, li, pri);
+        else item_mpc_dyn<R, MODE, FAST, 0>(a, B, io, li, pri);
         break;
-    default: item_elementwise<R, MODE>(a, B, io, li, pri); break;
+    default: item_elementwise<R, MODE, FAST>(a, B, io, li, pri); break;
     }
-}
-
-template <typename R, int MODE>
-__device__ __forceinline__ void process_item(const SweepArgs<R> &a, const EdgeIO<R> &io, long long it, double &pri) {
-    int b = 0;
-    while (b + 1 < a.nb && it >= a.bk[b + 1].item0) ++b;
-    process_in_bucket<R, MODE>(a, a.bk[b], io, it - a.bk[b].item0, pri);
 }
 
 // Canonical order: every work item on its own, rho*m scattered to the
 // variable-major array.  Fast order: CTAs walk their chunks; a chunk's
 // variables ("slots") get their z staged in shared memory, every edge's
 // rho*m lands in shared memory sorted by slot, and each slot's sum over the
-// chunk (edges in slot order, fixed shuffle tree) is written to the
-// variable-major partial array.  Both orders are deterministic.
+// chunk (edges in slot order) is written to the variable-major partial
+// array.  Both orders are deterministic.
 template <typename R, int MODE>
-__device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, double &pri) {
-    if (!io.fast) {
-        const long long stride = (long long)gridDim.x * blockDim.x;
-        for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < a.nitems_f; it += stride)
-            process_item<R, MODE>(a, io, it, pri);
+__device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, bool chk, double &pri) {
+    io.chk = chk ? 1 : 0;
+    if (a.zorder == 0) {
+        const int stride = gridDim.x * blockDim.x;
+        for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < a.nitems_f; it += stride) {
+            int b = 0;
+            while (b + 1 < a.nb && it >= a.bk[b + 1].item0) ++b;
+            process_in_bucket<R, MODE, false>(a, a.bk[b], io, it - a.bk[b].item0, pri);
+        }
         return;
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *pb = reinterpret_cast<R *>(smem_raw);
-    R *zl = pb + kChunkEdges;
+    constexpr ChunkSmem L = chunk_smem((int)sizeof(R));
+    R *pb = reinterpret_cast<R *>(smem_raw + L.pb);
+    R *zl = reinterpret_cast<R *>(smem_raw + L.zl);
+    int *lr_s = reinterpret_cast<int *>(smem_raw + L.lr);
+    int *pp_s = reinterpret_cast<int *>(smem_raw + L.pp);
+    unsigned long long *sbar = reinterpret_cast<unsigned long long *>(smem_raw + L.bar);
     io.pb = pb;
     io.zl = zl;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&sbar[0], 1);
+        mbar_init(&sbar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned par[2] = {0u, 0u};
+    bool staged_ok = true;
     for (int c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
         const ChunkDev ch = a.chunks[c];
-        for (int s = threadIdx.x; s < ch.nslots; s += blockDim.x) zl[s] = ldg_l2(io.zc + a.slot_var[ch.sbase + s]);
-        __syncthreads();
-        const BucketDev<R> &B = a.bk[ch.bucket];
-        for (int i = threadIdx.x; i < ch.nitems; i += blockDim.x)
-            process_in_bucket<R, MODE>(a, B, io, ch.f0 + i, pri);
-        __syncthreads();
-        if (MODE != F_U_ONLY) {
-            const int *lr = a.lrow + ch.lrbase;
-            for (int sl = warp; sl < ch.nslots; sl += nwarps) {
-                const int beg = lr[sl], end = lr[sl + 1];
-                R S = R(0);
-                for (int k = beg + lane; k < end; k += 32) S += pb[k];
-                #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
-                if (lane == 0) a.part[a.ppos[ch.sbase + sl]] = S;
+        const int *lr = a.lrow + ch.lrbase;
+        for (int s = threadIdx.x; s <= ch.nslots; s += blockDim.x) {
+            lr_s[s] = lr[s] + s;   // segment s starts after s pad elements
+            if (s < ch.nslots) {
+                zl[s] = ldg_l2(io.zc + a.slot_var[ch.sbase + s]);
+                pp_s[s] = a.ppos[ch.sbase + s];
             }
         }
         __syncthreads();
+        const BucketDev<R> &B = a.bk[ch.bucket];
+        const int f0 = (int)ch.f0;
+        if (B.type == 0) {
+            // disk pairs: double-buffered bulk copies of (u, x, index) for
+            // kStagePairs factors at a time
+            const int nst = (ch.nitems + kStagePairs - 1) / kStagePairs;
+            auto issue = [&](int st) {
+                const int fs = f0 + st * kStagePairs;
+                const int ns = min(kStagePairs, ch.nitems - st * kStagePairs);
+                unsigned char *buf = smem_raw + L.st + (st & 1) * L.stage_bytes;
+                const unsigned br = (unsigned)align16(6 * ns * (int)sizeof(R));
+                const unsigned bi = (unsigned)align16(6 * ns * 4);
+                const int e0 = B.ebase + 6 * fs;
+                unsigned long long *bar = &sbar[st & 1];
+                mbar_expect_tx(bar, br + (MODE != F_PROX ? br : 0u) + bi);
+                bulk_g2s(buf + L.stage_u, a.u + e0, br, bar);
+                if (MODE != F_PROX) bulk_g2s(buf + L.stage_x, io.xin + e0, br, bar);
+                bulk_g2s(buf + L.stage_i, a.lidx + e0, bi, bar);
+            };
+            if (threadIdx.x == 0) {
+                fence_proxy_async_shared();
+                issue(0);
+                if (nst > 1) issue(1);
+            }
+            for (int st = 0; st < nst; ++st) {
+                const int b = st & 1;
+                if (staged_ok) staged_ok = stage_wait(&sbar[b], par[b], a.bar);
+                par[b] ^= 1u;
+                const unsigned char *buf = smem_raw + L.st + b * L.stage_bytes;
+                const R *su = reinterpret_cast<const R *>(buf + L.stage_u);
+                const R *sx = reinterpret_cast<const R *>(buf + L.stage_x);
+                const unsigned *si = reinterpret_cast<const unsigned *>(buf + L.stage_i);
+                const int ns = min(kStagePairs, ch.nitems - st * kStagePairs);
+                if (staged_ok) {
+                    for (int i = threadIdx.x; i < ns; i += blockDim.x)
+                        item_pack_pair_staged<R, MODE>(a, B, io, f0 + st * kStagePairs + i, su + 6 * i, sx + 6 * i,
+                                                       si + 6 * i, pri);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0 && st + 2 < nst && staged_ok) {
+                    fence_proxy_async_shared();
+                    issue(st + 2);
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < ch.nitems; i += blockDim.x)
+                process_in_bucket<R, MODE, true>(a, B, io, f0 + i, pri);
+        }
+        __syncthreads();
+        if (MODE != F_U_ONLY) {
+            // one thread per slot, its segment in order (segments are padded
+            // by one element, so equal-length neighbours sit in different
+            // banks)
+            for (int sl = threadIdx.x; sl < ch.nslots; sl += blockDim.x) {
+                const int beg = lr_s[sl], end = lr_s[sl + 1] - 1;
+                R S = R(0);
+                for (int k = beg; k < end; ++k) S += pb[k];
+                a.part[pp_s[sl]] = S;
+            }
+        }
+        __syncthreads();
+    }
+    // u and x written here are read back by bulk copies (async proxy) in the
+    // next phase F
+    fence_proxy_async_global();
+    __syncthreads();
+    // after a stage wait ran out a copy may still be in flight: the barriers
+    // are then left alone (the grid-wide error word ends the launch)
+    if (threadIdx.x == 0 && staged_ok) {
+        mbar_inval(&sbar[0]);
+        mbar_inval(&sbar[1]);
     }
 }
 
@@ -617,7 +905,7 @@ __device__ __forceinline__ EdgeIO<R> make_io(const SweepArgs<R> &a, int xp, int 
     io.zc = a.z[zp];
     io.zl = nullptr;
     io.pb = nullptr;
-    io.fast = a.zorder;
+    io.chk = 1;
     return io;
 }
 
@@ -635,8 +923,8 @@ __global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> 
         const bool chk = pend && ((a.k0 + it - 1) % a.check_every == 0);
         const EdgeIO<R> io = make_io(a, xp, zp);
         double pri = 0.0;
-        if (pend) phase_f<R, F_U_PROX>(a, io, pri);
-        else phase_f<R, F_PROX>(a, io, pri);
+        if (pend) phase_f<R, F_U_PROX>(a, io, chk, pri);
+        else phase_f<R, F_PROX>(a, io, false, pri);
         if (chk) {
             const double s = block_sum(pri);
             if (threadIdx.x == 0) a.res_pri[blockIdx.x] = s;
@@ -665,7 +953,7 @@ __global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> 
     // u-update of the last iteration, and its residual check
     EdgeIO<R> io = make_io(a, xp, zp);
     double pri = 0.0;
-    phase_f<R, F_U_ONLY>(a, io, pri);
+    phase_f<R, F_U_ONLY>(a, io, true, pri);
     const double s = block_sum(pri);
     if (threadIdx.x == 0) a.res_pri[blockIdx.x] = s;
     if (!grid_barrier(a.bar, G, gen, a.timeout_ns, skip)) return;
@@ -682,7 +970,7 @@ __global__ void __launch_bounds__(256) k_phase_f(const SweepArgs<R> a, int xp, i
     if (*(volatile int *)&a.ctl->done) return;
     const EdgeIO<R> io = make_io(a, xp, zp);
     double pri = 0.0;
-    phase_f<R, MODE>(a, io, pri);
+    phase_f<R, MODE>(a, io, chk != 0, pri);
     if (chk) {
         const double s = block_sum(pri);
         if (threadIdx.x == 0) a.res_pri[blockIdx.x] = s;

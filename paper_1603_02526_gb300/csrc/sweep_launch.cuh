@@ -8,9 +8,13 @@ namespace fga {
 
 template <typename R>
 static cudaError_t allow_smem(int smem) {
-    // kernels that take the chunk buffers may need more than the default 48 KB
+    // kernels that take the chunk buffers may need more than the default 48 KB;
+    // ask for the largest shared-memory carveout so several CTAs fit per SM
     cudaError_t e = cudaFuncSetAttribute((const void *)k_sweep_persistent<R>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void *)k_sweep_persistent<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -130,6 +130,12 @@ class FactorGraph:
             check(rc, "fga_iterate")
         return out
 
+    def fga_launch_info(self):
+        info = (ctypes.c_int64 * 6)()
+        check(self._lib.fga_launch_info(self._g, info, 6), "fga_launch_info")
+        return dict(grid=info[0], block=info[1], smem=info[2], blocks_per_sm=info[3], chunks=info[4],
+                    buckets=info[5])
+
     def fga_residuals(self):
         a, b = ctypes.c_double(), ctypes.c_double()
         check(self._lib.fga_residuals(self._g, ctypes.byref(a), ctypes.byref(b)), "fga_residuals")
