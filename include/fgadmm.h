@@ -209,6 +209,95 @@ int fga_read_edge_state(fga_graph *g, int32_t which, double *out, int64_t n);
 /* Frees every host and device resource of the graph. */
 int fga_destroy(fga_graph *g);
 
+/* ==========================================================================
+ * Batched ragged MPC (Sec. V-B, Appendix B): many independent instances of
+ *   minimise 1/2 sum_{t<T} (x_t' Q x_t + u_t' R u_t) + 1/2 x_T' Q x_T
+ *   s.t. x_{t+1} = A x_t + B u_t, x_0 fixed, lo <= u_t <= hi (lo = -umax)
+ * each written as the factor graph FIX(x_0) | DYN(x_t,u_t,x_{t+1}) t<T |
+ * QUAD(x_t,u_t) t<T | QUAD(x_T) | BOX(u_t) t<T (creation order; z per
+ * instance = x_0, u_0, x_1, u_1, ..., u_{T-1}, x_T), solved by Algorithm 2
+ * with uniform rho, alpha, all instances in one persistent launch (one CTA
+ * per instance at a time, state in shared memory), optionally replayed from
+ * a CUDA graph.  Per instance: E = 2 nx + 3 (nx + nu) T scalar edges and
+ * V = (nx + nu) T + nx scalar variables; instance i's z starts at the sum
+ * of the V of instances 0..i-1, its u at the sum of their E.
+ * ========================================================================== */
+typedef struct fga_mpc_batch fga_mpc_batch; /* opaque, library-owned */
+
+/* n_inst instances of horizons T[i] (1..1e5) on n_sys systems: A (n_sys x
+ * nx x nx, row-major), B (n_sys x nx x nu), q (n_sys x nx, diagonal of Q),
+ * r (n_sys x nu, diagonal of R).  sys_of_inst[i] picks instance i's system
+ * (NULL: all use system 0 when n_sys == 1, instance i uses system i when
+ * n_sys == n_inst).  2 nx + nu <= 64.  stream NULL: the batch creates its
+ * own stream (needed to capture CUDA graphs).  Host pointers. */
+int fga_mpc_batch_create(fga_mpc_batch **out, int32_t precision, int32_t device, void *stream, int32_t n_inst,
+                         const int32_t *T, int32_t nx, int32_t nu, int32_t n_sys, const int32_t *sys_of_inst,
+                         const double *A, const double *B, const double *q, const double *r, double umax,
+                         double rho, double alpha);
+
+/* Initial states x_0 of all instances (n_inst x nx).  Host or device. */
+int fga_mpc_batch_set_x0(fga_mpc_batch *b, const double *x0);
+
+/* Start point: z (all instances, concatenated; NULL = 0) and per-edge u
+ * (concatenated, creation order; NULL = 0); x = 0.  Host or device. */
+int fga_mpc_batch_init(fga_mpc_batch *b, const double *z0, const double *u0);
+
+/* Warm start from a prediction (device pointer, FP32, one row of length
+ * >= 2 (nx+nu) Tmax per instance, stride ld): first T(nx+nu) values are
+ * (x_{t+1}, u_t) for t = 0..T-1, the next T(nx+nu) are (lambda_t, mu_t),
+ * the multipliers of the dynamics and of the input box.  Sets z from the
+ * trajectory and every edge's u from the fixed-point relation
+ * u = -(1/rho) (sub)gradient of its factor at z (the paper has no warm
+ * start; this is the start point a learned model supplies). */
+int fga_mpc_batch_warm_start(fga_mpc_batch *b, const float *pred, int64_t ld);
+
+/* Inverse of the warm-start map on the current state: writes, per
+ * instance, (x_{t+1}, u_t) and (lambda_t, mu_t) in the layout above (device
+ * pointer, FP32, stride ld) -- training targets for the learned model. */
+int fga_mpc_batch_targets(fga_mpc_batch *b, float *out, int64_t ld);
+
+typedef struct {
+    int64_t max_iters;          /* budget per instance                      */
+    double tol_pri, tol_dual;   /* RMS residual tolerances per instance     */
+    int32_t check_every;        /* 0 = autotuned value (default 1)          */
+    int32_t threads;            /* CTA size 64/128/256; 0 = autotuned (128) */
+    int32_t use_graph;          /* 1 = launch from a cached CUDA graph      */
+    int32_t reserved;
+} fga_mpc_opts;
+
+typedef struct {
+    int64_t total_iters;        /* sum over instances                       */
+    int64_t max_inst_iters;
+    int32_t n_converged, n_budget, n_nonfinite;
+    float ms;                   /* device time of the solve (CUDA events)   */
+    int32_t threads, check_every;
+} fga_mpc_result;
+
+/* Solves every instance from the current start point; each instance stops
+ * at the first checked iteration whose residuals meet both tolerances
+ * (status 0) or at the budget (FGA_EBUDGET).  Synchronises the stream. */
+int fga_mpc_batch_solve(fga_mpc_batch *b, const fga_mpc_opts *opts, fga_mpc_result *res);
+
+/* Readout (host pointers, any may be NULL): z (FP64, concatenated), u (FP64,
+ * concatenated, creation order), per-instance iterations, status, RMS
+ * residuals. */
+int fga_mpc_batch_read(fga_mpc_batch *b, double *z, double *u, int64_t *iters, int32_t *status, double *r_pri,
+                       double *r_dual);
+
+/* info[0] instances, [1] total edges, [2] total scalar variables, [3] longest
+ * horizon, [4] tuned CTA size, [5] tuned check interval.  n >= 6. */
+int fga_mpc_batch_info(const fga_mpc_batch *b, int64_t *info, int32_t n);
+
+/* Autotuner: times CTA sizes {64,128,256} x check intervals {1,2,5,10} on
+ * the batch from its current start point (which it restores) and keeps the
+ * fastest for later solves.  cache_path (may be NULL): a text file of
+ * previous results keyed by GPU, precision and problem shape; a hit skips
+ * the timing, a miss appends the result. */
+int fga_mpc_batch_autotune(fga_mpc_batch *b, const char *cache_path, int64_t max_iters, double tol,
+                           int32_t *threads_out, int32_t *check_every_out);
+
+int fga_mpc_batch_destroy(fga_mpc_batch *b);
+
 /* Message describing the last failure on this thread ("" if none). */
 const char *fga_last_error(void);
 

@@ -44,6 +44,18 @@ class fga_iter_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class fga_mpc_opts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int64), ("tol_pri", ctypes.c_double), ("tol_dual", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("threads", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class fga_mpc_result(ctypes.Structure):
+    _fields_ = [("total_iters", ctypes.c_int64), ("max_inst_iters", ctypes.c_int64),
+                ("n_converged", ctypes.c_int32), ("n_budget", ctypes.c_int32), ("n_nonfinite", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("threads", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+
+
 class fga_iter_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("r_pri", ctypes.c_double), ("r_dual", ctypes.c_double),
                 ("status", ctypes.c_int32), ("ms", ctypes.c_float)]
@@ -72,6 +84,17 @@ def _declare(lib):
         "fga_read_z": [P, P, i64],
         "fga_read_edge_state": [P, i32, P, i64],
         "fga_destroy": [P],
+        "fga_mpc_batch_create": [PP, i32, i32, P, i32, P, i32, i32, i32, P, P, P, P, P, dbl, dbl, dbl],
+        "fga_mpc_batch_set_x0": [P, P],
+        "fga_mpc_batch_init": [P, P, P],
+        "fga_mpc_batch_warm_start": [P, P, i64],
+        "fga_mpc_batch_targets": [P, P, i64],
+        "fga_mpc_batch_solve": [P, ctypes.POINTER(fga_mpc_opts), ctypes.POINTER(fga_mpc_result)],
+        "fga_mpc_batch_read": [P, P, P, P, P, P, P],
+        "fga_mpc_batch_info": [P, pi64, i32],
+        "fga_mpc_batch_autotune": [P, ctypes.c_char_p, i64, dbl, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32)],
+        "fga_mpc_batch_destroy": [P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -81,16 +104,6 @@ def _declare(lib):
     lib.fga_last_error.argtypes = []
     lib.fga_version.restype = ctypes.c_char_p
     lib.fga_version.argtypes = []
-    _declare_extra(lib)
-
-
-def _declare_extra(lib):
-    """Entry points added by later parts of the library (batched MPC, MLP)."""
-    try:
-        from . import _lib_extra
-    except ImportError:
-        return
-    _lib_extra.declare(lib)
 
 
 def load():

@@ -1,0 +1,177 @@
+"""GPU parity of the batched ragged MPC solver against the FP64 oracle,
+which solves every instance as a general factor graph (Sec. V-B graph,
+Appendix B operators).  The batch applies a precomputed projector for the
+dynamics while the oracle solves a Cholesky system per call, so FP64
+agreement is to rounding (1e-9 relative with the floor), not bit for bit."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import from_problem as oracle_from_problem
+from oracle.oracle import EDGE_U
+from paper_1603_02526_gb300 import inputs
+from paper_1603_02526_gb300.mpc import MpcBatch, batch_from_inputs
+from tests.helpers import rel_close_floor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1603_02526_gb300 import build
+    build.build()
+
+
+def _oracle_instance(d, i, iters, tol=0.0, check_every=1):
+    s = 0 if d["A"].shape[0] == 1 else i
+    p = inputs.mpc_problem(d["A"][s], d["B"][s], d["q"][s], d["r"][s], d["x0"][i], int(d["T"][i]), umax=d["umax"])
+    g = oracle_from_problem(p)
+    r = g.iterate(iters, tol, tol, check_every)
+    return g, r
+
+
+@pytest.mark.parametrize("precision,rtol", [("f64", 1e-9), ("f32", None)])
+def test_batch_matches_oracle_fixed_iterations(precision, rtol):
+    d = inputs.mpc_batch_inputs(12, seed=4100, tmin=3, tmax=20)
+    b = batch_from_inputs(d, precision)
+    b.fga_mpc_batch_solve(300, tol=0.0, check_every=1, use_graph=False)
+    out = b.fga_mpc_batch_read()
+    assert np.all(out["iters"] == 300)
+    for i in range(b.n):
+        g, r = _oracle_instance(d, i, 300)
+        zg, ug = b.instance_z(out["z"], i), b.instance_u(out["u"], i)
+        if precision == "f64":
+            ok, emax, _ = rel_close_floor(zg, g.z(), rtol)
+            assert ok, (i, emax)
+            ok, emax, _ = rel_close_floor(ug, g.edge(EDGE_U), rtol)
+            assert ok, (i, emax)
+        else:
+            # FP32: contractive convex iteration; errors stay at a few
+            # hundred ulps of the state's scale
+            S = max(1.0, np.abs(g.z()).max())
+            assert np.abs(zg - g.z()).max() <= 2e-5 * S, i
+            assert np.abs(ug - g.edge(EDGE_U)).max() <= 2e-5 * S, i
+        np.testing.assert_allclose([out["r_pri"][i], out["r_dual"][i]], [r["r_pri"], r["r_dual"]],
+                                   rtol=1e-6 if precision == "f64" else 5e-2)
+
+
+def test_per_instance_stop_rule():
+    d = inputs.mpc_batch_inputs(10, seed=4200, tmin=5, tmax=15)
+    b = batch_from_inputs(d, "f64")
+    res = b.fga_mpc_batch_solve(20000, tol=1e-6, check_every=1, use_graph=False)
+    out = b.fga_mpc_batch_read()
+    assert res["n_converged"] == b.n
+    for i in range(b.n):
+        g, r = _oracle_instance(d, i, 20000, tol=1e-6)
+        assert out["iters"][i] == r["iters"], (i, out["iters"][i], r["iters"])
+        ok, emax, _ = rel_close_floor(b.instance_z(out["z"], i), g.z(), 1e-8)
+        assert ok, (i, emax)
+
+
+def test_inactive_box_is_lqr():
+    from tests.test_oracle_alg import _lqr, _mpc_split
+    d = inputs.mpc_batch_inputs(4, seed=4300, T_fixed=12, umax=1e6)
+    b = batch_from_inputs(d, "f64")
+    b.fga_mpc_batch_solve(100000, tol=1e-11, check_every=10, use_graph=False)
+    out = b.fga_mpc_batch_read()
+    for i in range(b.n):
+        xs, us = _mpc_split(b.instance_z(out["z"], i), 12, 4, 12)
+        xl, ul = _lqr(d["A"][i], d["B"][i], d["q"][i], d["r"][i], d["x0"][i], 12)
+        np.testing.assert_allclose(us, ul, atol=1e-7)
+        np.testing.assert_allclose(xs, xl, atol=1e-7)
+
+
+def test_graph_launch_equals_direct_and_is_deterministic():
+    d = inputs.mpc_batch_inputs(64, seed=4400)
+    outs = []
+    for use_graph in (False, True, True):
+        b = batch_from_inputs(d, "f32")
+        b.fga_mpc_batch_solve(5000, tol=1e-4, check_every=5, threads=128, use_graph=use_graph)
+        outs.append(b.fga_mpc_batch_read())
+    for o in outs[1:]:
+        assert np.array_equal(o["z"], outs[0]["z"]) and np.array_equal(o["iters"], outs[0]["iters"])
+
+
+def test_graph_replay_on_same_batch():
+    """A cached graph replays correctly after a re-initialisation."""
+    d = inputs.mpc_batch_inputs(32, seed=4450)
+    b = batch_from_inputs(d, "f32")
+    r1 = b.fga_mpc_batch_solve(3000, tol=1e-4, check_every=2, use_graph=True)
+    z1 = b.fga_mpc_batch_read()["z"]
+    b.fga_mpc_batch_init()
+    r2 = b.fga_mpc_batch_solve(3000, tol=1e-4, check_every=2, use_graph=True)
+    assert np.array_equal(z1, b.fga_mpc_batch_read()["z"]) and r1["total_iters"] == r2["total_iters"]
+
+
+def test_warm_start_from_exact_multipliers():
+    """Targets extracted from a converged solve, fed back through the warm
+    start map, restart the solver at (nearly) its fixed point."""
+    torch = pytest.importorskip("torch")
+    d = inputs.mpc_batch_inputs(16, seed=4500, T_fixed=30, shared_system=True)
+    b = batch_from_inputs(d, "f64")
+    cold = b.fga_mpc_batch_solve(50000, tol=1e-9, check_every=1, use_graph=False)
+    assert cold["n_converged"] == b.n
+    ld = 2 * 16 * 30
+    tgt = torch.zeros((b.n, ld), dtype=torch.float32, device="cuda")
+    b.fga_mpc_batch_targets(tgt, ld)
+    b2 = batch_from_inputs(d, "f64")
+    b2.fga_mpc_batch_warm_start(tgt, ld)
+    warm = b2.fga_mpc_batch_solve(50000, tol=1e-4, check_every=1, use_graph=False)
+    out = b2.fga_mpc_batch_read()
+    assert warm["n_converged"] == b.n
+    assert out["iters"].max() <= 20, out["iters"]
+    b3 = batch_from_inputs(d, "f64")
+    cold4 = b3.fga_mpc_batch_solve(50000, tol=1e-4, check_every=1, use_graph=False)
+    assert warm["total_iters"] * 5 < cold4["total_iters"]
+
+
+def test_autotune_and_cache(tmp_path):
+    d = inputs.mpc_batch_inputs(128, seed=4600)
+    b = batch_from_inputs(d, "f32")
+    cache = tmp_path / "mpc_tune.txt"
+    th, ce = b.fga_mpc_batch_autotune(2000, 1e-4, cache)
+    assert th in (64, 128, 256) and ce in (1, 2, 5, 10)
+    assert cache.exists() and cache.read_text().strip()
+    b2 = batch_from_inputs(d, "f32")
+    assert b2.fga_mpc_batch_autotune(2000, 1e-4, cache) == (th, ce)     # cache hit
+    info = b2.fga_mpc_batch_info()
+    assert (info["threads"], info["check_every"]) == (th, ce)
+    r = b2.fga_mpc_batch_solve(2000, tol=1e-4)
+    assert (r["threads"], r["check_every"]) == (th, ce)
+
+
+def test_full_batch_4096_sampled_against_oracle():
+    """The benchmark batch (4096 instances, horizons 10..50, FP32, one CUDA
+    graph launch) to residual 1e-4; eight sampled instances re-solved by the
+    oracle to the same rule: same state to 1e-3 of its scale and objective
+    within 1e-3 relative."""
+    d = inputs.mpc_batch_inputs(4096, seed=4000)
+    b = batch_from_inputs(d, "f32")
+    res = b.fga_mpc_batch_solve(20000, tol=1e-4, check_every=1, use_graph=True)
+    out = b.fga_mpc_batch_read()
+    assert res["n_nonfinite"] == 0
+    assert res["n_converged"] >= 0.99 * b.n
+    rng = np.random.default_rng(0)
+    for i in rng.choice(b.n, 8, replace=False):
+        if out["status"][i] != 0:
+            continue
+        g, r = _oracle_instance(d, i, 20000, tol=1e-4)
+        zg = b.instance_z(out["z"], i)
+        zo = g.z()
+        S = max(1.0, np.abs(zo).max())
+        assert np.abs(zg - zo).max() <= 1e-3 * S, i
+        T = int(d["T"][i])
+        fo, fg = _mpc_cost(zo, d, i, T), _mpc_cost(zg, d, i, T)
+        assert abs(fg - fo) <= 1e-3 * max(1.0, abs(fo)), (i, fg, fo)
+
+
+def _mpc_cost(z, d, i, T, nx=12, nu=4):
+    q, r = d["q"][i], d["r"][i]
+    c = 0.0
+    for t in range(T):
+        xt = z[t * (nx + nu): t * (nx + nu) + nx]
+        ut = z[t * (nx + nu) + nx: (t + 1) * (nx + nu)]
+        c += 0.5 * (np.sum(q * xt * xt) + np.sum(r * ut * ut))
+    xT = z[T * (nx + nu):]
+    return c + 0.5 * np.sum(q * xT * xT)
