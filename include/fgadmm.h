@@ -298,6 +298,38 @@ int fga_mpc_batch_autotune(fga_mpc_batch *b, const char *cache_path, int64_t max
 
 int fga_mpc_batch_destroy(fga_mpc_batch *b);
 
+/* ==========================================================================
+ * Learned warm start: a ReLU MLP in -> h1 -> h2 -> out, BF16 weights and
+ * activations on tensor cores with FP32 accumulation, FP32 master weights
+ * and Adam (beta 0.9, 0.999, eps 1e-8), MSE loss on standardised targets.
+ * Not in the paper; it supplies fga_mpc_batch_warm_start's prediction.
+ * Parameters are packed as W1 (h1 x in, row-major), b1, W2 (h2 x h1), b2,
+ * W3 (out x h2), b3.  h1, h2, out and every batch: multiples of 8.
+ * ========================================================================== */
+typedef struct fga_mlp fga_mlp; /* opaque, library-owned */
+
+/* He-initialised (seeded splitmix64 + Box-Muller) network; buffers for up
+ * to max_batch rows. */
+int fga_mlp_create(fga_mlp **out, int32_t in, int32_t h1, int32_t h2, int32_t out_dim, int32_t max_batch,
+                   uint64_t seed, int32_t device, void *stream);
+int fga_mlp_num_params(const fga_mlp *m, int64_t *n);
+/* FP32 master weights from / to host memory (packed order above). */
+int fga_mlp_set_params(fga_mlp *m, const float *params, int64_t n);
+int fga_mlp_get_params(fga_mlp *m, float *params, int64_t n);
+/* Per-output mean and standard deviation of Y (device, rows x out FP32);
+ * Y is standardised in place, and fga_mlp_forward de-standardises. */
+int fga_mlp_fit_normalization(fga_mlp *m, float *Y, int64_t rows);
+int fga_mlp_get_normalization(fga_mlp *m, float *mean, float *stdv);
+/* Loss (mean squared error against standardised targets Y) and the
+ * gradient of every parameter, into host `grads` (packed order).  X, Y:
+ * device, FP32, batch x in / batch x out. */
+int fga_mlp_gradients(fga_mlp *m, const float *X, const float *Y, int32_t batch, float *grads, double *loss);
+/* One Adam step on a minibatch (device X, Y); loss may be NULL (no sync). */
+int fga_mlp_train_step(fga_mlp *m, const float *X, const float *Y, int32_t batch, float lr, double *loss);
+/* Prediction in target units (de-standardised), device X and Y. */
+int fga_mlp_forward(fga_mlp *m, const float *X, float *Y, int32_t batch);
+int fga_mlp_destroy(fga_mlp *m);
+
 /* Message describing the last failure on this thread ("" if none). */
 const char *fga_last_error(void);
 

@@ -95,6 +95,16 @@ def _declare(lib):
         "fga_mpc_batch_autotune": [P, ctypes.c_char_p, i64, dbl, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_int32)],
         "fga_mpc_batch_destroy": [P],
+        "fga_mlp_create": [PP, i32, i32, i32, i32, i32, ctypes.c_uint64, i32, P],
+        "fga_mlp_num_params": [P, pi64],
+        "fga_mlp_set_params": [P, P, i64],
+        "fga_mlp_get_params": [P, P, i64],
+        "fga_mlp_fit_normalization": [P, P, i64],
+        "fga_mlp_get_normalization": [P, P, P],
+        "fga_mlp_gradients": [P, P, P, i32, P, pdbl],
+        "fga_mlp_train_step": [P, P, P, i32, ctypes.c_float, pdbl],
+        "fga_mlp_forward": [P, P, P, i32],
+        "fga_mlp_destroy": [P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

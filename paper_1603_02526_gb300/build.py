@@ -39,6 +39,7 @@ def _units():
         ("mlp.cu", nv),
         ("fga_graph.cpp", None),
         ("fga_batch.cpp", None),
+        ("fga_mlp.cpp", None),
     ]
     return [(s, f) for s, f in units if os.path.exists(os.path.join(CSRC, s))]
 
