@@ -230,6 +230,16 @@ def mpc_batch_inputs(n_inst, seed=4000, nx=12, nu=4, tmin=10, tmax=50, shared_sy
                 shared_system=bool(shared_system))
 
 
+def mpc_warmstart_inputs(n_inst, system_seed=5000, x0_seed=5001, T=30, nx=12, nu=4, umax=1.0):
+    """Learned-warm-start workload: ONE fixed system of the MPC family (drawn
+    with system_seed) and n_inst initial states x0 ~ N(0, I) (x0_seed), all
+    with horizon T.  Training and evaluation sets use different x0 seeds."""
+    A, B, q, r = mpc_system(nx, nu, np.random.default_rng(system_seed))
+    x0 = np.random.default_rng(x0_seed).standard_normal((n_inst, nx))
+    return dict(T=np.full(n_inst, T, dtype=np.int32), A=A[None], B=B[None], q=q[None], r=r[None], x0=x0,
+                nx=nx, nu=nu, umax=float(umax), shared_system=True)
+
+
 def mpc_problem(A, B, q, r, x0, T, umax=1.0, rho=1.0, alpha=1.0):
     """One MPC instance as a general factor graph.  Variables in creation
     order: x_0, u_0, x_1, u_1, ..., u_{T-1}, x_T.  Factors: FIX(x_0);
