@@ -472,7 +472,10 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         for (int64_t f = 0; f < nf; ++f) {
             const FactorBatch &b = g->batches[bk.members[f].first];
             const double *p = b.param(bk.members[f].second);
-            for (int j = 0; j < bk.np; ++j) prm[(size_t)j * nf + f] = (R)p[j];
+            // hinge parameters factor-major (a warp reads one factor's data
+            // point contiguously); every other type edge-major
+            for (int j = 0; j < bk.np; ++j)
+                prm[bk.type == FGA_SVM_HINGE ? (size_t)f * bk.np + j : (size_t)j * nf + f] = (R)p[j];
         }
         auto pb = std::make_unique<DevBuf>();
         if ((rc = upload_vec(*pb, prm))) return rc;
@@ -703,7 +706,8 @@ extern "C" int fga_finalize(fga_graph *g) {
             nb.np = b.np;
             nb.arity = b.arity;
             nb.per_edge = is_per_edge(b.type);
-            nb.aos = b.type == FGA_PACK_PAIR || b.type == FGA_PACK_WALL || b.type == FGA_MPC_DYN;
+            nb.aos = b.type == FGA_PACK_PAIR || b.type == FGA_PACK_WALL || b.type == FGA_MPC_DYN ||
+                     b.type == FGA_SVM_HINGE;
             g->buckets.push_back(nb);
             found = (int)g->buckets.size() - 1;
         }

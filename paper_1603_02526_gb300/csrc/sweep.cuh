@@ -498,21 +498,22 @@ __device__ __forceinline__ void item_pack_wall(const SweepArgs<R> &a, const Buck
     for (int k = 0; k < 3; ++k) edge_post<R, FAST>(a, io, e[k], ix[k], x[k], u[k]);
 }
 
-// Hinge c max(0, 1 - y (w.x + b)) on (w in R^D, b): two passes over the
-// factor's edges (the first computes the margin, the second writes x).
+// Hinge c max(0, 1 - y (w.x + b)) on (w in R^D, b), one thread per factor:
+// two passes over the factor's edges (the first computes the margin in the
+// order of a serial loop, the second writes x).  Parameters factor-major:
+// p[f*(D+2) + j] = x_j, then y, c.
 template <typename R, int MODE, bool FAST>
 __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                int f, double &pri) {
     const int D = B.arity - 1;
-    const int nf = B.nf;
-    const R *p = B.prm;
+    const R *p = B.prm + (long long)f * (D + 2);
     R dot = R(0), s = R(0), nb = R(0), rb = R(1);
     for (int j = 0; j < D; ++j) {
         const int e = bedge(B, f, j);
         R u;
         unsigned ix;
         const R n = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
-        const R xi = p[j * nf + f];
+        const R xi = p[j];
         dot += n * xi;
         s += (xi * xi) / edge_rho(a, e);
     }
@@ -526,8 +527,8 @@ __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const Buck
     if (MODE == F_U_ONLY) return;
     dot += nb;
     s += R(1) / rb;
-    const R y = p[D * nf + f];
-    const R c = p[(D + 1) * nf + f];
+    const R y = p[D];
+    const R c = p[D + 1];
     const R t = R(1) - y * dot;
     const bool active = t > R(0);
     R gy = R(0);
@@ -542,8 +543,58 @@ __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const Buck
         unsigned ix;
         const R n = edge_z<R, FAST>(a, io, e, ix) - u;
         R x = n;
-        if (active) x = (j < D) ? n + (gy * p[j * nf + f]) / edge_rho(a, e) : n + gy / edge_rho(a, e);
+        if (active) x = (j < D) ? n + (gy * p[j]) / edge_rho(a, e) : n + gy / edge_rho(a, e);
         edge_post<R, FAST>(a, io, e, ix, x, u);
+    }
+}
+
+// The same operator with one warp per factor (fast order): lane l owns the
+// edges j = l, l + 32, ...; the margin and the weight sum are reduced with a
+// fixed shuffle tree; one pass, the factor's edges and data point read
+// contiguously (factor-major storage).
+template <typename R, int MODE>
+__device__ __forceinline__ void item_svm_hinge_warp(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
+                                                    int f, double &pri) {
+    constexpr int JMAX = 4;   // up to 128 edges per factor kept in registers
+    const int D = B.arity - 1;
+    const int lane = threadIdx.x & 31;
+    const R *p = B.prm + (long long)f * (D + 2);
+    const int e0 = B.ebase + f * B.arity;
+    R n[JMAX], u[JMAX], rho[JMAX], xi[JMAX];
+    unsigned ix[JMAX];
+    R dot = R(0), s = R(0);
+    #pragma unroll
+    for (int q = 0; q < JMAX; ++q) {
+        const int j = lane + 32 * q;
+        if (j > D) continue;
+        const int e = e0 + j;
+        n[q] = edge_pre<R, MODE, true>(a, io, e, u[q], ix[q], pri);
+        rho[q] = edge_rho(a, e);
+        xi[q] = j < D ? p[j] : R(1);
+        dot += n[q] * xi[q];
+        s += (xi[q] * xi[q]) / rho[q];
+    }
+    if (MODE == F_U_ONLY) return;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    const R y = p[D];
+    const R c = p[D + 1];
+    const R t = R(1) - y * dot;
+    R gy = R(0);
+    if (t > R(0)) {
+        R gam = t / s;
+        if (gam > c) gam = c;
+        gy = gam * y;
+    }
+    #pragma unroll
+    for (int q = 0; q < JMAX; ++q) {
+        const int j = lane + 32 * q;
+        if (j > D) continue;
+        const R x = n[q] + (gy * xi[q]) / rho[q];
+        edge_post<R, true>(a, io, e0 + j, ix[q], x, u[q]);
     }
 }
 
@@ -736,6 +787,9 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, boo
                     issue(st + 2);
                 }
             }
+        } else if (B.type == 4 && B.arity <= 128) {
+            const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+            for (int i = warp; i < ch.nitems; i += nwarps) item_svm_hinge_warp<R, MODE>(a, B, io, f0 + i, pri);
         } else {
             for (int i = threadIdx.x; i < ch.nitems; i += blockDim.x)
                 process_in_bucket<R, MODE, true>(a, B, io, f0 + i, pri);
