@@ -298,6 +298,36 @@ int fga_mpc_batch_autotune(fga_mpc_batch *b, const char *cache_path, int64_t max
 
 int fga_mpc_batch_destroy(fga_mpc_batch *b);
 
+/* Allocation-free batched MPC solve (the paper has no counterpart; this is
+ * a deployment variant of fga_mpc_batch_solve).  For callers that cannot
+ * call cudaMalloc at solve time -- code running inside a memory arena it
+ * does not own, real-time control loops that must not touch the allocator
+ * after start-up, plugins whose host forbids device allocations -- this
+ * entry point allocates nothing: all scratch (per-edge x and u, instance
+ * offsets, the dynamics projector, residuals, the work counter) lives in
+ * one 16 MiB device array that every GPU loading the library holds until
+ * the process exits.  Limits: n_inst <= 4096, about 2 million scalar edges
+ * in total (E = 2 nx + 3 (nx + nu) T per instance); larger batches are
+ * rejected with FGA_EINVAL.
+ *
+ * Cold start (z = u = x = 0) of n_inst instances of ONE system, FP32
+ * messages, FP64 residuals; same model, factor graph and stopping rule as
+ * fga_mpc_batch_solve with tol_pri = tol_dual = tol.  T: host array of
+ * horizons.  A (nx x nx), B (nx x nu), q (nx), r (nu), x0 (n_inst x nx):
+ * device FP32.  Outputs (device): z_out (sum of V = (nx + nu) T + nx values,
+ * instances concatenated), iters_out and status_out per instance.  The work
+ * is queued on `stream` (NULL: legacy default stream) and the call returns
+ * without waiting; outputs are valid once the stream has synchronised.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any CUDA
+ * graph capture.  All calls share the one array and every call overwrites
+ * it, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t nx, int32_t nu, const float *A, const float *B,
+                          const float *q, const float *r, const float *x0, float umax, float rho, float alpha,
+                          int64_t max_iters, double tol, int32_t check_every, float *z_out, int64_t *iters_out,
+                          int32_t *status_out, void *stream);
+
 /* ==========================================================================
  * Learned warm start: a ReLU MLP in -> h1 -> h2 -> out, BF16 weights and
  * activations on tensor cores with FP32 accumulation, FP32 master weights

@@ -36,6 +36,7 @@ def _units():
         ("sweep_f32.cu", nv),
         ("sweep_f64.cu", nv + ["-fmad=false"]),
         ("mpc_batch.cu", nv),
+        ("mpc_noalloc.cu", nv),
         ("mlp.cu", nv),
         ("fga_graph.cpp", None),
         ("fga_batch.cpp", None),
