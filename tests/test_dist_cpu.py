@@ -1,0 +1,55 @@
+"""The benchmark's multi-rank path on CPU (gloo, world size 2): every rank
+solves its own problem (replicas, no data-path collective); the timing is
+the maximum over ranks, and only rank 0 reports."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2",
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    bench._barrier(2)
+    m = bench._max_over_ranks(10.0 + 5.0 * rank, 2)
+    ws, rk, local = bench._dist()
+    q.put((rank, m, ws, rk, local))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [15.0, 15.0]
+    assert [(o[2], o[3], o[4]) for o in out] == [(2, 0, 0), (2, 1, 1)]
+
+
+def test_reference_arm_nonzero_rank_is_silent(capsys, monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        gpus, steps, warmup = 2, 1, 0
+    assert bench.run_reference(A()) == 0
+    assert capsys.readouterr().out == ""
