@@ -138,7 +138,7 @@ struct fga_graph {
     std::vector<std::unique_ptr<DevBuf>> bucket_bufs;
     int n_small = 0, n_witems = 0, n_hubs = 0;
     DevBuf chunks, slot_var, ppos, lrow, lidx, part, prow;
-    int nchunks = 0, smem = 0, bps = 0;
+    int nchunks = 0, smem = 0, bps = 0, kind = 0;
     bool uniform_rho = true, uniform_alpha = true;
     int grid = 1, blk = 256;
 
@@ -791,8 +791,11 @@ extern "C" int fga_finalize(fga_graph *g) {
     CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
     g->blk = g->block ? g->block : 256;
     g->smem = g->zorder == 1 ? chunk_smem((int)g->rsize()).total : 0;
-    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem)
-                                            : sweep_max_blocks_per_sm<double>(g->blk, g->smem);
+    g->kind = 1;   // the kernel without hinge / dynamics paths when the graph has neither
+    for (const Bucket &bk : g->buckets)
+        if (bk.type == FGA_SVM_HINGE || bk.type == FGA_MPC_DYN) g->kind = 0;
+    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem, g->kind)
+                                            : sweep_max_blocks_per_sm<double>(g->blk, g->smem, g->kind);
     if (bps < 1) return fail(FGA_ECUDA, "fga_finalize: the sweep kernel cannot be resident at %d threads", g->blk);
     g->bps = bps;
     const int64_t full = (int64_t)bps * dev_sms;
@@ -1026,13 +1029,14 @@ static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
     if (g->n_hubs) CUDA_TRY(cudaMemsetAsync(g->hub_ticket.p, 0, g->hub_ticket.bytes, s));
     CUDA_TRY(cudaEventRecord(g->ev0, s));
     if (o.fused) {
-        CUDA_TRY(sweep_persistent<R>(a, g->grid, g->blk, g->smem, s));
+        CUDA_TRY(sweep_persistent<R>(a, g->grid, g->blk, g->smem, g->kind, s));
     } else {
         int xp = g->xpar, zp = g->zpar;
         for (long long it = 1; it <= a.K; ++it) {
             const bool pend = it > 1;
             const bool chk = pend && ((a.k0 + it - 1) % a.check_every == 0);
-            CUDA_TRY(sweep_phase_f<R>(a, pend ? F_U_PROX : F_PROX, xp, zp, chk ? 1 : 0, g->grid, g->blk, g->smem, s));
+            const int mode = !pend ? F_PROX : chk ? F_U_PROX_CHK : F_U_PROX;
+            CUDA_TRY(sweep_phase_f<R>(a, mode, xp, zp, g->grid, g->blk, g->smem, g->kind, s));
             if (chk) CUDA_TRY(sweep_check<R>(a, it - 1, xp, zp, 0, g->grid, s));
             xp ^= 1;
             const bool chkz = ((a.k0 + it) % a.check_every == 0) || it == a.K;
@@ -1040,7 +1044,7 @@ static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
             zp ^= 1;
         }
         if (a.K > 0) {
-            CUDA_TRY(sweep_phase_f<R>(a, F_U_ONLY, xp, zp, 1, g->grid, g->blk, g->smem, s));
+            CUDA_TRY(sweep_phase_f<R>(a, F_U_ONLY, xp, zp, g->grid, g->blk, g->smem, g->kind, s));
             CUDA_TRY(sweep_check<R>(a, a.K, xp, zp, 1, g->grid, s));
         }
     }

@@ -43,8 +43,13 @@ inline __host__ __device__ constexpr ChunkSmem chunk_smem(int rsize) {
 
 // Phase-F modes: the x-update of one iteration, preceded (from the second
 // iteration of a call on) by the deferred u- and n-updates of the previous
-// iteration; or the u-update alone at the end of a call.
-enum FMode : int { F_PROX = 0, F_U_PROX = 1, F_U_ONLY = 2 };
+// iteration; or the u-update alone at the end of a call.  F_U_PROX_CHK is
+// F_U_PROX on a check iteration (it also sums the primal residual); the
+// check is a compile-time mode so that the FP64 residual arithmetic is not
+// issued, predicated off, on every edge of the other iterations.
+enum FMode : int { F_PROX = 0, F_U_PROX = 1, F_U_ONLY = 2, F_U_PROX_CHK = 3 };
+
+inline __host__ __device__ constexpr bool fmode_checks(int mode) { return mode == F_U_PROX_CHK || mode == F_U_ONLY; }
 
 // Grid-wide barrier state (device memory, zeroed before every launch).
 struct Barrier {
@@ -165,10 +170,11 @@ struct SweepArgs {
 
 // Launchers (sweep_f32.cu / sweep_f64.cu).  `smem` = dynamic shared memory
 // per CTA (the fast order's chunk buffers; 0 in canonical order).
+// `kind`: 0 = every factor type, 1 = no hinge / dynamics factors.
 template <typename R>
-cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, int smem, cudaStream_t s);
+cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, int smem, int kind, cudaStream_t s);
 template <typename R>
-cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block, int smem,
+cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int grid, int block, int smem, int kind,
                           cudaStream_t s);
 template <typename R>
 cudaError_t sweep_phase_z(const SweepArgs<R> &a, int zp, long long it, int chk, int grid, int block,
@@ -177,6 +183,6 @@ template <typename R>
 cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int zp, int final_check,
                         int grid_partials, cudaStream_t s);
 template <typename R>
-int sweep_max_blocks_per_sm(int block, int smem);
+int sweep_max_blocks_per_sm(int block, int smem, int kind);
 
 }  // namespace fga

@@ -289,7 +289,6 @@ struct EdgeIO {
     // (shared memory), addressed through lidx = slot | position << 16
     const R *zl;
     R *pb;
-    int chk;        // accumulate the primal residual (check iterations only)
 };
 
 template <typename R>
@@ -322,7 +321,7 @@ __device__ __forceinline__ R update_un(const SweepArgs<R> &a, const EdgeIO<R> &i
     if (MODE != F_PROX) {
         const R al = a.alpha_e ? a.alpha_e[e] : a.alpha_u;
         const R d = xo - z;
-        if (io.chk) {
+        if constexpr (fmode_checks(MODE)) {
             const double dd = (double)xo - (double)z;
             pri += dd * dd;
         }
@@ -682,19 +681,41 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
     edge_post<R, FAST>(a, io, e, ix, x, u);
 }
 
-template <typename R, int MODE, bool FAST>
+// KIND 0: every factor type; KIND 1: graphs without hinge and dynamics
+// factors (packing), compiled without those paths so that their register
+// demand does not limit the packing kernel.
+template <typename R, int MODE, bool FAST, int KIND>
 __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                   int li, double &pri) {
     switch (B.type) {
     case 0: item_pack_pair<R, MODE, FAST>(a, B, io, li, pri); break;
     case 1: item_pack_wall<R, MODE, FAST>(a, B, io, li, pri); break;
-    case 4: item_svm_hinge<R, MODE, FAST>(a, B, io, li, pri); break;
+    case 4:
+        if constexpr (KIND == 0) item_svm_hinge<R, MODE, FAST>(a, B, io, li, pri);
+        break;
     case 6:
-        if (B.arity == 28) item_mpc_dyn<R, MODE, FAST, 28>(a, B, io, li, pri);
-        else item_mpc_dyn<R, MODE, FAST, 0>(a, B, io, li, pri);
+        if constexpr (KIND == 0) {
+            if (B.arity == 28) item_mpc_dyn<R, MODE, FAST, 28>(a, B, io, li, pri);
+            else item_mpc_dyn<R, MODE, FAST, 0>(a, B, io, li, pri);
+        }
         break;
     default: item_elementwise<R, MODE, FAST>(a, B, io, li, pri); break;
     }
+}
+
+// Issues one stage of bulk copies (u, x when needed, index) for the disk
+// pairs [fs, fs + ns) into `buf`, completing on `bar`.
+template <typename R, int MODE>
+__device__ __forceinline__ void issue_pair_stage(const SweepArgs<R> &a, const EdgeIO<R> &io, const BucketDev<R> &B,
+                                                 const ChunkSmem &L, unsigned char *buf, unsigned long long *bar,
+                                                 int fs, int ns) {
+    const unsigned br = (unsigned)align16(6 * ns * (int)sizeof(R));
+    const unsigned bi = (unsigned)align16(6 * ns * 4);
+    const int e0 = B.ebase + 6 * fs;
+    mbar_expect_tx(bar, br + (MODE != F_PROX ? br : 0u) + bi);
+    bulk_g2s(buf + L.stage_u, a.u + e0, br, bar);
+    if (MODE != F_PROX) bulk_g2s(buf + L.stage_x, io.xin + e0, br, bar);
+    bulk_g2s(buf + L.stage_i, a.lidx + e0, bi, bar);
 }
 
 // Canonical order: every work item on its own, rho*m scattered to the
@@ -703,15 +724,14 @@ __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const B
 // rho*m lands in shared memory sorted by slot, and each slot's sum over the
 // chunk (edges in slot order) is written to the variable-major partial
 // array.  Both orders are deterministic.
-template <typename R, int MODE>
-__device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, bool chk, double &pri) {
-    io.chk = chk ? 1 : 0;
+template <typename R, int MODE, int KIND>
+__device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, double &pri) {
     if (a.zorder == 0) {
         const int stride = gridDim.x * blockDim.x;
         for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < a.nitems_f; it += stride) {
             int b = 0;
             while (b + 1 < a.nb && it >= a.bk[b + 1].item0) ++b;
-            process_in_bucket<R, MODE, false>(a, a.bk[b], io, it - a.bk[b].item0, pri);
+            process_in_bucket<R, MODE, false, KIND>(a, a.bk[b], io, it - a.bk[b].item0, pri);
         }
         return;
     }
@@ -730,7 +750,7 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, boo
         mbar_fence_init();
     }
     __syncthreads();
-    unsigned par[2] = {0u, 0u};
+    unsigned parity = 0u;   // bit b: phase of stage barrier b
     bool staged_ok = true;
     for (int c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
         const ChunkDev ch = a.chunks[c];
@@ -749,28 +769,17 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, boo
             // disk pairs: double-buffered bulk copies of (u, x, index) for
             // kStagePairs factors at a time
             const int nst = (ch.nitems + kStagePairs - 1) / kStagePairs;
-            auto issue = [&](int st) {
-                const int fs = f0 + st * kStagePairs;
-                const int ns = min(kStagePairs, ch.nitems - st * kStagePairs);
-                unsigned char *buf = smem_raw + L.st + (st & 1) * L.stage_bytes;
-                const unsigned br = (unsigned)align16(6 * ns * (int)sizeof(R));
-                const unsigned bi = (unsigned)align16(6 * ns * 4);
-                const int e0 = B.ebase + 6 * fs;
-                unsigned long long *bar = &sbar[st & 1];
-                mbar_expect_tx(bar, br + (MODE != F_PROX ? br : 0u) + bi);
-                bulk_g2s(buf + L.stage_u, a.u + e0, br, bar);
-                if (MODE != F_PROX) bulk_g2s(buf + L.stage_x, io.xin + e0, br, bar);
-                bulk_g2s(buf + L.stage_i, a.lidx + e0, bi, bar);
-            };
             if (threadIdx.x == 0) {
                 fence_proxy_async_shared();
-                issue(0);
-                if (nst > 1) issue(1);
+                issue_pair_stage<R, MODE>(a, io, B, L, smem_raw + L.st, &sbar[0], f0, min(kStagePairs, ch.nitems));
+                if (nst > 1)
+                    issue_pair_stage<R, MODE>(a, io, B, L, smem_raw + L.st + L.stage_bytes, &sbar[1],
+                                              f0 + kStagePairs, min(kStagePairs, ch.nitems - kStagePairs));
             }
             for (int st = 0; st < nst; ++st) {
                 const int b = st & 1;
-                if (staged_ok) staged_ok = stage_wait(&sbar[b], par[b], a.bar);
-                par[b] ^= 1u;
+                if (staged_ok) staged_ok = stage_wait(&sbar[b], (parity >> b) & 1u, a.bar);
+                parity ^= 1u << b;
                 const unsigned char *buf = smem_raw + L.st + b * L.stage_bytes;
                 const R *su = reinterpret_cast<const R *>(buf + L.stage_u);
                 const R *sx = reinterpret_cast<const R *>(buf + L.stage_x);
@@ -784,15 +793,17 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, boo
                 __syncthreads();
                 if (threadIdx.x == 0 && st + 2 < nst && staged_ok) {
                     fence_proxy_async_shared();
-                    issue(st + 2);
+                    issue_pair_stage<R, MODE>(a, io, B, L, smem_raw + L.st + b * L.stage_bytes, &sbar[b],
+                                              f0 + (st + 2) * kStagePairs,
+                                              min(kStagePairs, ch.nitems - (st + 2) * kStagePairs));
                 }
             }
-        } else if (B.type == 4 && B.arity <= 128) {
+        } else if (KIND == 0 && B.type == 4 && B.arity <= 128) {
             const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
             for (int i = warp; i < ch.nitems; i += nwarps) item_svm_hinge_warp<R, MODE>(a, B, io, f0 + i, pri);
         } else {
             for (int i = threadIdx.x; i < ch.nitems; i += blockDim.x)
-                process_in_bucket<R, MODE, true>(a, B, io, f0 + i, pri);
+                process_in_bucket<R, MODE, true, KIND>(a, B, io, f0 + i, pri);
         }
         __syncthreads();
         if (MODE != F_U_ONLY) {
@@ -823,21 +834,20 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, boo
 // ---------------------------------------------------------------------------
 // phase Z: z_b = sum_k pvm[k] / srho_b over the variable's row.
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void z_store(const SweepArgs<R> &a, int b, R S, const R *zo, R *zn, bool chk,
-                                        double &dual) {
+template <typename R, bool CHK>
+__device__ __forceinline__ void z_store(const SweepArgs<R> &a, int b, R S, const R *zo, R *zn, double &dual) {
     const R zold = zo[b];
     R znew = zold;
     if (a.srho[b] > R(0)) znew = S / a.srho[b];   // a variable without edges keeps z
     zn[b] = znew;
-    if (chk) {
+    if constexpr (CHK) {
         const double dz = (double)znew - (double)zold;
         dual += a.srho2[b] * dz * dz;
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *zn, bool chk, double &dual) {
+template <typename R, bool CHK>
+__device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *zn, double &dual) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     if (a.zorder == 0) {
@@ -845,7 +855,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         for (long long b = gtid; b < a.nz; b += gstride) {
             R S = R(0);
             for (int k = a.row[b]; k < a.row[b + 1]; ++k) S += ldg_l2(a.pvm + k);
-            z_store(a, (int)b, S, zo, zn, chk, dual);
+            z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
         }
         return;
     }
@@ -857,7 +867,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         const int b = a.small_vars[i];
         R S = R(0);
         for (int k = row[b]; k < row[b + 1]; ++k) S += ldg_l2(src + k);
-        z_store(a, b, S, zo, zn, chk, dual);
+        z_store<R, CHK>(a, b, S, zo, zn, dual);
     }
     // ... the others one warp per item (a whole row, or one piece of a hub
     // row whose pieces are combined in piece order by the last warp done).
@@ -870,7 +880,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
         if (wi.w < 0) {
-            if (lane == 0) z_store(a, wi.x, S, zo, zn, chk, dual);
+            if (lane == 0) z_store<R, CHK>(a, wi.x, S, zo, zn, dual);
             continue;
         }
         const int h = wi.w;
@@ -891,7 +901,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
             for (int o = 16; o > 0; o >>= 1) T += __shfl_xor_sync(0xffffffffu, T, o);
             if (lane == 0) {
                 a.hub_ticket[h] = 0u;
-                z_store(a, wi.x, T, zo, zn, chk, dual);
+                z_store<R, CHK>(a, wi.x, T, zo, zn, dual);
             }
         }
     }
@@ -959,14 +969,13 @@ __device__ __forceinline__ EdgeIO<R> make_io(const SweepArgs<R> &a, int xp, int 
     io.zc = a.z[zp];
     io.zl = nullptr;
     io.pb = nullptr;
-    io.chk = 1;
     return io;
 }
 
 // ---------------------------------------------------------------------------
 // the persistent kernel: a whole call in one launch
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, int KIND>
 __global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> a) {
     unsigned int gen = 0;
     const unsigned int G = gridDim.x;
@@ -977,8 +986,9 @@ __global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> 
         const bool chk = pend && ((a.k0 + it - 1) % a.check_every == 0);
         const EdgeIO<R> io = make_io(a, xp, zp);
         double pri = 0.0;
-        if (pend) phase_f<R, F_U_PROX>(a, io, chk, pri);
-        else phase_f<R, F_PROX>(a, io, false, pri);
+        if (chk) phase_f<R, F_U_PROX_CHK, KIND>(a, io, pri);
+        else if (pend) phase_f<R, F_U_PROX, KIND>(a, io, pri);
+        else phase_f<R, F_PROX, KIND>(a, io, pri);
         if (chk) {
             const double s = block_sum(pri);
             if (threadIdx.x == 0) a.res_pri[blockIdx.x] = s;
@@ -995,7 +1005,8 @@ __global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> 
         xp ^= 1;
         const bool chkz = ((a.k0 + it) % a.check_every == 0) || it == a.K;
         double dual = 0.0;
-        phase_z(a, a.z[zp], a.z[zp ^ 1], chkz, dual);
+        if (chkz) phase_z<R, true>(a, a.z[zp], a.z[zp ^ 1], dual);
+        else phase_z<R, false>(a, a.z[zp], a.z[zp ^ 1], dual);
         if (chkz) {
             const double s = block_sum(dual);
             if (threadIdx.x == 0) a.res_dual[(long long)(it & 1) * a.gmax + blockIdx.x] = s;
@@ -1007,7 +1018,7 @@ __global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> 
     // u-update of the last iteration, and its residual check
     EdgeIO<R> io = make_io(a, xp, zp);
     double pri = 0.0;
-    phase_f<R, F_U_ONLY>(a, io, true, pri);
+    phase_f<R, F_U_ONLY, KIND>(a, io, pri);
     const double s = block_sum(pri);
     if (threadIdx.x == 0) a.res_pri[blockIdx.x] = s;
     if (!grid_barrier(a.bar, G, gen, a.timeout_ns, skip)) return;
@@ -1019,13 +1030,13 @@ __global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> 
 // unfused launches: one kernel per phase; each exits at once when an
 // earlier check of this call has stopped it.
 // ---------------------------------------------------------------------------
-template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_phase_f(const SweepArgs<R> a, int xp, int zp, int chk) {
+template <typename R, int MODE, int KIND>
+__global__ void __launch_bounds__(256) k_phase_f(const SweepArgs<R> a, int xp, int zp) {
     if (*(volatile int *)&a.ctl->done) return;
     const EdgeIO<R> io = make_io(a, xp, zp);
     double pri = 0.0;
-    phase_f<R, MODE>(a, io, chk != 0, pri);
-    if (chk) {
+    phase_f<R, MODE, KIND>(a, io, pri);
+    if constexpr (fmode_checks(MODE)) {
         const double s = block_sum(pri);
         if (threadIdx.x == 0) a.res_pri[blockIdx.x] = s;
     }
@@ -1035,7 +1046,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_phase_z(const SweepArgs<R> a, int zp, long long it, int chk) {
     if (*(volatile int *)&a.ctl->done) return;
     double dual = 0.0;
-    phase_z(a, a.z[zp], a.z[zp ^ 1], chk != 0, dual);
+    if (chk) phase_z<R, true>(a, a.z[zp], a.z[zp ^ 1], dual);
+    else phase_z<R, false>(a, a.z[zp], a.z[zp ^ 1], dual);
     if (chk) {
         const double s = block_sum(dual);
         if (threadIdx.x == 0) a.res_dual[(long long)(it & 1) * a.gmax + blockIdx.x] = s;

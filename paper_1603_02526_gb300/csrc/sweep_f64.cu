@@ -4,10 +4,10 @@
 #include "sweep_launch.cuh"
 
 namespace fga {
-template cudaError_t sweep_persistent<double>(const SweepArgs<double> &, int, int, int, cudaStream_t);
+template cudaError_t sweep_persistent<double>(const SweepArgs<double> &, int, int, int, int, cudaStream_t);
 template cudaError_t sweep_phase_f<double>(const SweepArgs<double> &, int, int, int, int, int, int, int,
                                           cudaStream_t);
 template cudaError_t sweep_phase_z<double>(const SweepArgs<double> &, int, long long, int, int, int, cudaStream_t);
 template cudaError_t sweep_check<double>(const SweepArgs<double> &, long long, int, int, int, int, cudaStream_t);
-template int sweep_max_blocks_per_sm<double>(int, int);
+template int sweep_max_blocks_per_sm<double>(int, int, int);
 }  // namespace fga

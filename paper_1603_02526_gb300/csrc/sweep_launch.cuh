@@ -6,44 +6,62 @@
 
 namespace fga {
 
-template <typename R>
-static cudaError_t allow_smem(int smem) {
+template <typename R, int KIND>
+static cudaError_t allow_smem_k(int smem) {
     // kernels that take the chunk buffers may need more than the default 48 KB;
     // ask for the largest shared-memory carveout so several CTAs fit per SM
-    cudaError_t e = cudaFuncSetAttribute((const void *)k_sweep_persistent<R>,
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_sweep_persistent<R, KIND>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)k_sweep_persistent<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute((const void *)k_sweep_persistent<R, KIND>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_PROX, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_U_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_U_PROX, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void *)k_phase_f<R, F_U_ONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem);
+    e = cudaFuncSetAttribute((const void *)k_phase_f<R, F_U_PROX_CHK, KIND>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)k_phase_f<R, F_U_ONLY, KIND>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 template <typename R>
-cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, int smem, cudaStream_t s) {
-    cudaError_t e = allow_smem<R>(smem);
+static cudaError_t allow_smem(int smem, int kind) {
+    return kind == 1 ? allow_smem_k<R, 1>(smem) : allow_smem_k<R, 0>(smem);
+}
+
+template <typename R>
+cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, int smem, int kind, cudaStream_t s) {
+    cudaError_t e = allow_smem<R>(smem, kind);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
     // Cooperative launch: the runtime refuses a grid that cannot be
     // co-resident, so the grid-wide barrier can never wait on a CTA that
     // was not scheduled.
-    return cudaLaunchCooperativeKernel((const void *)k_sweep_persistent<R>, dim3(grid), dim3(block), args,
-                                       (size_t)smem, s);
+    const void *fn = kind == 1 ? (const void *)k_sweep_persistent<R, 1> : (const void *)k_sweep_persistent<R, 0>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, (size_t)smem, s);
+}
+
+template <typename R, int KIND>
+static void phase_f_k(const SweepArgs<R> &a, int mode, int xp, int zp, int grid, int block, int smem,
+                      cudaStream_t s) {
+    if (mode == F_PROX) k_phase_f<R, F_PROX, KIND><<<grid, block, smem, s>>>(a, xp, zp);
+    else if (mode == F_U_PROX) k_phase_f<R, F_U_PROX, KIND><<<grid, block, smem, s>>>(a, xp, zp);
+    else if (mode == F_U_PROX_CHK) k_phase_f<R, F_U_PROX_CHK, KIND><<<grid, block, smem, s>>>(a, xp, zp);
+    else k_phase_f<R, F_U_ONLY, KIND><<<grid, block, smem, s>>>(a, xp, zp);
 }
 
 template <typename R>
-cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int chk, int grid, int block, int smem,
+cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int grid, int block, int smem, int kind,
                           cudaStream_t s) {
-    cudaError_t e = allow_smem<R>(smem);
+    cudaError_t e = allow_smem<R>(smem, kind);
     if (e != cudaSuccess) return e;
-    if (mode == F_PROX) k_phase_f<R, F_PROX><<<grid, block, smem, s>>>(a, xp, zp, chk);
-    else if (mode == F_U_PROX) k_phase_f<R, F_U_PROX><<<grid, block, smem, s>>>(a, xp, zp, chk);
-    else k_phase_f<R, F_U_ONLY><<<grid, block, smem, s>>>(a, xp, zp, chk);
+    if (kind == 1) phase_f_k<R, 1>(a, mode, xp, zp, grid, block, smem, s);
+    else phase_f_k<R, 0>(a, mode, xp, zp, grid, block, smem, s);
     return cudaGetLastError();
 }
 
@@ -62,11 +80,11 @@ cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int
 }
 
 template <typename R>
-int sweep_max_blocks_per_sm(int block, int smem) {
-    if (allow_smem<R>(smem) != cudaSuccess) return 0;
+int sweep_max_blocks_per_sm(int block, int smem, int kind) {
+    if (allow_smem<R>(smem, kind) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_persistent<R>, block, (size_t)smem) != cudaSuccess)
-        return 0;
+    const void *fn = kind == 1 ? (const void *)k_sweep_persistent<R, 1> : (const void *)k_sweep_persistent<R, 0>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, (size_t)smem) != cudaSuccess) return 0;
     return n;
 }
 
