@@ -35,7 +35,7 @@ BYTES_PER_EDGE_ITER = 20  # algorithmic: read u, read m|x, write u, write m|x, r
 METRIC = "edge-updates/s"
 UNIT = "scalar edge-updates/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_packing_n1000_f32.md")
-SWEEP_SOURCES = ["sweep.cuh", "sweep_launch.cuh", "sweep_f32.cu", "fga_internal.h"]
+SWEEP_SOURCES = ["sweep_tile.cu", "tile_internal.h", "fga_tile.cpp", "sweep.cuh", "fga_internal.h"]
 
 
 def _peaks():
@@ -212,8 +212,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     p = inputs.packing_problem(N_DISKS, seed=SEED)
     E = p.num_edges
-    g = graph_from_problem(p, "f32", device=local, stream=stream,
-                           options={_lib.FGA_OPT_ZORDER: 1, _lib.FGA_OPT_STORE_M: 0}, init=False)
+    g = graph_from_problem(p, "f32", device=local, stream=stream, options={_lib.FGA_OPT_STORE_M: 0}, init=False)
+    launch = g.fga_launch_info()
     z0_host = torch.from_numpy(p.z0).pin_memory()
     z_out = torch.empty(p.num_scalar_vars, dtype=torch.float64).pin_memory()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
@@ -266,7 +266,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": BYTES_PER_EDGE_ITER * E * ITERS,
-            "kernel": "k_sweep_persistent<float>"}
+            "kernel": "k_tile_sweep" if launch["zorder"] == 2 else "k_sweep_persistent<float>"}
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
@@ -285,7 +285,7 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps, "wall_s_timed_region": wall,
-            "launch": g.fga_launch_info()}
+            "launch": launch}
     line.update(extras)
     print(json.dumps(line))
     if ws > 1:
@@ -363,7 +363,10 @@ def run_profile(args):
     from paper_1603_02526_gb300.graph import graph_from_problem
     build.build()
     p = inputs.packing_problem(N_DISKS, seed=SEED)
-    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_ZORDER: 1, _lib.FGA_OPT_STORE_M: 0})
+    opts = {_lib.FGA_OPT_STORE_M: 0}
+    if args.zorder is not None:
+        opts[_lib.FGA_OPT_ZORDER] = args.zorder
+    g = graph_from_problem(p, "f32", options=opts)
     g.fga_iterate(args.profile_iters, check_every=args.profile_iters)
     g.fga_init(p.z0)
     r = g.fga_iterate(args.profile_iters, check_every=args.profile_iters)
@@ -382,6 +385,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the packing sweep (no SVM / MPC / warm start)")
+    ap.add_argument("--zorder", type=int, default=None, help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 tiles)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")
     args = ap.parse_args()

@@ -17,6 +17,7 @@
 #include "../../include/fgadmm.h"
 #include "fga_internal.h"
 #include "fga_host.h"
+#include "tile_internal.h"
 
 using namespace fga;
 
@@ -139,6 +140,10 @@ struct fga_graph {
     int n_small = 0, n_witems = 0, n_hubs = 0;
     DevBuf chunks, slot_var, ppos, lrow, lidx, part, prow;
     int nchunks = 0, smem = 0, bps = 0, kind = 0;
+    // disk-tile order (zorder 2): the plan and its device copies
+    TilePlan tile;
+    DevBuf t_cta, t_rowslot, t_colslot, t_mask, t_sv, t_zden, t_cptr, t_clist, t_loc, t_part, t_res;
+    int64_t tile_pair_ebase = 0;
     bool uniform_rho = true, uniform_alpha = true;
     int grid = 1, blk = 256;
 
@@ -221,7 +226,7 @@ extern "C" int fga_set_option(fga_graph *g, int32_t option, int64_t value) {
     if (g->finalized) return fail(FGA_ESTATE, "fga_set_option: graph already finalized");
     switch (option) {
     case FGA_OPT_ZORDER:
-        if (value != 0 && value != 1) return fail(FGA_EINVAL, "FGA_OPT_ZORDER must be 0 or 1");
+        if (value < 0 || value > 2) return fail(FGA_EINVAL, "FGA_OPT_ZORDER must be 0, 1 or 2");
         g->zorder = (int)value;
         return FGA_OK;
     case FGA_OPT_STORE_M:
@@ -427,7 +432,20 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
     // 64 spare elements: a bulk copy may read up to 16 bytes past the last edge
     const size_t eb = (size_t)(std::max<int64_t>(ES, 1) + 64) * sizeof(R);
     (void)E;
-    if (g->zorder == 0) {
+    if (g->zorder == 2) {
+        const TilePlan &T = g->tile;
+        if ((rc = upload_vec(g->t_cta, T.cta))) return rc;
+        if ((rc = upload_vec(g->t_rowslot, T.rowslot))) return rc;
+        if ((rc = upload_vec(g->t_colslot, T.colslot))) return rc;
+        if ((rc = upload_vec(g->t_mask, T.mask))) return rc;
+        if ((rc = upload_vec(g->t_sv, T.sv))) return rc;
+        if ((rc = upload_vec(g->t_zden, T.zden))) return rc;
+        if ((rc = upload_vec(g->t_cptr, T.cptr))) return rc;
+        if ((rc = upload_vec(g->t_clist, T.clist))) return rc;
+        if ((rc = upload_vec(g->t_loc, T.loc))) return rc;
+        CUDA_TRY(g->t_part.alloc((size_t)2 * T.ptot * sizeof(float)));
+        CUDA_TRY(cudaMemset(g->t_part.p, 0, g->t_part.bytes));
+    } else if (g->zorder == 0) {
         // canonical order: per-edge variable ids and positions in the
         // creation-ordered variable-major array
         if ((rc = upload_vec(g->d_svar, g->svar))) return rc;
@@ -668,11 +686,100 @@ static int build_zlists(fga_graph *g, const std::vector<int32_t> &rowp) {
     return FGA_OK;
 }
 
+// Disk-tile order: checks that the graph is a circle-packing graph the tile
+// kernel can run (FP32, one rho and alpha, only disk-pair / wall / radius
+// factors, m not kept) and builds the plan.  0: planned; 1: not suitable
+// (reason in `why`); < 0: error.
+static int try_tile_plan(fga_graph *g, std::string &why) {
+    if (!g->rho_c.empty() || !g->alpha_c.empty()) {
+        why = "rho or alpha set per edge";
+        return 1;
+    }
+    if (g->store_m == 1) {
+        why = "m is kept (FGA_OPT_STORE_M)";
+        return 1;
+    }
+    int npair_buckets = 0;
+    for (const Bucket &bk : g->buckets) {
+        if (bk.type == FGA_PACK_PAIR) ++npair_buckets;
+        else if (bk.type != FGA_PACK_WALL && bk.type != FGA_PACK_RADIUS_LIN && bk.type != FGA_PACK_RADIUS_QUAD) {
+            why = "factor types other than disk pairs, walls and radius rewards";
+            return 1;
+        }
+    }
+    if (npair_buckets != 1) {
+        why = "no disk pairs";
+        return 1;
+    }
+    TileInput in;
+    in.nz = g->nz;
+    try {
+        in.deg.assign((size_t)g->nz, 0.0);
+        const double rho = g->rho_u;
+        for (const Bucket &bk : g->buckets) {
+            for (int64_t f = 0; f < (int64_t)bk.members.size(); ++f) {
+                const FactorBatch &b = g->batches[bk.members[f].first];
+                const int64_t fi = bk.members[f].second;
+                const int64_t *v = b.vars.data() + fi * b.nv;
+                const double *p = b.param(fi);
+                if (bk.type == FGA_PACK_PAIR) {
+                    const int32_t c1 = (int32_t)g->voff[v[0]], r1 = (int32_t)g->voff[v[1]];
+                    const int32_t c2 = (int32_t)g->voff[v[2]], r2 = (int32_t)g->voff[v[3]];
+                    in.c1.push_back(c1);
+                    in.r1.push_back(r1);
+                    in.c2.push_back(c2);
+                    in.r2.push_back(r2);
+                    for (int32_t s : {c1, c1 + 1, r1, c2, c2 + 1, r2}) in.deg[s] += 1.0;
+                } else {
+                    TileInput::Local L;
+                    std::memset(&L, 0, sizeof L);
+                    L.type = bk.type;
+                    L.member = f;
+                    if (bk.type == FGA_PACK_WALL) {
+                        L.c = (int32_t)g->voff[v[0]];
+                        L.r = (int32_t)g->voff[v[1]];
+                        for (int k = 0; k < 4; ++k) L.p[k] = (float)p[k];
+                        L.p[4] = (float)(1.0 / (p[0] * p[0] + p[1] * p[1] + 1.0));
+                        for (int32_t s : {L.c, L.c + 1, L.r}) in.deg[s] += 1.0;
+                    } else {
+                        L.c = -1;
+                        L.r = (int32_t)g->voff[v[0]];
+                        L.p[0] = bk.type == FGA_PACK_RADIUS_LIN ? (float)(p[0] / rho) : (float)(rho / (rho - 1.0));
+                        in.deg[L.r] += 1.0;
+                    }
+                    in.locs.push_back(L);
+                }
+            }
+        }
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
+    }
+    CUDA_TRY(cudaDeviceGetAttribute(&in.sms, cudaDevAttrMultiProcessorCount, g->device));
+    in.wmax = tile_max_warps();
+    int rc;
+    try {
+        rc = tile_plan(in, g->tile, why);
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
+    }
+    if (rc) return rc;
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
+    if (tile_smem_bytes(g->tile) > optin) {
+        why = "the z table of a CTA does not fit in shared memory";
+        return 1;
+    }
+    return 0;
+}
+
 extern "C" int fga_finalize(fga_graph *g) {
     if (!g) return fail(FGA_EINVAL, "fga_finalize: NULL graph");
     if (g->finalized) return fail(FGA_ESTATE, "fga_finalize: graph already finalized");
     int rc = set_device(g);
     if (rc) return rc;
+    const int zreq = g->zorder;   // -1: library choice
+    if (zreq == 2 && g->precision != FGA_F32)
+        return fail(FGA_EINVAL, "fga_finalize: FGA_OPT_ZORDER 2 (disk tiles) needs FGA_F32");
     if (g->zorder < 0) g->zorder = g->precision == FGA_F64 ? 0 : 1;
     if (g->store_m < 0) g->store_m = g->precision == FGA_F64 ? 1 : 0;
     const int64_t E = g->ne;
@@ -713,6 +820,17 @@ extern "C" int fga_finalize(fga_graph *g) {
         }
         for (int64_t f = 0; f < b.count; ++f) g->buckets[found].members.emplace_back(bi, f);
     }
+    // 1a. disk-tile order when the graph suits it (FP32 default) or when asked
+    if (g->precision == FGA_F32 && (zreq < 0 || zreq == 2)) {
+        std::string why;
+        const int r = try_tile_plan(g, why);
+        if (r < 0) return r;
+        if (r == 0) g->zorder = 2;
+        else if (zreq == 2)
+            return fail(FGA_EINVAL, "fga_finalize: the disk-tile order does not apply: %s", why.c_str());
+    }
+    const bool tile = g->zorder == 2;
+    const int64_t tile_span = (int64_t)g->tile.U * kUnitEdges;
     // 1b. fast order: inside a bucket, factors that touch nearby variables
     // are stored together (stable sort by the blocks of the first and last
     // variable), so that a chunk of consecutive factors touches few variables
@@ -733,7 +851,9 @@ extern "C" int fga_finalize(fga_graph *g) {
     // 2. storage order: bucket by bucket (each base a multiple of 4),
     // factor-major or edge-major inside a bucket
     int64_t es = 0;
-    for (const Bucket &bk : g->buckets) es = ((es + 3) & ~int64_t(3)) + (int64_t)bk.members.size() * bk.arity;
+    for (const Bucket &bk : g->buckets)
+        es = ((es + 3) & ~int64_t(3)) +
+             (tile && bk.type == FGA_PACK_PAIR ? tile_span : (int64_t)bk.members.size() * bk.arity);
     if (es > (int64_t)INT32_MAX - 8) return fail(FGA_EINVAL, "fga_finalize: more than 2^31 edges with padding");
     std::vector<int64_t> c2s;
     try {
@@ -746,29 +866,46 @@ extern "C" int fga_finalize(fga_graph *g) {
     int64_t ebase = 0, item = 0;
     for (Bucket &bk : g->buckets) {
         const int64_t nf = (int64_t)bk.members.size();
+        const bool tp = tile && bk.type == FGA_PACK_PAIR;
         ebase = (ebase + 3) & ~int64_t(3);
         bk.ebase = ebase;
         bk.item0 = item;
         bk.nitems = bk.per_edge ? nf * bk.arity : nf;
+        if (tp) g->tile_pair_ebase = ebase;
         for (int64_t f = 0; f < nf; ++f) {
             const FactorBatch &b = g->batches[bk.members[f].first];
             const int64_t fi = bk.members[f].second;
             const int64_t c0 = b.edge0 + fi * b.arity;
+            // disk-tile order: pair slot (unit, column, lane), edge k at
+            // unit * kUnitEdges + (column * 6 + k) * 32 + lane
+            const int64_t tpos = tp ? (int64_t)g->tile.pair_pos[f] : 0;
+            const int64_t tbase = (tpos / 256) * kUnitEdges + ((tpos % 256) / 32) * 6 * 32 + tpos % 32;
             int k = 0;
             for (int v = 0; v < b.nv; ++v) {
                 const int64_t var = b.vars[fi * b.nv + v];
                 for (int d = 0; d < b.dims[v]; ++d, ++k) {
-                    const int64_t s = bk.aos ? ebase + f * bk.arity + k : ebase + (int64_t)k * nf + f;
+                    const int64_t s = tp ? ebase + tbase + (int64_t)k * 32
+                                         : bk.aos ? ebase + f * bk.arity + k : ebase + (int64_t)k * nf + f;
                     g->s2c[s] = c0 + k;
                     c2s[c0 + k] = s;
                     g->svar[s] = (int32_t)(g->voff[var] + d);
                 }
             }
         }
-        ebase += nf * bk.arity;
+        ebase += tp ? tile_span : nf * bk.arity;
         item += bk.nitems;
     }
     g->es = es;
+    if (tile) {
+        // storage of the walls' and rewards' first edges
+        for (size_t i = 0; i < g->tile.loc.size(); ++i) {
+            for (const Bucket &bk : g->buckets) {
+                if (bk.type != g->tile.loc_bucket_type[i]) continue;
+                const int64_t f = g->tile.loc_member[i];
+                g->tile.loc[i].e0 = (int)(bk.aos ? bk.ebase + f * bk.arity : bk.ebase + f);
+            }
+        }
+    }
     g->nitems_f = item;
     // 3. variable-major rows, each in ascending creation order
     const int64_t Z = g->nz;
@@ -794,8 +931,13 @@ extern "C" int fga_finalize(fga_graph *g) {
     g->kind = 1;   // the kernel without hinge / dynamics paths when the graph has neither
     for (const Bucket &bk : g->buckets)
         if (bk.type == FGA_SVM_HINGE || bk.type == FGA_MPC_DYN) g->kind = 0;
-    const int bps = g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem, g->kind)
-                                            : sweep_max_blocks_per_sm<double>(g->blk, g->smem, g->kind);
+    if (tile) {
+        g->blk = g->tile.W * 32;
+        g->smem = tile_smem_bytes(g->tile);
+    }
+    const int bps = tile ? 1
+                    : g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem, g->kind)
+                                              : sweep_max_blocks_per_sm<double>(g->blk, g->smem, g->kind);
     if (bps < 1) return fail(FGA_ECUDA, "fga_finalize: the sweep kernel cannot be resident at %d threads", g->blk);
     g->bps = bps;
     const int64_t full = (int64_t)bps * dev_sms;
@@ -821,12 +963,19 @@ extern "C" int fga_finalize(fga_graph *g) {
     if (rc) return rc;
     // 6. launch shape: co-resident CTAs, no more than the work needs
     int64_t work;
-    if (g->zorder == 1)
+    if (tile)
+        work = (int64_t)g->tile.G * g->blk;
+    else if (g->zorder == 1)
         work = std::max<int64_t>(std::max<int64_t>((int64_t)g->nchunks * g->blk, g->n_small),
                                  (int64_t)g->n_witems * 32);
     else
         work = std::max<int64_t>(g->nitems_f, Z);
     g->grid = (int)std::max<int64_t>(1, std::min<int64_t>(full, (work + g->blk - 1) / g->blk));
+    if (tile) {
+        g->grid = g->tile.G;
+        CUDA_TRY(g->t_res.alloc((size_t)4 * g->grid * sizeof(double)));
+        CUDA_TRY(cudaMemset(g->t_res.p, 0, g->t_res.bytes));
+    }
     CUDA_TRY(g->res_pri.alloc((size_t)g->grid * sizeof(double)));
     CUDA_TRY(g->res_dual.alloc((size_t)2 * g->grid * sizeof(double)));
     CUDA_TRY(cudaMemset(g->res_pri.p, 0, g->res_pri.bytes));
@@ -1010,6 +1159,95 @@ static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
     a.bar = g->bar.as<Barrier>();
 }
 
+// Disk-tile order: one cooperative launch for the whole call (FP32).
+static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
+    const TilePlan &T = g->tile;
+    TileArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.G = T.G;
+    a.U = T.U;
+    a.smax = T.smax;
+    a.stgmax = T.stgmax;
+    a.svmax = T.svmax;
+    a.locmax = T.locmax;
+    a.clmax = T.clmax;
+    a.cta = g->t_cta.as<TileCta>();
+    a.rowslot = g->t_rowslot.as<unsigned short>();
+    a.colslot = g->t_colslot.as<unsigned short>();
+    a.mask = g->t_mask.as<unsigned char>();
+    a.sv = g->t_sv.as<int4>();
+    a.zden = g->t_zden.as<float>();
+    a.cptr = g->t_cptr.as<int>();
+    a.clist = g->t_clist.as<int>();
+    a.loc = g->t_loc.as<TileLocal>();
+    a.srho2 = g->srho2.as<double>();
+    a.u = g->u.as<float>();
+    a.xw = g->xpar ^ 1;
+    a.zw = g->zpar ^ 1;
+    a.xout = g->x[a.xw].as<float>();
+    a.zin = g->z[g->zpar].as<float>();
+    a.zout = g->z[a.zw].as<float>();
+    a.tpart = g->t_part.as<float>();
+    a.ptot = T.ptot;
+    a.res = g->t_res.as<double>();
+    a.pair_ebase = (int)g->tile_pair_ebase;
+    a.alpha = (float)g->alpha_u;
+    a.E = g->ne;
+    a.ctl = g->ctl.as<Ctl>();
+    a.sync = g->bar.as<TileSync>();
+    a.k0 = g->iters_done;
+    a.K = o.max_iters;
+    a.check_every = o.check_every;
+    a.tol_pri = o.tol_pri;
+    a.tol_dual = o.tol_dual;
+    a.timeout_ns = o.barrier_timeout_ns > 0 ? o.barrier_timeout_ns : 2000000000LL;
+    a.skip_block = o.fault_skip_block;
+    cudaStream_t s = g->stream;
+    if (a.K <= 0) {
+        res.iters = 0;
+        res.r_pri = g->last_rp;
+        res.r_dual = g->last_rd;
+        res.status = FGA_OK;
+        res.ms = 0.f;
+        return FGA_OK;
+    }
+    CUDA_TRY(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), s));
+    CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
+    // z of variables outside every tile (none in a qualifying graph) keep
+    // their value in the buffer the call writes
+    CUDA_TRY(cudaMemcpyAsync(a.zout, a.zin, (size_t)g->nz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaEventRecord(g->ev0, s));
+    CUDA_TRY(tile_sweep_launch(a, g->blk, g->smem, s));
+    CUDA_TRY(cudaEventRecord(g->ev1, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    Ctl c;
+    TileSync b;
+    CUDA_TRY(cudaMemcpy(&c, g->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&b, g->bar.p, sizeof b, cudaMemcpyDeviceToHost));
+    res.ms = ms;
+    if (b.error) {
+        g->initialized = false;
+        res.iters = 0;
+        res.r_pri = res.r_dual = std::numeric_limits<double>::quiet_NaN();
+        res.status = b.error;
+        return fail(b.error, "fga_iterate: a grid-wide wait timed out (status %d)", b.error);
+    }
+    if (!c.done) return fail(FGA_ECUDA, "fga_iterate: the sweep ended without reporting");
+    g->iters_done += c.iters;
+    g->xpar = c.xpar;
+    g->zpar = c.zpar;
+    g->last_rp = c.r_pri;
+    g->last_rd = c.r_dual;
+    res.iters = c.iters;
+    res.r_pri = c.r_pri;
+    res.r_dual = c.r_dual;
+    res.status = c.status;
+    if (c.status == FGA_ENONFINITE) return fail(FGA_ENONFINITE, "fga_iterate: residual became non-finite");
+    return FGA_OK;
+}
+
 template <typename R>
 static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
     SweepArgs<R> a;
@@ -1093,11 +1331,16 @@ extern "C" int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_res
         return fail(FGA_EINVAL, "fga_iterate: bad options");
     if (opts->fault_skip_block >= 0 && !opts->fused)
         return fail(FGA_EINVAL, "fga_iterate: fault_skip_block needs the fused kernel");
+    if (g->zorder == 2 && !opts->fused)
+        return fail(FGA_EINVAL, "fga_iterate: the disk-tile order runs as one persistent launch (fused = 1); "
+                                "set FGA_OPT_ZORDER 1 for one launch per phase");
     int rc = set_device(g);
     if (rc) return rc;
     fga_iter_result r;
     std::memset(&r, 0, sizeof r);
-    rc = g->precision == FGA_F32 ? iterate_typed<float>(g, *opts, r) : iterate_typed<double>(g, *opts, r);
+    rc = g->zorder == 2                ? iterate_tile(g, *opts, r)
+         : g->precision == FGA_F32 ? iterate_typed<float>(g, *opts, r)
+                                   : iterate_typed<double>(g, *opts, r);
     *result = r;   // also on timeout / non-finite, so the caller sees the status
     return rc;
 }
@@ -1109,8 +1352,9 @@ extern "C" int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n) {
     info[1] = g->blk;
     info[2] = g->smem;
     info[3] = g->bps;
-    info[4] = g->zorder == 1 ? g->nchunks : 0;
+    info[4] = g->zorder == 1 ? g->nchunks : g->zorder == 2 ? g->tile.U : 0;
     info[5] = (int64_t)g->buckets.size();
+    if (n >= 7) info[6] = g->zorder;
     return FGA_OK;
 }
 

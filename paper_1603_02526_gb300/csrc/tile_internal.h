@@ -1,0 +1,175 @@
+// tile_internal.h -- the disk-tile sweep: descriptors shared by the host
+// planner (fga_tile.cpp) and the kernel (sweep_tile.cu).  Not part of the
+// public C-ABI.
+//
+// A graph qualifies when it holds only circle-packing factors (disk pairs,
+// walls, radius rewards), runs in FP32 with one rho and one alpha, and its
+// disk pairs fill most of a 32 x 8 tiling of the pair matrix.  Disks are
+// numbered by the scalar id of their centre.  A disk pair (a, b) sits in
+// unit (a / 32, b / 8) at lane a % 32 and column b % 8; a warp owns one unit
+// for the whole call and keeps the unit's 1,536 u values in registers.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fga_internal.h"
+
+namespace fga {
+
+constexpr int kTileRows = 32;                               // disks per row block (one per lane)
+constexpr int kTileCols = 8;                                // disks per column group
+constexpr int kUnitEdges = kTileRows * kTileCols * 6;       // storage slots of one unit
+constexpr int kUnitStage = 3 * kTileRows + 3 * kTileCols;   // staged partial sums of one unit
+constexpr int kTileMaxWarps = 16;                           // units (warps) per CTA, at most
+
+// A wall or radius factor, processed by one thread of the CTA it is given
+// to.  p: wall Qx, Qy, Vx, Vy, 1 / (|Q|^2 + 1); linear reward w / rho;
+// area reward rho / (rho - 1).
+struct TileLocal {
+    int type;   // FGA_PACK_WALL (3 edges) or FGA_PACK_RADIUS_LIN / _QUAD (1 edge)
+    int e0;     // storage index of the first edge
+    int slot;   // the disk's slot in the CTA's z table
+    int stg;    // first staging position
+    float p[5];
+    int pad[3];
+};
+
+// Per CTA: its units (one per warp), its scalar variables ("slot-vars",
+// three per slot: centre x, centre y, radius), its local factors.
+struct TileCta {
+    int unit0, nunit;
+    int sv0, nsv;
+    int loc0, nloc;
+    int pad[2];
+};
+
+// Barrier word of the tile kernel: a counter that only grows (arrivals of
+// all CTAs over all iterations of a launch) and the error word, at the same
+// offset as Barrier::error so that the host reads both the same way.
+struct TileSync {
+    unsigned long long count;
+    int error;
+    int pad;
+};
+static_assert(sizeof(TileSync) == sizeof(Barrier), "TileSync and Barrier share one buffer");
+static_assert(offsetof(TileSync, error) == offsetof(Barrier, error), "error words must coincide");
+
+// Shared memory of one CTA (byte offsets, each 16-byte aligned): z and the
+// previous z per slot (float4: x, y, r, unused), slot-var descriptors, the
+// walls and rewards with their u, the edge counts, the contribution lists,
+// and the staging area of the partial sums.
+struct TileSmem {
+    int z4, zp4, sv, loc, uloc, zden, cptr, clist, stg, total;
+};
+inline __host__ __device__ constexpr int tile_align16(int v) { return (v + 15) & ~15; }
+inline __host__ __device__ TileSmem tile_smem_layout(int smax, int svmax, int locmax, int clmax, int stgmax) {
+    TileSmem L{};
+    int o = 0;
+    L.z4 = o;
+    o = tile_align16(o + smax * 16);
+    L.zp4 = o;
+    o = tile_align16(o + smax * 16);
+    L.sv = o;
+    o = tile_align16(o + svmax * 16);
+    L.loc = o;
+    o = tile_align16(o + locmax * (int)sizeof(TileLocal));
+    L.uloc = o;
+    o = tile_align16(o + locmax * 16);
+    L.zden = o;
+    o = tile_align16(o + svmax * 4);
+    L.cptr = o;
+    o = tile_align16(o + (svmax + 1) * 4);
+    L.clist = o;
+    o = tile_align16(o + clmax * 4);
+    L.stg = o;
+    o = tile_align16(o + stgmax * 4);
+    L.total = o;
+    return L;
+}
+
+struct TileArgs {
+    int G;          // CTAs
+    int U;          // units
+    int smax;       // slots of the largest z table
+    int stgmax;     // staging floats of the largest CTA
+    int svmax;      // slot-vars of the largest CTA
+    int locmax;     // walls and rewards of the largest CTA
+    int clmax;      // contributions of the largest CTA
+    const TileCta *cta;
+    const unsigned short *rowslot;   // [U][32] slot of each lane's row disk
+    const unsigned short *colslot;   // [U][8]  slot of each column disk
+    const unsigned char *mask;       // [U][32] bit c: pair (lane, c) exists
+    const int4 *sv;                  // per slot-var: var, first partial, end, this CTA's partial | owner << 31
+    const float *zden;               // per slot-var: number of edges of the variable
+    const int *cptr;                 // per slot-var: contributions cptr[i] .. cptr[i + 1] in clist
+    const int *clist;                // staging positions (relative to the CTA's staging area)
+    const TileLocal *loc;
+    const double *srho2;             // per variable: sum of rho^2 over its edges
+    float *u;                        // per edge (storage order)
+    float *xout;                     // x buffer written at checks and at the end
+    const float *zin;                // z at the start of the call
+    float *zout;                     // z written at checks and at the end
+    float *tpart;                    // [2][ptot] per-CTA partial sums, variable-major,
+                                     // each variable's row padded to a multiple of 4
+    int ptot;
+    double *res;                     // [2][2][G] residual partial sums (pri, dual)
+    int pair_ebase;                  // storage index of unit 0
+    float alpha;
+    long long E;
+    Ctl *ctl;
+    TileSync *sync;
+    long long k0, K;
+    int check_every;
+    double tol_pri, tol_dual;
+    long long timeout_ns;
+    int skip_block;
+    int xw, zw;                      // buffers written (for the control block)
+};
+
+// Host planner input: the graph's packing factors in bucket order.
+struct TileInput {
+    int64_t nz = 0;
+    // disk pairs: scalar ids of the two centres (first coordinate) and radii
+    std::vector<int32_t> c1, r1, c2, r2;
+    // walls (c, r, Q, V) and radius rewards (r, parameter)
+    struct Local {
+        int type;
+        int32_t c, r;          // c = -1 for a radius reward
+        int64_t member;        // factor index inside its bucket
+        float p[5];
+    };
+    std::vector<Local> locs;
+    std::vector<double> deg;   // per scalar variable: number of edges
+    int sms = 0;
+    int wmax = 0;              // warps per CTA the kernel can run with
+};
+
+struct TilePlan {
+    int U = 0, W = 0, G = 0, smax = 0, stgmax = 0, svmax = 0, locmax = 0, clmax = 0, ptot = 0;
+    std::vector<int32_t> pair_pos;      // per disk pair (bucket order): unit * 256 + column * 32 + lane
+    std::vector<TileCta> cta;
+    std::vector<uint16_t> rowslot, colslot;
+    std::vector<uint8_t> mask;
+    std::vector<int4> sv;
+    std::vector<float> zden;
+    std::vector<int32_t> cptr, clist;
+    std::vector<TileLocal> loc;         // e0 filled in after the storage layout
+    std::vector<int64_t> loc_member;    // bucket member of each local item (same order as loc)
+    std::vector<int> loc_bucket_type;   // its type
+};
+
+// Builds the plan; returns 0 when the graph qualifies, 1 (reason in `why`)
+// when it does not.
+int tile_plan(const TileInput &in, TilePlan &P, std::string &why);
+
+// Kernel launch (sweep_tile.cu) and the warps per CTA it can run with.
+cudaError_t tile_sweep_launch(const TileArgs &a, int block, int smem, cudaStream_t s);
+int tile_max_warps();
+int tile_smem_bytes(const TilePlan &P);
+
+}  // namespace fga

@@ -131,10 +131,10 @@ class FactorGraph:
         return out
 
     def fga_launch_info(self):
-        info = (ctypes.c_int64 * 6)()
-        check(self._lib.fga_launch_info(self._g, info, 6), "fga_launch_info")
+        info = (ctypes.c_int64 * 7)()
+        check(self._lib.fga_launch_info(self._g, info, 7), "fga_launch_info")
         return dict(grid=info[0], block=info[1], smem=info[2], blocks_per_sm=info[3], chunks=info[4],
-                    buckets=info[5])
+                    buckets=info[5], zorder=info[6])
 
     def fga_residuals(self):
         a, b = ctypes.c_double(), ctypes.c_double()

@@ -1,0 +1,182 @@
+"""GPU parity of the disk-tile sweep (FGA_OPT_ZORDER 2: FP32 circle packing,
+disk-pair state in registers, x recomputed, one grid barrier per
+iteration) against the FP64 oracle and against the chunked fast order,
+through the C-ABI.
+
+FP32 rule (as for the chunked order): z and the edge messages are compared
+with the oracle on the scale S of the variables; the disk-pair operator
+divides by the distance of two incoming centres, so FP32 rounding is
+amplified on the few pairs whose messages come close, and the edge
+messages are bounded by percentile and maximum separately."""
+import numpy as np
+import pytest
+
+from oracle import from_problem as oracle_from_problem
+from oracle.oracle import EDGE_X, EDGE_U, EDGE_N
+from paper_1603_02526_gb300 import inputs
+from paper_1603_02526_gb300 import _lib
+from paper_1603_02526_gb300.graph import graph_from_problem
+from tests.helpers import packing_objective
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1603_02526_gb300 import build
+    build.build()
+
+
+def _tile(p, **opt):
+    g = graph_from_problem(p, "f32", options=opt or None)
+    assert g.fga_launch_info()["zorder"] == 2
+    return g
+
+
+def _edges(g):
+    return [g.fga_read_edge_state(w) for w in (_lib.FGA_EDGE_X, _lib.FGA_EDGE_U, _lib.FGA_EDGE_N)]
+
+
+def test_tile_order_is_the_f32_packing_default():
+    p = inputs.packing_problem(1000)
+    g = graph_from_problem(p, "f32")
+    info = g.fga_launch_info()
+    assert info["zorder"] == 2
+    # 2016 units of 32 x 8 disks, one per warp, at most 16 warps per CTA
+    assert info["chunks"] == 2016
+    assert info["grid"] * info["block"] // 32 >= 2016
+    # m kept, or per-edge rho, or FP64: the chunked / canonical orders
+    assert graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1}).fga_launch_info()["zorder"] == 1
+    q = inputs.packing_problem(20)
+    assert graph_from_problem(q, "f64").fga_launch_info()["zorder"] == 0
+
+
+def test_tile_n1000_first_iterations_against_oracle():
+    """The benchmark graph after 3 iterations: z to 1e-5 S; edge messages
+    99.9th percentile <= 1e-5 S and maximum <= 5e-3 S (an FP32 emulation of
+    the same iterations gives 5e-7 S and 9e-5 S)."""
+    p = inputs.packing_problem(1000)
+    g = _tile(p)
+    r = g.fga_iterate(3)
+    assert r["iters"] == 3
+    o = oracle_from_problem(p)
+    ro = o.iterate(3)
+    S = float(np.max(np.abs(o.z())))
+    assert np.max(np.abs(g.fga_read_z() - o.z())) <= 1e-5 * S
+    for got, w in zip(_edges(g), (EDGE_X, EDGE_U, EDGE_N)):
+        err = np.abs(got - o.edge(w))
+        assert np.percentile(err, 99.9) <= 1e-5 * S, (w, np.percentile(err, 99.9))
+        assert err.max() <= 5e-3 * S, (w, err.max())
+    # residuals of the last iteration agree with the oracle's to FP32 level
+    np.testing.assert_allclose([r["r_pri"], r["r_dual"]], [ro["r_pri"], ro["r_dual"]], rtol=1e-3)
+
+
+@pytest.mark.parametrize("n", [5, 20, 200])
+def test_tile_small_graphs_against_oracle(n):
+    """Ragged tiles (N not a multiple of 32 or 8, diagonal tiles half
+    empty): 10 iterations, z within 1e-4 S of the oracle."""
+    p = inputs.packing_problem(n)
+    g = _tile(p)
+    g.fga_iterate(10)
+    o = oracle_from_problem(p)
+    o.iterate(10)
+    S = float(np.max(np.abs(o.z())))
+    err = np.max(np.abs(g.fga_read_z() - o.z()))
+    print("N=%d: max |dz| = %.3e S" % (n, err / S))
+    assert err <= 1e-4 * S
+
+
+def test_tile_against_chunked_order():
+    """The two FP32 fast orders differ only in summation order: after 10
+    iterations of N=200 their z agree to 1e-4 S."""
+    p = inputs.packing_problem(200)
+    a = _tile(p)
+    a.fga_iterate(10)
+    b = graph_from_problem(p, "f32", options={_lib.FGA_OPT_ZORDER: 1})
+    assert b.fga_launch_info()["zorder"] == 1
+    b.fga_iterate(10)
+    S = float(np.max(np.abs(b.fga_read_z())))
+    err = np.max(np.abs(a.fga_read_z() - b.fga_read_z()))
+    print("tile vs chunked: max |dz| = %.3e S" % (err / S))
+    assert err <= 1e-4 * S
+
+
+def test_tile_chained_calls_equal_one_call():
+    """Resume: x is recomputed from u and the previous z, so a call that
+    starts from a stored state must continue with the same bits."""
+    p = inputs.packing_problem(200)
+    a = _tile(p)
+    a.fga_iterate(500)
+    b = _tile(p)
+    for _ in range(5):
+        b.fga_iterate(100, check_every=7)
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+    for x, y in zip(_edges(a), _edges(b)):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("ce", [1, 7])
+def test_tile_stop_rule_state(ce):
+    """A call that stops at the first checked iteration meeting the
+    tolerances leaves exactly the state of a plain call of that many
+    iterations."""
+    p = inputs.packing_problem(20)
+    p.factor_blocks[-1].params[:] = 0.01
+    a = _tile(p)
+    r = a.fga_iterate(20000, 1e-4, 1e-4, check_every=ce)
+    assert r["status"] == 0 and r["iters"] < 20000 and r["iters"] % ce == 0
+    assert r["r_pri"] <= 1e-4 and r["r_dual"] <= 1e-4
+    b = _tile(p)
+    rb = b.fga_iterate(r["iters"], check_every=r["iters"])
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+    for x, y in zip(_edges(a), _edges(b)):
+        assert np.array_equal(x, y)
+    assert (rb["r_pri"], rb["r_dual"]) == (r["r_pri"], r["r_dual"])
+
+
+def test_tile_objective_matches_oracle():
+    """N=20 run to residual 1e-4 (reward 0.01): objective within 1e-4
+    relative of the oracle's under the same stop rule."""
+    p = inputs.packing_problem(20)
+    p.factor_blocks[-1].params[:] = 0.01
+    g = _tile(p)
+    rg = g.fga_iterate(50000, 1e-4, 1e-4)
+    o = oracle_from_problem(p)
+    ro = o.iterate(50000, 1e-4, 1e-4)
+    assert rg["status"] == 0 and ro["status"] == 0
+    fg, fo = packing_objective(g.fga_read_z()), packing_objective(o.z())
+    assert abs(fg - fo) <= 1e-4 * abs(fo), (fg, fo, rg, ro)
+
+
+def test_tile_deterministic():
+    p = inputs.packing_problem(1000)
+    a = _tile(p)
+    a.fga_iterate(50)
+    b = _tile(p)
+    b.fga_iterate(50)
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+    assert np.array_equal(a.fga_read_edge_state(_lib.FGA_EDGE_U), b.fga_read_edge_state(_lib.FGA_EDGE_U))
+
+
+def test_tile_area_reward_and_alpha():
+    """The area reward -r^2/2 (rho 25) and a dual step alpha 0.7 through the
+    tile kernel: 200 iterations, z within 1e-4 S of the oracle."""
+    p = inputs.packing_problem(30, reward="quad", rho=25.0)
+    p.alpha = 0.7
+    g = _tile(p)
+    g.fga_iterate(200)
+    o = oracle_from_problem(p)
+    o.iterate(200)
+    S = float(np.max(np.abs(o.z())))
+    assert np.max(np.abs(g.fga_read_z() - o.z())) <= 1e-4 * S
+
+
+def test_tile_rejections():
+    p = inputs.packing_problem(20)
+    with pytest.raises(_lib.FgaError):
+        graph_from_problem(p, "f64", options={_lib.FGA_OPT_ZORDER: 2})
+    with pytest.raises(_lib.FgaError):
+        graph_from_problem(p, "f32", options={_lib.FGA_OPT_ZORDER: 2, _lib.FGA_OPT_STORE_M: 1})
+    g = _tile(p)
+    with pytest.raises(_lib.FgaError):
+        g.fga_iterate(10, fused=False)
