@@ -92,8 +92,19 @@ extern "C" {
 #define FGA_OPT_ZORDER 0      /* 0 = canonical: each z_b sums its edges one by
                                  one in ascending creation order (bit-exact
                                  with a serial FP64 loop); 1 = fast:
-                                 deterministic warp / block / hub trees.
-                                 Default: 0 for FGA_F64, 1 for FGA_F32.       */
+                                 deterministic warp / block / hub trees over
+                                 chunks of factors; 2 = disk tiles: circle
+                                 packing only (Sec. V-A: disk pairs, walls,
+                                 radius rewards), FP32, one rho and one
+                                 alpha, m not kept -- a warp holds 32 x 8
+                                 disk pairs' state in registers, x is
+                                 recomputed from u and the previous z, one
+                                 grid-wide barrier per iteration; fused
+                                 launches only.  Default: 0 for FGA_F64; for
+                                 FGA_F32, 2 when the graph qualifies, else
+                                 1.  Asking for 2 on a graph that does not
+                                 qualify makes fga_finalize return
+                                 FGA_EINVAL.                                 */
 #define FGA_OPT_STORE_M 1     /* 1 = keep m per edge so FGA_EDGE_M can be read
                                  back (default 1 for FGA_F64, 0 for FGA_F32)  */
 #define FGA_OPT_BLOCK 2       /* threads per CTA of the sweep (0 = library
@@ -161,7 +172,8 @@ typedef struct {
                                    check_every-th iteration and after the
                                    last one (>= 1)                           */
     int32_t fused;              /* 1 = one persistent kernel for the whole
-                                   call; 0 = one launch per update phase     */
+                                   call; 0 = one launch per update phase
+                                   (FGA_EINVAL in the disk-tile order)      */
     int64_t barrier_timeout_ns; /* limit on one grid-wide wait inside the
                                    persistent kernel (0 = 2e9 ns)            */
     int32_t fault_skip_block;   /* testing: >= 0 makes that CTA skip its
@@ -190,8 +202,9 @@ int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result
 
 /* Launch configuration chosen at fga_finalize, for reports: info[0] CTAs,
  * info[1] threads per CTA, info[2] dynamic shared memory per CTA (bytes),
- * info[3] co-resident CTAs per SM, info[4] work chunks (fast z-order; 0 in
- * canonical order), info[5] type buckets.  n >= 6. */
+ * info[3] co-resident CTAs per SM, info[4] work chunks (fast z-order), disk
+ * tiles (tile order) or 0 (canonical order), info[5] type buckets, and when
+ * n >= 7 info[6] the z-order in use (FGA_OPT_ZORDER values).  n >= 6. */
 int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n);
 
 /* Residuals of the last checked iteration (NaN before any). */

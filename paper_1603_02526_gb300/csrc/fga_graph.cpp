@@ -142,7 +142,9 @@ struct fga_graph {
     int nchunks = 0, smem = 0, bps = 0, kind = 0;
     // disk-tile order (zorder 2): the plan and its device copies
     TilePlan tile;
-    DevBuf t_cta, t_rowslot, t_colslot, t_mask, t_sv, t_zden, t_cptr, t_clist, t_loc, t_part, t_res;
+    DevBuf t_cta, t_rowslot, t_colslot, t_mask, t_sv, t_zden, t_cptr, t_clist, t_loc, t_part, t_res, t_dsave;
+    DevBuf t_dres, t_zprev;
+    bool tile_resume = false;   // alpha = 1: the last call left its displacements to resume from
     int64_t tile_pair_ebase = 0;
     bool uniform_rho = true, uniform_alpha = true;
     int grid = 1, blk = 256;
@@ -445,6 +447,9 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         if ((rc = upload_vec(g->t_loc, T.loc))) return rc;
         CUDA_TRY(g->t_part.alloc((size_t)2 * T.ptot * sizeof(float)));
         CUDA_TRY(cudaMemset(g->t_part.p, 0, g->t_part.bytes));
+        CUDA_TRY(g->t_dsave.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
+        CUDA_TRY(g->t_dres.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
+        CUDA_TRY(g->t_zprev.alloc((size_t)std::max<int64_t>(g->nz, 1) * sizeof(float)));
     } else if (g->zorder == 0) {
         // canonical order: per-edge variable ids and positions in the
         // creation-ordered variable-major array
@@ -744,7 +749,7 @@ static int try_tile_plan(fga_graph *g, std::string &why) {
                     } else {
                         L.c = -1;
                         L.r = (int32_t)g->voff[v[0]];
-                        L.p[0] = bk.type == FGA_PACK_RADIUS_LIN ? (float)(p[0] / rho) : (float)(rho / (rho - 1.0));
+                        L.p[0] = bk.type == FGA_PACK_RADIUS_LIN ? (float)(p[0] / rho) : (float)(1.0 / (rho - 1.0));
                         in.deg[L.r] += 1.0;
                     }
                     in.locs.push_back(L);
@@ -1083,6 +1088,7 @@ extern "C" int fga_init(fga_graph *g, const double *z0, const double *u0) {
     g->iters_done = 0;
     g->xpar = 0;
     g->zpar = 0;
+    g->tile_resume = false;
     g->last_rp = g->last_rd = std::numeric_limits<double>::quiet_NaN();
     g->initialized = true;
     return FGA_OK;
@@ -1182,6 +1188,11 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     a.loc = g->t_loc.as<TileLocal>();
     a.srho2 = g->srho2.as<double>();
     a.u = g->u.as<float>();
+    a.dsave = g->t_dsave.as<float>();
+    a.dres = g->t_dres.as<float>();
+    a.zpin = g->t_zprev.as<float>();
+    a.zpout = g->t_zprev.as<float>();
+    a.resume = g->tile_resume ? 1 : 0;
     a.xw = g->xpar ^ 1;
     a.zw = g->zpar ^ 1;
     a.xout = g->x[a.xw].as<float>();
@@ -1240,6 +1251,7 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     g->zpar = c.zpar;
     g->last_rp = c.r_pri;
     g->last_rd = c.r_dual;
+    g->tile_resume = a.alpha == 1.0f;
     res.iters = c.iters;
     res.r_pri = c.r_pri;
     res.r_dual = c.r_dual;

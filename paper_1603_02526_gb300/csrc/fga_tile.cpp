@@ -93,7 +93,10 @@ int tile_plan(const TileInput &in, TilePlan &P, std::string &why) {
             ls.push_back(uid);
         }
         ut[uid].m[l] |= (uint8_t)(1u << c);
-        tmp_pos[p] = uid * 256 + c * 32 + l;
+        // lane l keeps column c in register slot c ^ ((l >> 2) & 7): with
+        // this relabelling the kernel's reduce-scatter over the lanes needs
+        // no selects
+        tmp_pos[p] = uid * 256 + (c ^ ((l >> 2) & 7)) * 32 + l;
     }
     const int64_t U = (int64_t)ut.size();
     // sparse pair sets would waste most lanes; a graph of at most one unit
@@ -151,7 +154,10 @@ int tile_plan(const TileInput &in, TilePlan &P, std::string &why) {
             uint8_t colany = 0;
             for (int l = 0; l < kTileRows; ++l) colany |= t.m[l];
             for (int l = 0; l < kTileRows; ++l) {
-                P.mask[r * kTileRows + l] = t.m[l];
+                uint8_t mp = 0;   // bit j: pair of register slot j (column j ^ ((l >> 2) & 7))
+                for (int j = 0; j < kTileCols; ++j)
+                    if ((t.m[l] >> (j ^ ((l >> 2) & 7))) & 1u) mp |= (uint8_t)(1u << j);
+                P.mask[r * kTileRows + l] = mp;
                 if (t.m[l]) P.rowslot[r * kTileRows + l] = (uint16_t)slot_for(g, (int32_t)(t.I * kTileRows + l));
             }
             for (int c = 0; c < kTileCols; ++c)

@@ -2,24 +2,35 @@
 // graph (Sec. V-A, Appendix A operators) in FP32, one persistent launch per
 // call, the per-edge state of the disk pairs held in registers.
 //
-// Work: a unit is 32 row disks x 8 column disks of the pair matrix; lane l
-// of the warp that owns it holds the u of its 8 pairs (48 values) for the
-// whole launch.  x is not stored between iterations: with the deferred
-// update of Algorithm 2, iteration k needs x^{k-1} = Prox(z^{k-2} - u^{k-2}),
-// which the lane recomputes from u and the z two iterations back (the same
-// operations on the same operands, so the same bits).  Per iteration a lane
-// then runs, for each of its 8 pairs,
-//   u += alpha (x^{k-1} - z^{k-1}),  n = z^{k-1} - u,  x^k = Prox(n),
-//   m = x^k + u,
-// adds m of its row disk in registers and leaves m of the column disk for a
-// fixed shuffle reduce-scatter over the 32 lanes (27 shuffles per unit).
+// Displacements.  Write each operator's result as x = n + Delta.  With one
+// rho, m = x + u = z + Delta (since n = z - u), so the z-update of Algorithm
+// 2 is z_b <- z_b + (sum of Delta over the edges of b) / deg(b): the CTAs
+// reduce displacements, which are zero for every factor that is already
+// satisfied.  A disk pair's displacement has three numbers (a, b, t):
+// Delta = (-a, -b, -t, a, b, -t) on (c1, r1, c2, r2).
+//
+// Two forms of the per-pair state, both kept in registers by the lane that
+// owns the pair for the whole launch:
+//  * alpha = 1: u^k = z^{k-1} - z^k + Delta^k, hence n^k = y^k - Delta^k
+//    with y^k = 2 z^k - z^{k-1} per variable: the pair's state is its
+//    displacement (3 values), and an iteration is one operator evaluation.
+//  * any alpha: the pair keeps its 6 u values; x^{k-1} (needed by the
+//    deferred u-update) is recomputed from u and z^{k-2} -- the same
+//    operations on the same operands, so the same bits -- instead of being
+//    stored.
+// Walls and radius rewards (few) keep u in shared memory in both forms.
+//
+// Work: a unit is 32 row disks x 8 column disks of the pair matrix, one warp
+// each; a lane adds its row disk's displacements in registers and leaves
+// those of the column disks to a fixed shuffle reduce-scatter over the 32
+// lanes (21 shuffles of sums, then 6 of a butterfly, per unit).
 //
 // z-update (deterministic, no float atomics): each CTA sums the staged unit
 // and local-factor contributions per variable in a fixed order and writes
 // one partial per (CTA, variable) into a variable-major array; after the
 // grid-wide barrier every CTA sums, for each variable of its z table, that
 // variable's partials in CTA order -- every CTA obtains the same bits.  One
-// grid barrier per iteration.  The residuals (FP64) ride on the same
+// grid barrier per iteration.  The residuals (FP64 sums) ride on the same
 // barrier: the check of iteration k-1 is evaluated during iteration k.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,50 +40,49 @@
 
 namespace fga {
 
+// What one pass over a unit does:
+//  T_FIRST: the first iteration of a call (n from the stored u);
+//  T_MID:   one iteration;
+//  T_CHK:   one iteration, preceded by the residual and the stored state of
+//           the previous iteration;
+//  T_FINAL: only the residual and the stored state of the last iteration.
 enum TileMode : int { T_FIRST = 0, T_MID = 1, T_CHK = 2, T_FINAL = 3 };
 
 // ---------------------------------------------------------------------------
-// operators (Appendix A), FP32, one rho.  Explicit round-to-nearest
-// intrinsics pin every rounding, so a recomputed x has the bits of the first
-// evaluation whatever the surrounding code.
+// operators (Appendix A), FP32, one rho; explicit round-to-nearest
+// intrinsics pin every rounding.
 // ---------------------------------------------------------------------------
 
-// No-collision operator on (c1, r1, c2, r2): with one rho every share of the
-// displacement D = max(0, r1 + r2 - |c1 - c2|) is D/4; centres move apart
-// along (c2 - c1)/|c2 - c1| ((1, 0) when they coincide), radii shrink.
-// D <= 0 gives t = 0 and x = n exactly.
-static __device__ __forceinline__ void tile_prox_pair(const float (&n)[6], float (&x)[6]) {
-    const float dx = __fsub_rn(n[3], n[0]);
-    const float dy = __fsub_rn(n[4], n[1]);
+// No-collision operator: from dx, dy = n_c2 - n_c1 and sr = n_r1 + n_r2, the
+// displacement (a, b, t): t = qw max(0, sr - |(dx, dy)|) with qw = 1/4 (the
+// four equal shares of one rho; 0 for an empty pair slot), (a, b) = t times
+// the unit vector along (dx, dy), or (t, 0) when the centres coincide.
+static __device__ __forceinline__ void pair_disp(float dx, float dy, float sr, float qw, float &a, float &b,
+                                                 float &t) {
     const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
     const bool pos = d2 > 0.f;
     const float rd = rsqrtf(pos ? d2 : 1.f);
-    const float D = __fsub_rn(__fadd_rn(n[2], n[5]), __fmul_rn(d2, rd));
-    const float t = __fmul_rn(0.25f, fmaxf(D, 0.f));
-    const float hx = pos ? __fmul_rn(dx, rd) : 1.f;
-    const float hy = pos ? __fmul_rn(dy, rd) : 0.f;
-    x[0] = __fmaf_rn(-t, hx, n[0]);
-    x[1] = __fmaf_rn(-t, hy, n[1]);
-    x[2] = __fsub_rn(n[2], t);
-    x[3] = __fmaf_rn(t, hx, n[3]);
-    x[4] = __fmaf_rn(t, hy, n[4]);
-    x[5] = __fsub_rn(n[5], t);
+    const float D = __fsub_rn(sr, __fmul_rn(d2, rd));
+    t = __fmul_rn(qw, fmaxf(D, 0.f));
+    const float tr = __fmul_rn(t, rd);
+    a = pos ? __fmul_rn(tr, dx) : t;
+    b = __fmul_rn(tr, dy);
 }
 
 // Wall: keep the disk in the half-plane Q.(c - V) >= r.  With one rho the
-// violation h < 0 is removed by g = -h / (|Q|^2 + 1): c += g Q, r -= g.
-static __device__ __forceinline__ void tile_prox_wall(const float (&n)[3], const float *p, float (&x)[3]) {
+// violation h < 0 is removed by g = -h / (|Q|^2 + 1): Delta = g (Qx, Qy, -1).
+static __device__ __forceinline__ void wall_disp(const float (&n)[3], const float *p, float (&dl)[3]) {
     const float h = __fsub_rn(__fmaf_rn(p[0], __fsub_rn(n[0], p[2]), __fmul_rn(p[1], __fsub_rn(n[1], p[3]))), n[2]);
     const float g = __fmul_rn(-fminf(h, 0.f), p[4]);
-    x[0] = __fmaf_rn(g, p[0], n[0]);
-    x[1] = __fmaf_rn(g, p[1], n[1]);
-    x[2] = __fsub_rn(n[2], g);
+    dl[0] = __fmul_rn(g, p[0]);
+    dl[1] = __fmul_rn(g, p[1]);
+    dl[2] = -g;
 }
 
-// Radius rewards: linear -w r gives n + w / rho; the area reward -r^2 / 2
-// gives rho n / (rho - 1).
-static __device__ __forceinline__ float tile_prox_radius(int type, float n, float p0) {
-    return type == 2 ? __fadd_rn(n, p0) : __fmul_rn(p0, n);
+// Radius rewards: linear -w r: Delta = w / rho (p0); the area reward
+// -r^2 / 2: x = rho n / (rho - 1), Delta = n / (rho - 1) (p0 = 1 / (rho - 1)).
+static __device__ __forceinline__ float radius_disp(int type, float n, float p0) {
+    return type == 2 ? p0 : __fmul_rn(p0, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -88,7 +98,6 @@ static __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsign
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-
 static __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -130,13 +139,15 @@ static __device__ __forceinline__ bool tile_barrier(TileSync *s, unsigned long l
 }
 
 // ---------------------------------------------------------------------------
-// z gather: z of every slot-var from its partials (previous iteration),
-// the old z kept as z_prev; owners write z out (checks) and add the dual
-// residual rho^2 (z - z_prev)^2 of their variables.
+// z gather: z <- z + (sum of the variable's partials) / deg, the old z kept
+// as z_prev and, for the alpha = 1 form, y = 2 z - z_prev (the old y kept as
+// y_prev).  Owners write z out (checks) and add the dual residual
+// rho^2 (z - z_prev)^2 of their variables.
 // ---------------------------------------------------------------------------
-template <bool CHK>
+template <bool CHK, bool A1>
 static __device__ __forceinline__ void tile_gather(const TileArgs &a, int nsv, const int4 *sv, const float *zden,
-                                                   float *zt, float *zpt, int rbuf, double &dual) {
+                                                   float *zt, float *zpt, float *yt, float *ypt, int rbuf,
+                                                   double &dual) {
     const float4 *src = reinterpret_cast<const float4 *>(a.tpart + (size_t)rbuf * a.ptot);
     for (int i = threadIdx.x; i < nsv; i += blockDim.x) {
         const int4 d = sv[i];
@@ -162,29 +173,178 @@ static __device__ __forceinline__ void tile_gather(const TileArgs &a, int nsv, c
             S = __fadd_rn(S, t.z);
             S = __fadd_rn(S, t.w);
         }
-        const float zn = __fdiv_rn(S, zden[i]);
-        const int s = i / 3, q = i - 3 * s;
-        const float zo = zt[4 * s + q];
-        zpt[4 * s + q] = zo;
-        zt[4 * s + q] = zn;
+        const int s = i / 3, q = i - 3 * s, o = 4 * s + q;
+        const float zo = zt[o];
+        const float zn = __fadd_rn(zo, __fdiv_rn(S, zden[i]));
+        zpt[o] = zo;
+        zt[o] = zn;
+        if (A1) {
+            ypt[o] = yt[o];
+            yt[o] = __fmaf_rn(2.f, zn, -zo);
+        }
         if (CHK && d.w < 0) {
             a.zout[d.x] = zn;
+            if (A1) a.zpout[d.x] = zo;
             const double dz = (double)zn - (double)zo;
             dual += __ldg(a.srho2 + d.x) * dz * dz;
         }
     }
 }
 
+// Register slot j of lane l holds column j ^ mp, mp = (l >> 2) & 7, of the
+// unit; csp packs the z-table slots of the lane's register slots (two
+// 16-bit values per word).  An empty pair slot has weight w = 0: its share
+// qw = w / 4 makes its displacement exactly 0, and in the u form its u
+// stays 0.
+static __device__ __forceinline__ unsigned col_slot(const unsigned (&csp)[4], int c) {
+    return (c & 1) ? (csp[c >> 1] >> 16) : (csp[c >> 1] & 0xffffu);
+}
+
+// Row displacements of the lane's pairs to the staging area, column ones
+// reduce-scattered over the lanes.  The partner at distance 16 (8, 4)
+// holds the same columns in its upper half (quarter, eighth) of slots that
+// this lane holds in its lower one, so each step adds the partner's upper
+// values to the lane's lower ones; the lane ends with the sums of column
+// (lane >> 2) & 7.
+static __device__ __forceinline__ void stage_unit(int lane, float ar0, float ar1, float ar2, const float (&col)[8][3],
+                                                  float *stg_w) {
+    stg_w[lane] = ar0;
+    stg_w[32 + lane] = ar1;
+    stg_w[64 + lane] = ar2;
+    const unsigned FULL = 0xffffffffu;
+    float h4[4][3];
+    #pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        #pragma unroll
+        for (int q = 0; q < 3; ++q) h4[i][q] = __fadd_rn(col[i][q], __shfl_xor_sync(FULL, col[i + 4][q], 16));
+    }
+    float h2[2][3];
+    #pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        #pragma unroll
+        for (int q = 0; q < 3; ++q) h2[i][q] = __fadd_rn(h4[i][q], __shfl_xor_sync(FULL, h4[i + 2][q], 8));
+    }
+    float h1[3];
+    #pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        h1[q] = __fadd_rn(h2[0][q], __shfl_xor_sync(FULL, h2[1][q], 4));
+        h1[q] = __fadd_rn(h1[q], __shfl_xor_sync(FULL, h1[q], 2));
+        h1[q] = __fadd_rn(h1[q], __shfl_xor_sync(FULL, h1[q], 1));
+    }
+    const int cc = (lane >> 2) & 7;
+    const int q = lane & 3;
+    if (q < 3) stg_w[96 + q * 8 + cc] = q == 0 ? h1[0] : q == 1 ? h1[1] : h1[2];
+}
+
 // ---------------------------------------------------------------------------
-// one unit (one warp): the iteration of Algorithm 2 on its <= 256 pairs
+// one unit, alpha = 1: state D[c] = (a, b, t) of each pair.  In pass `it`
+// (>= 2) D holds Delta^{it-1}.  A pass that checks also needs Delta^{it-2}:
+// the pass before stores it to a.dsave (SAVE); when the previous pass was
+// the call's first, the stored u is read again instead (RELOAD).
+// ---------------------------------------------------------------------------
+template <int MODE, bool RELOAD, bool SAVE>
+static __device__ __forceinline__ void tile_unit_a1(const TileArgs &a, int unit, int lane, int rs, unsigned msk,
+                                                    const unsigned (&csp)[4], float (&D)[8][3], const float4 *z4,
+                                                    const float4 *zp4, const float4 *y4, const float4 *yp4,
+                                                    float *stg_w, double &pri) {
+    constexpr bool CHK = MODE == T_CHK || MODE == T_FINAL;
+    const size_t ubase = (size_t)a.pair_ebase + (size_t)unit * kUnitEdges + lane;
+    const size_t dbase = (size_t)unit * (kUnitEdges / 2) + lane;
+    float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zpr = zr, yr = zr, ypr = zr;
+    if (MODE == T_FIRST || CHK) zr = z4[rs];
+    if (CHK) zpr = zp4[rs];
+    if (CHK && !RELOAD) ypr = yp4[rs];
+    if (MODE == T_MID || MODE == T_CHK) yr = y4[rs];
+    float ar0 = 0.f, ar1 = 0.f, ar2 = 0.f;
+    float col[8][3];
+    #pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const unsigned slot = col_slot(csp, c);
+        const float w = ((msk >> c) & 1u) ? 1.f : 0.f;
+        if constexpr (CHK) {
+            // iteration it-1: x = n^{it-2} + Delta^{it-1}, u = z_prev - z + Delta^{it-1}
+            const float4 zc = z4[slot], zpc = zp4[slot];
+            const float z[6] = {zr.x, zr.y, zr.z, zc.x, zc.y, zc.z};
+            const float zp[6] = {zpr.x, zpr.y, zpr.z, zpc.x, zpc.y, zpc.z};
+            float no[6];
+            if (RELOAD) {
+                #pragma unroll
+                for (int k = 0; k < 6; ++k) no[k] = __fsub_rn(zp[k], a.u[ubase + (c * 6 + k) * 32]);
+            } else {
+                const float4 ypc = yp4[slot];
+                const float pa = a.dsave[dbase + (c * 3) * 32], pb = a.dsave[dbase + (c * 3 + 1) * 32],
+                            pt = a.dsave[dbase + (c * 3 + 2) * 32];
+                no[0] = __fadd_rn(ypr.x, pa);
+                no[1] = __fadd_rn(ypr.y, pb);
+                no[2] = __fadd_rn(ypr.z, pt);
+                no[3] = __fsub_rn(ypc.x, pa);
+                no[4] = __fsub_rn(ypc.y, pb);
+                no[5] = __fadd_rn(ypc.z, pt);
+            }
+            const float dl[6] = {-D[c][0], -D[c][1], -D[c][2], D[c][0], D[c][1], -D[c][2]};
+            float sq = 0.f;
+            #pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float xo = __fadd_rn(no[k], dl[k]);
+                const float uo = __fadd_rn(__fsub_rn(zp[k], z[k]), dl[k]);
+                const float d = __fsub_rn(xo, z[k]);
+                sq = __fmaf_rn(d, d, sq);
+                a.xout[ubase + (c * 6 + k) * 32] = xo;
+                a.u[ubase + (c * 6 + k) * 32] = uo;
+            }
+            // the pair's squared differences in FP32, the sum over pairs in
+            // FP64 (the FP64 pipe is narrow on this part)
+            pri += (double)__fmul_rn(sq, w);
+            // the displacements of the stored state, for a later call to
+            // resume from (with the z before it, written by the owners)
+            #pragma unroll
+            for (int j = 0; j < 3; ++j) a.dres[dbase + (c * 3 + j) * 32] = D[c][j];
+        }
+        if (MODE == T_FINAL) continue;
+        if (SAVE) {
+            #pragma unroll
+            for (int j = 0; j < 3; ++j) a.dsave[dbase + (c * 3 + j) * 32] = D[c][j];
+        }
+        float dx, dy, sr;
+        if (MODE == T_FIRST) {
+            // n = z - u from the stored u
+            const float4 zc = z4[slot];
+            float n[6];
+            const float z[6] = {zr.x, zr.y, zr.z, zc.x, zc.y, zc.z};
+            #pragma unroll
+            for (int k = 0; k < 6; ++k) n[k] = __fsub_rn(z[k], a.u[ubase + (c * 6 + k) * 32]);
+            dx = __fsub_rn(n[3], n[0]);
+            dy = __fsub_rn(n[4], n[1]);
+            sr = __fadd_rn(n[2], n[5]);
+        } else {
+            // n = y - Delta: n_c2 - n_c1 = (y_c2 - y_c1) - 2 (a, b), n_r1 + n_r2 = y_r1 + y_r2 + 2 t
+            const float4 yc = y4[slot];
+            dx = __fmaf_rn(-2.f, D[c][0], __fsub_rn(yc.x, yr.x));
+            dy = __fmaf_rn(-2.f, D[c][1], __fsub_rn(yc.y, yr.y));
+            sr = __fmaf_rn(2.f, D[c][2], __fadd_rn(yr.z, yc.z));
+        }
+        float pa, pb, pt;
+        pair_disp(dx, dy, sr, __fmul_rn(0.25f, w), pa, pb, pt);
+        D[c][0] = pa;
+        D[c][1] = pb;
+        D[c][2] = pt;
+        ar0 = __fsub_rn(ar0, pa);
+        ar1 = __fsub_rn(ar1, pb);
+        ar2 = __fsub_rn(ar2, pt);
+        col[c][0] = pa;
+        col[c][1] = pb;
+        col[c][2] = -pt;
+    }
+    if (MODE != T_FINAL) stage_unit(lane, ar0, ar1, ar2, col, stg_w);
+}
+
+// ---------------------------------------------------------------------------
+// one unit, any alpha: state u[c][k]; x^{it-1} recomputed from u and z_prev
 // ---------------------------------------------------------------------------
 template <int MODE>
-static __device__ __forceinline__ void tile_unit(const TileArgs &a, int unit, int lane, int rs, unsigned msk,
-                                                 float (&u)[8][6], const float4 *z4, const float4 *zp4, float *stg_w,
-                                                 double &pri) {
-    const uint4 cw = __ldg(reinterpret_cast<const uint4 *>(a.colslot) + unit);
-    const unsigned cs[8] = {cw.x & 0xffffu, cw.x >> 16, cw.y & 0xffffu, cw.y >> 16,
-                            cw.z & 0xffffu, cw.z >> 16, cw.w & 0xffffu, cw.w >> 16};
+static __device__ __forceinline__ void tile_unit_u(const TileArgs &a, int unit, int lane, int rs, unsigned msk,
+                                                   const unsigned (&csp)[4], float (&u)[8][6], const float4 *z4,
+                                                   const float4 *zp4, float *stg_w, double &pri) {
     const float4 zr = z4[rs];
     float4 zrp = make_float4(0.f, 0.f, 0.f, 0.f);
     if (MODE != T_FIRST) zrp = zp4[rs];
@@ -194,97 +354,55 @@ static __device__ __forceinline__ void tile_unit(const TileArgs &a, int unit, in
     const float al = a.alpha;
     #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const bool on = (msk >> c) & 1u;
-        const float4 zc = z4[cs[c]];
+        const unsigned slot = col_slot(csp, c);
+        const float w = ((msk >> c) & 1u) ? 1.f : 0.f;
+        const float qw = __fmul_rn(0.25f, w);
+        const float4 zc = z4[slot];
         const float z[6] = {zr.x, zr.y, zr.z, zc.x, zc.y, zc.z};
         if (MODE != T_FIRST) {
-            // deferred update of the previous iteration, x^{k-1} recomputed
-            const float4 zcp = zp4[cs[c]];
+            // deferred update of the previous iteration, x^{it-1} recomputed
+            const float4 zcp = zp4[slot];
             const float zp[6] = {zrp.x, zrp.y, zrp.z, zcp.x, zcp.y, zcp.z};
-            float no[6], xo[6];
+            float no[6];
             #pragma unroll
             for (int k = 0; k < 6; ++k) no[k] = __fsub_rn(zp[k], u[c][k]);
-            tile_prox_pair(no, xo);
+            float oa, ob, ot;
+            pair_disp(__fsub_rn(no[3], no[0]), __fsub_rn(no[4], no[1]), __fadd_rn(no[2], no[5]), qw, oa, ob, ot);
+            const float dl[6] = {-oa, -ob, -ot, oa, ob, -ot};
+            const float aw = __fmul_rn(al, w);
+            float sq = 0.f;
             #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                const float d = __fsub_rn(xo[k], z[k]);
-                if (MODE >= T_CHK && on) {
-                    const double dd = (double)xo[k] - (double)z[k];
-                    pri += dd * dd;
+                const float xo = __fadd_rn(no[k], dl[k]);
+                const float d = __fsub_rn(xo, z[k]);
+                if (MODE >= T_CHK) {
+                    sq = __fmaf_rn(d, d, sq);
+                    a.xout[ubase + (c * 6 + k) * 32] = xo;
                 }
-                u[c][k] = on ? __fmaf_rn(al, d, u[c][k]) : u[c][k];
+                u[c][k] = __fmaf_rn(aw, d, u[c][k]);
+                if (MODE >= T_CHK) a.u[ubase + (c * 6 + k) * 32] = u[c][k];
             }
-            if (MODE >= T_CHK) {
-                #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    a.xout[ubase + (c * 6 + k) * 32] = xo[k];
-                    a.u[ubase + (c * 6 + k) * 32] = u[c][k];
-                }
-            }
+            if (MODE >= T_CHK) pri += (double)__fmul_rn(sq, w);
         }
         if (MODE != T_FINAL) {
-            float n[6], x[6];
+            float n[6];
             #pragma unroll
             for (int k = 0; k < 6; ++k) n[k] = __fsub_rn(z[k], u[c][k]);
-            tile_prox_pair(n, x);
-            float m[6];
-            #pragma unroll
-            for (int k = 0; k < 6; ++k) m[k] = on ? __fadd_rn(x[k], u[c][k]) : 0.f;
-            ar0 = __fadd_rn(ar0, m[0]);
-            ar1 = __fadd_rn(ar1, m[1]);
-            ar2 = __fadd_rn(ar2, m[2]);
-            col[c][0] = m[3];
-            col[c][1] = m[4];
-            col[c][2] = m[5];
+            float pa, pb, pt;
+            pair_disp(__fsub_rn(n[3], n[0]), __fsub_rn(n[4], n[1]), __fadd_rn(n[2], n[5]), qw, pa, pb, pt);
+            ar0 = __fsub_rn(ar0, pa);
+            ar1 = __fsub_rn(ar1, pb);
+            ar2 = __fsub_rn(ar2, pt);
+            col[c][0] = pa;
+            col[c][1] = pb;
+            col[c][2] = -pt;
         }
     }
-    if (MODE == T_FINAL) return;
-    // row disks: one partial per lane
-    stg_w[lane] = ar0;
-    stg_w[32 + lane] = ar1;
-    stg_w[64 + lane] = ar2;
-    // column disks: reduce-scatter over the lanes.  Step s halves the
-    // columns a lane keeps and adds the partner's value of the kept ones.
-    const unsigned FULL = 0xffffffffu;
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    float h4[4][3];
-    #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const float keep = b4 ? col[i + 4][q] : col[i][q];
-            const float send = b4 ? col[i][q] : col[i + 4][q];
-            h4[i][q] = __fadd_rn(keep, __shfl_xor_sync(FULL, send, 16));
-        }
-    }
-    float h2[2][3];
-    #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const float keep = b3 ? h4[i + 2][q] : h4[i][q];
-            const float send = b3 ? h4[i][q] : h4[i + 2][q];
-            h2[i][q] = __fadd_rn(keep, __shfl_xor_sync(FULL, send, 8));
-        }
-    }
-    float h1[3];
-    #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const float keep = b2 ? h2[1][q] : h2[0][q];
-        const float send = b2 ? h2[0][q] : h2[1][q];
-        h1[q] = __fadd_rn(keep, __shfl_xor_sync(FULL, send, 4));
-        h1[q] = __fadd_rn(h1[q], __shfl_xor_sync(FULL, h1[q], 2));
-        h1[q] = __fadd_rn(h1[q], __shfl_xor_sync(FULL, h1[q], 1));
-    }
-    // lane holds the full sums of column 4 b4 + 2 b3 + b2; lanes 0..2 of
-    // each group of four write one component each
-    const int cc = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
-    const int q = lane & 3;
-    if (q < 3) stg_w[96 + q * 8 + cc] = q == 0 ? h1[0] : q == 1 ? h1[1] : h1[2];
+    if (MODE != T_FINAL) stage_unit(lane, ar0, ar1, ar2, col, stg_w);
 }
 
 // ---------------------------------------------------------------------------
-// walls and radius rewards (one thread each, u in global memory)
+// walls and radius rewards (one thread each, u in shared memory, any alpha)
 // ---------------------------------------------------------------------------
 template <int MODE>
 static __device__ __forceinline__ void tile_local(const TileArgs &a, const TileLocal &L, float *ul, const float *zt,
@@ -298,38 +416,40 @@ static __device__ __forceinline__ void tile_local(const TileArgs &a, const TileL
             z[k] = zt[4 * L.slot + k];
         }
         if (MODE != T_FIRST) {
-            float no[3], xo[3];
+            float no[3], dl[3];
             #pragma unroll
             for (int k = 0; k < 3; ++k) no[k] = __fsub_rn(zpt[4 * L.slot + k], u[k]);
-            tile_prox_wall(no, L.p, xo);
+            wall_disp(no, L.p, dl);
             #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float d = __fsub_rn(xo[k], z[k]);
+                const float xo = __fadd_rn(no[k], dl[k]);
+                const float d = __fsub_rn(xo, z[k]);
                 if (MODE >= T_CHK) {
-                    const double dd = (double)xo[k] - (double)z[k];
+                    const double dd = (double)xo - (double)z[k];
                     pri += dd * dd;
                 }
                 u[k] = __fmaf_rn(al, d, u[k]);
                 ul[k] = u[k];
                 if (MODE >= T_CHK) {
-                    a.xout[L.e0 + k] = xo[k];
+                    a.xout[L.e0 + k] = xo;
                     a.u[L.e0 + k] = u[k];
                 }
             }
         }
         if (MODE != T_FINAL) {
-            float n[3], x[3];
+            float n[3], dl[3];
             #pragma unroll
             for (int k = 0; k < 3; ++k) n[k] = __fsub_rn(z[k], u[k]);
-            tile_prox_wall(n, L.p, x);
+            wall_disp(n, L.p, dl);
             #pragma unroll
-            for (int k = 0; k < 3; ++k) stg[L.stg + k] = __fadd_rn(x[k], u[k]);
+            for (int k = 0; k < 3; ++k) stg[L.stg + k] = dl[k];
         }
     } else {
         float u = ul[0];
         const float z = zt[4 * L.slot + 2];
         if (MODE != T_FIRST) {
-            const float xo = tile_prox_radius(L.type, __fsub_rn(zpt[4 * L.slot + 2], u), L.p[0]);
+            const float no = __fsub_rn(zpt[4 * L.slot + 2], u);
+            const float xo = __fadd_rn(no, radius_disp(L.type, no, L.p[0]));
             const float d = __fsub_rn(xo, z);
             if (MODE >= T_CHK) {
                 const double dd = (double)xo - (double)z;
@@ -342,36 +462,65 @@ static __device__ __forceinline__ void tile_local(const TileArgs &a, const TileL
                 a.u[L.e0] = u;
             }
         }
-        if (MODE != T_FINAL) {
-            const float x = tile_prox_radius(L.type, __fsub_rn(z, u), L.p[0]);
-            stg[L.stg] = __fadd_rn(x, u);
-        }
+        if (MODE != T_FINAL) stg[L.stg] = radius_disp(L.type, __fsub_rn(z, u), L.p[0]);
     }
 }
 
 // Walls and rewards go to every warp in turn (item i: warp i mod warps,
 // lane i / warps), after the warp's unit.
 template <int MODE>
-static __device__ __forceinline__ void tile_work(const TileArgs &a, int nloc, const TileLocal *loc, float *uloc,
-                                                 bool has_unit, int unit, int lane, int rs, unsigned msk,
-                                                 float (&u)[8][6], const float4 *z4, const float4 *zp4, float *stg,
-                                                 double &pri) {
+static __device__ __forceinline__ void tile_locals(const TileArgs &a, int nloc, const TileLocal *loc, float *uloc,
+                                                   int lane, const float4 *z4, const float4 *zp4, float *stg,
+                                                   double &pri) {
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (has_unit) tile_unit<MODE>(a, unit, lane, rs, msk, u, z4, zp4, stg + warp * kUnitStage, pri);
     const float *zt = reinterpret_cast<const float *>(z4);
     const float *zpt = reinterpret_cast<const float *>(zp4);
     for (int i = lane * nw + warp; i < nloc; i += 32 * nw) tile_local<MODE>(a, loc[i], uloc + 4 * i, zt, zpt, stg, pri);
+}
+
+// Per-lane state of its pairs, for either form.
+template <bool A1>
+struct PairState;
+template <>
+struct PairState<true> {
+    float D[8][3];
+};
+template <>
+struct PairState<false> {
+    float u[8][6];
+};
+
+// LMODE: the walls' and rewards' pass (differs from the pairs' only when a
+// call resumes: the pairs continue from their displacements, the walls and
+// rewards start from their stored u).
+template <int MODE, int LMODE, bool RELOAD, bool SAVE, bool A1>
+static __device__ __forceinline__ void tile_pass(const TileArgs &a, int nloc, const TileLocal *loc, float *uloc,
+                                                 bool has_unit, int unit, int lane, int rs, unsigned msk,
+                                                 const unsigned (&csp)[4], PairState<A1> &ps, const float4 *z4,
+                                                 const float4 *zp4, const float4 *y4, const float4 *yp4, float *stg,
+                                                 double &pri) {
+    float *stg_w = stg + (threadIdx.x >> 5) * kUnitStage;
+    if (has_unit) {
+        if constexpr (A1)
+            tile_unit_a1<MODE, RELOAD, SAVE>(a, unit, lane, rs, msk, csp, ps.D, z4, zp4, y4, yp4, stg_w, pri);
+        else
+            tile_unit_u<MODE>(a, unit, lane, rs, msk, csp, ps.u, z4, zp4, stg_w, pri);
+    }
+    tile_locals<LMODE>(a, nloc, loc, uloc, lane, z4, zp4, stg, pri);
 }
 
 // ---------------------------------------------------------------------------
 // the kernel: iterations 1..K of one call, then the deferred update of
 // iteration K (with its residual check), in one cooperative launch
 // ---------------------------------------------------------------------------
+template <bool A1>
 __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const TileArgs a) {
     extern __shared__ __align__(16) unsigned char tsm[];
     const TileSmem L = tile_smem_layout(a.smax, a.svmax, a.locmax, a.clmax, a.stgmax);
     float4 *z4 = reinterpret_cast<float4 *>(tsm + L.z4);
     float4 *zp4 = reinterpret_cast<float4 *>(tsm + L.zp4);
+    float4 *y4 = reinterpret_cast<float4 *>(tsm + L.y4);
+    float4 *yp4 = reinterpret_cast<float4 *>(tsm + L.yp4);
     int4 *sv = reinterpret_cast<int4 *>(tsm + L.sv);
     TileLocal *loc = reinterpret_cast<TileLocal *>(tsm + L.loc);
     float *uloc = reinterpret_cast<float *>(tsm + L.uloc);
@@ -381,6 +530,8 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     float *stg = reinterpret_cast<float *>(tsm + L.stg);
     float *zt = reinterpret_cast<float *>(z4);
     float *zpt = reinterpret_cast<float *>(zp4);
+    float *yt = reinterpret_cast<float *>(y4);
+    float *ypt = reinterpret_cast<float *>(yp4);
     __shared__ double s_res[2];
 
     const TileCta C = a.cta[blockIdx.x];
@@ -389,21 +540,31 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     const int unit = C.unit0 + warp;
     int rs = 0;
     unsigned msk = 0u;
-    float u[8][6];
+    unsigned csp[4] = {0u, 0u, 0u, 0u};
+    PairState<A1> ps;
     if (has_unit) {
         rs = a.rowslot[unit * 32 + lane];
         msk = a.mask[unit * 32 + lane];
+        const int mp = (lane >> 2) & 7;
+        #pragma unroll
+        for (int j = 0; j < 4; ++j)
+            csp[j] = (unsigned)a.colslot[unit * 8 + ((2 * j) ^ mp)] |
+                     ((unsigned)a.colslot[unit * 8 + ((2 * j + 1) ^ mp)] << 16);
+    }
+    if constexpr (A1) {
+        // a call that resumes the previous one takes up its displacements
+        const size_t dbase = (size_t)unit * (kUnitEdges / 2) + lane;
+        #pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            #pragma unroll
+            for (int k = 0; k < 3; ++k) ps.D[c][k] = (a.resume && has_unit) ? a.dres[dbase + (c * 3 + k) * 32] : 0.f;
+        }
+    } else {
         const size_t ubase = (size_t)a.pair_ebase + (size_t)unit * kUnitEdges + lane;
         #pragma unroll
         for (int c = 0; c < 8; ++c) {
             #pragma unroll
-            for (int k = 0; k < 6; ++k) u[c][k] = a.u[ubase + (c * 6 + k) * 32];
-        }
-    } else {
-        #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            #pragma unroll
-            for (int k = 0; k < 6; ++k) u[c][k] = 0.f;
+            for (int k = 0; k < 6; ++k) ps.u[c][k] = has_unit ? a.u[ubase + (c * 6 + k) * 32] : 0.f;
         }
     }
     // the CTA's tables, once per launch
@@ -413,7 +574,15 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
         sv[i] = d;
         zden[i] = a.zden[C.sv0 + i];
         const int s = i / 3, q = i - 3 * s;
-        zt[4 * s + q] = a.zin[d.x];
+        const float z0 = a.zin[d.x];
+        zt[4 * s + q] = z0;
+        if (A1 && a.resume) {
+            const float zp0 = a.zpin[d.x];
+            zpt[4 * s + q] = zp0;
+            yt[4 * s + q] = __fmaf_rn(2.f, z0, -zp0);
+        } else {
+            yt[4 * s + q] = 0.f;
+        }
     }
     for (int i = threadIdx.x; i <= C.nsv; i += blockDim.x) cptr[i] = a.cptr[C.sv0 + i] - cbase;
     const int ncl = a.cptr[C.sv0 + C.nsv] - cbase;
@@ -431,20 +600,49 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
 
     const unsigned long long G = (unsigned long long)a.G;
     bool skip = a.skip_block == (int)blockIdx.x;
+    // resuming (alpha = 1): the first pass is an ordinary one, from the
+    // displacements and the two z of the previous call's last iteration
+    const bool res1 = A1 && a.resume;
     for (long long it = 1; it <= a.K + 1; ++it) {
         const bool fin = it == a.K + 1;
         const bool pend = it > 1;
         const bool chk = fin || (pend && (a.k0 + it - 1) % a.check_every == 0);
+        // the next pass checks: keep the displacements this pass replaces
+        const bool save = A1 && (pend || res1) && !fin && (it == a.K || (a.k0 + it) % a.check_every == 0);
+        const bool reload = it == 2 && !res1;
         double pri = 0.0, dual = 0.0;
         if (pend) {
-            if (chk) tile_gather<true>(a, C.nsv, sv, zden, zt, zpt, (int)((it - 1) & 1), dual);
-            else tile_gather<false>(a, C.nsv, sv, zden, zt, zpt, (int)((it - 1) & 1), dual);
+            if (chk) tile_gather<true, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, (int)((it - 1) & 1), dual);
+            else tile_gather<false, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, (int)((it - 1) & 1), dual);
         }
         __syncthreads();
-        if (!pend) tile_work<T_FIRST>(a, C.nloc, loc, uloc, has_unit, unit, lane, rs, msk, u, z4, zp4, stg, pri);
-        else if (fin) tile_work<T_FINAL>(a, C.nloc, loc, uloc, has_unit, unit, lane, rs, msk, u, z4, zp4, stg, pri);
-        else if (chk) tile_work<T_CHK>(a, C.nloc, loc, uloc, has_unit, unit, lane, rs, msk, u, z4, zp4, stg, pri);
-        else tile_work<T_MID>(a, C.nloc, loc, uloc, has_unit, unit, lane, rs, msk, u, z4, zp4, stg, pri);
+#define TILE_PASS2(M, LM, R, S) \
+    tile_pass<M, LM, R, S, A1>(a, C.nloc, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg, pri)
+#define TILE_PASS(M, R, S) TILE_PASS2(M, M, R, S)
+        if (!pend) {
+            if (res1) {
+                if (save) TILE_PASS2(T_MID, T_FIRST, false, true);
+                else TILE_PASS2(T_MID, T_FIRST, false, false);
+            } else {
+                TILE_PASS(T_FIRST, false, false);
+            }
+        } else if (fin) {
+            if (reload) TILE_PASS(T_FINAL, true, false);
+            else TILE_PASS(T_FINAL, false, false);
+        } else if (chk) {
+            if (reload) {
+                if (save) TILE_PASS(T_CHK, true, true);
+                else TILE_PASS(T_CHK, true, false);
+            } else {
+                if (save) TILE_PASS(T_CHK, false, true);
+                else TILE_PASS(T_CHK, false, false);
+            }
+        } else {
+            if (save) TILE_PASS(T_MID, false, true);
+            else TILE_PASS(T_MID, false, false);
+        }
+#undef TILE_PASS
+#undef TILE_PASS2
         __syncthreads();
         if (!fin) {
             // one partial per (CTA, variable): staged contributions in list order
@@ -507,11 +705,18 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     }
 }
 
+static const void *tile_kernel(bool a1) {
+    return a1 ? (const void *)k_tile_sweep<true> : (const void *)k_tile_sweep<false>;
+}
+
 int tile_max_warps() {
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, (const void *)k_tile_sweep) != cudaSuccess) return 0;
-    const int w = fa.maxThreadsPerBlock / 32;
-    return w < kTileMaxWarps ? w : kTileMaxWarps;
+    int w = kTileMaxWarps;
+    for (bool a1 : {true, false}) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, tile_kernel(a1)) != cudaSuccess) return 0;
+        if (fa.maxThreadsPerBlock / 32 < w) w = fa.maxThreadsPerBlock / 32;
+    }
+    return w;
 }
 
 int tile_smem_bytes(const TilePlan &P) {
@@ -519,11 +724,12 @@ int tile_smem_bytes(const TilePlan &P) {
 }
 
 cudaError_t tile_sweep_launch(const TileArgs &a, int block, int smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute((const void *)k_tile_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const void *fn = tile_kernel(a.alpha == 1.0f);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
     // cooperative: the grid must be co-resident for the grid-wide barrier
-    return cudaLaunchCooperativeKernel((const void *)k_tile_sweep, dim3(a.G), dim3(block), args, (size_t)smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(a.G), dim3(block), args, (size_t)smem, s);
 }
 
 }  // namespace fga

@@ -6,8 +6,9 @@
 // walls, radius rewards), runs in FP32 with one rho and one alpha, and its
 // disk pairs fill most of a 32 x 8 tiling of the pair matrix.  Disks are
 // numbered by the scalar id of their centre.  A disk pair (a, b) sits in
-// unit (a / 32, b / 8) at lane a % 32 and column b % 8; a warp owns one unit
-// for the whole call and keeps the unit's 1,536 u values in registers.
+// unit (a / 32, b / 8) at lane l = a % 32 and column c = b % 8, which the
+// lane keeps in register slot c ^ ((l >> 2) & 7); a warp owns one unit for
+// the whole call and keeps the unit's 1,536 u values in registers.
 #pragma once
 
 #include <cstddef>
@@ -29,7 +30,7 @@ constexpr int kTileMaxWarps = 16;                           // units (warps) per
 
 // A wall or radius factor, processed by one thread of the CTA it is given
 // to.  p: wall Qx, Qy, Vx, Vy, 1 / (|Q|^2 + 1); linear reward w / rho;
-// area reward rho / (rho - 1).
+// area reward 1 / (rho - 1).
 struct TileLocal {
     int type;   // FGA_PACK_WALL (3 edges) or FGA_PACK_RADIUS_LIN / _QUAD (1 edge)
     int e0;     // storage index of the first edge
@@ -59,12 +60,13 @@ struct TileSync {
 static_assert(sizeof(TileSync) == sizeof(Barrier), "TileSync and Barrier share one buffer");
 static_assert(offsetof(TileSync, error) == offsetof(Barrier, error), "error words must coincide");
 
-// Shared memory of one CTA (byte offsets, each 16-byte aligned): z and the
-// previous z per slot (float4: x, y, r, unused), slot-var descriptors, the
+// Shared memory of one CTA (byte offsets, each 16-byte aligned): z, the
+// previous z, y = 2 z - z_prev and the previous y per slot (float4: x, y,
+// r, unused), slot-var descriptors, the
 // walls and rewards with their u, the edge counts, the contribution lists,
 // and the staging area of the partial sums.
 struct TileSmem {
-    int z4, zp4, sv, loc, uloc, zden, cptr, clist, stg, total;
+    int z4, zp4, y4, yp4, sv, loc, uloc, zden, cptr, clist, stg, total;
 };
 inline __host__ __device__ constexpr int tile_align16(int v) { return (v + 15) & ~15; }
 inline __host__ __device__ TileSmem tile_smem_layout(int smax, int svmax, int locmax, int clmax, int stgmax) {
@@ -73,6 +75,10 @@ inline __host__ __device__ TileSmem tile_smem_layout(int smax, int svmax, int lo
     L.z4 = o;
     o = tile_align16(o + smax * 16);
     L.zp4 = o;
+    o = tile_align16(o + smax * 16);
+    L.y4 = o;
+    o = tile_align16(o + smax * 16);
+    L.yp4 = o;
     o = tile_align16(o + smax * 16);
     L.sv = o;
     o = tile_align16(o + svmax * 16);
@@ -103,7 +109,7 @@ struct TileArgs {
     const TileCta *cta;
     const unsigned short *rowslot;   // [U][32] slot of each lane's row disk
     const unsigned short *colslot;   // [U][8]  slot of each column disk
-    const unsigned char *mask;       // [U][32] bit c: pair (lane, c) exists
+    const unsigned char *mask;       // [U][32] bit j: the pair of register slot j exists
     const int4 *sv;                  // per slot-var: var, first partial, end, this CTA's partial | owner << 31
     const float *zden;               // per slot-var: number of edges of the variable
     const int *cptr;                 // per slot-var: contributions cptr[i] .. cptr[i + 1] in clist
@@ -111,6 +117,11 @@ struct TileArgs {
     const TileLocal *loc;
     const double *srho2;             // per variable: sum of rho^2 over its edges
     float *u;                        // per edge (storage order)
+    float *dsave;                    // alpha = 1: [U][24][32] displacements kept for the next check
+    float *dres;                     // alpha = 1: [U][24][32] displacements of the stored state
+    const float *zpin;               // alpha = 1: z before the stored state (resume)
+    float *zpout;                    // alpha = 1: written at checks with the state
+    int resume;                      // alpha = 1: dres / zpin hold the state this call starts from
     float *xout;                     // x buffer written at checks and at the end
     const float *zin;                // z at the start of the call
     float *zout;                     // z written at checks and at the end
@@ -151,7 +162,7 @@ struct TileInput {
 
 struct TilePlan {
     int U = 0, W = 0, G = 0, smax = 0, stgmax = 0, svmax = 0, locmax = 0, clmax = 0, ptot = 0;
-    std::vector<int32_t> pair_pos;      // per disk pair (bucket order): unit * 256 + column * 32 + lane
+    std::vector<int32_t> pair_pos;      // per disk pair (bucket order): unit * 256 + slot * 32 + lane
     std::vector<TileCta> cta;
     std::vector<uint16_t> rowslot, colslot;
     std::vector<uint8_t> mask;

@@ -115,6 +115,33 @@ def test_tile_chained_calls_equal_one_call():
         assert np.array_equal(x, y)
 
 
+def test_tile_resume_after_stop_and_alpha():
+    """Resume after a call that stopped at its tolerance (the state of the
+    checked iteration, not the last one computed) continues with the bits of
+    an unbroken run; the same for the u form (alpha 0.7)."""
+    p = inputs.packing_problem(20)
+    p.factor_blocks[-1].params[:] = 0.01
+    a = _tile(p)
+    r = a.fga_iterate(20000, 1e-3, 1e-3, check_every=5)
+    assert r["status"] == 0 and 0 < r["iters"] < 20000
+    a.fga_iterate(300, check_every=300)
+    b = _tile(p)
+    b.fga_iterate(r["iters"] + 300, check_every=10**6)
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+    for x, y in zip(_edges(a), _edges(b)):
+        assert np.array_equal(x, y)
+    q = inputs.packing_problem(200)
+    q.alpha = 0.7
+    c = _tile(q)
+    c.fga_iterate(300)
+    d = _tile(q)
+    for _ in range(3):
+        d.fga_iterate(100, check_every=7)
+    assert np.array_equal(c.fga_read_z(), d.fga_read_z())
+    for x, y in zip(_edges(c), _edges(d)):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("ce", [1, 7])
 def test_tile_stop_rule_state(ce):
     """A call that stops at the first checked iteration meeting the
