@@ -445,7 +445,7 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         if ((rc = upload_vec(g->t_cptr, T.cptr))) return rc;
         if ((rc = upload_vec(g->t_clist, T.clist))) return rc;
         if ((rc = upload_vec(g->t_loc, T.loc))) return rc;
-        CUDA_TRY(g->t_part.alloc((size_t)2 * T.ptot * sizeof(float)));
+        CUDA_TRY(g->t_part.alloc((size_t)3 * T.ptot * sizeof(long long)));
         CUDA_TRY(cudaMemset(g->t_part.p, 0, g->t_part.bytes));
         CUDA_TRY(g->t_dsave.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
         CUDA_TRY(g->t_dres.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
@@ -1198,7 +1198,7 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     a.xout = g->x[a.xw].as<float>();
     a.zin = g->z[g->zpar].as<float>();
     a.zout = g->z[a.zw].as<float>();
-    a.tpart = g->t_part.as<float>();
+    a.acc = g->t_part.as<long long>();
     a.ptot = T.ptot;
     a.res = g->t_res.as<double>();
     a.pair_ebase = (int)g->tile_pair_ebase;
@@ -1224,6 +1224,7 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     }
     CUDA_TRY(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), s));
     CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
+    CUDA_TRY(cudaMemsetAsync(g->t_part.p, 0, g->t_part.bytes, s));   // the fixed-point accumulators
     // z of variables outside every tile (none in a qualifying graph) keep
     // their value in the buffer the call writes
     CUDA_TRY(cudaMemcpyAsync(a.zout, a.zin, (size_t)g->nz * sizeof(float), cudaMemcpyDeviceToDevice, s));

@@ -4,9 +4,9 @@
 // Output: the units (32 row disks x 8 column disks of the pair matrix) in
 // row-major order, their assignment to CTAs (one unit per warp), each CTA's
 // z table (slots = disks it touches), the staging positions of every
-// contribution to a slot variable and the order they are summed in, the
-// variable-major layout of the per-CTA partial sums, and the CTA that owns
-// each variable (writes its z and adds its dual residual).
+// contribution to a slot variable and the order they are summed in, and
+// the CTA that owns each variable (writes its z, adds its dual residual and
+// clears its accumulator for reuse).
 #include <algorithm>
 #include <cstring>
 #include <unordered_map>
@@ -269,21 +269,21 @@ int tile_plan(const TileInput &in, TilePlan &P, std::string &why) {
         locmax = std::max(locmax, C.nloc);
         clmax = std::max(clmax, P.cptr.back() - P.cptr[C.sv0]);
     }
-    // rows padded to a multiple of 4 (16-byte loads; the padding stays zero)
-    std::vector<int64_t> prow((size_t)in.nz + 1, 0);
-    for (int64_t v = 0; v < in.nz; ++v) prow[v + 1] = prow[v] + ((pcount[v] + 3) & ~int64_t(3));
-    if (prow[in.nz] > (int64_t)INT32_MAX / 4) {
-        why = "too many partial sums";
-        return 1;
+    // one fixed-point accumulator per variable; the owner of a variable is
+    // its first holder
+    for (int64_t v = 0; v < in.nz; ++v) {
+        if (pcount[v] > kTileMaxHolders) {
+            why = "a variable is held by too many CTAs";
+            return 1;
+        }
     }
     for (int4 &d : P.sv) {
         const int k = d.w;
-        const int beg = (int)prow[d.x];
-        d.y = beg;
-        d.z = (int)prow[d.x + 1];
-        d.w = (beg + k) | (k == 0 ? (int)0x80000000u : 0);
+        d.y = (int)pcount[d.x];
+        d.z = 0;
+        d.w = k == 0 ? (int)0x80000000u : 0;
     }
-    P.ptot = (int)std::max<int64_t>(prow[in.nz], 1);
+    P.ptot = (int)std::max<int64_t>(in.nz, 1);
     P.smax = smax;
     P.stgmax = stgmax;
     P.svmax = svmax;

@@ -26,12 +26,13 @@
 // lanes (21 shuffles of sums, then 6 of a butterfly, per unit).
 //
 // z-update (deterministic, no float atomics): each CTA sums the staged unit
-// and local-factor contributions per variable in a fixed order and writes
-// one partial per (CTA, variable) into a variable-major array; after the
-// grid-wide barrier every CTA sums, for each variable of its z table, that
-// variable's partials in CTA order -- every CTA obtains the same bits.  One
-// grid barrier per iteration.  The residuals (FP64 sums) ride on the same
-// barrier: the check of iteration k-1 is evaluated during iteration k.
+// and local-factor contributions per variable in a fixed order and adds
+// that partial, as a 64-bit fixed-point integer, into the variable's
+// accumulator; integer addition is exact and associative, so after the
+// grid-wide barrier every CTA reads the same sum whatever the order of the
+// additions.  One grid barrier per iteration.  The residuals (FP64 sums)
+// ride on the same barrier: the check of iteration k-1 is evaluated during
+// iteration k.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -146,33 +147,13 @@ static __device__ __forceinline__ bool tile_barrier(TileSync *s, unsigned long l
 // ---------------------------------------------------------------------------
 template <bool CHK, bool A1>
 static __device__ __forceinline__ void tile_gather(const TileArgs &a, int nsv, const int4 *sv, const float *zden,
-                                                   float *zt, float *zpt, float *yt, float *ypt, int rbuf,
+                                                   float *zt, float *zpt, float *yt, float *ypt, int rbuf, int cbuf,
                                                    double &dual) {
-    const float4 *src = reinterpret_cast<const float4 *>(a.tpart + (size_t)rbuf * a.ptot);
+    const long long *src = a.acc + (size_t)rbuf * a.ptot;
+    long long *clr = a.acc + (size_t)cbuf * a.ptot;
     for (int i = threadIdx.x; i < nsv; i += blockDim.x) {
         const int4 d = sv[i];
-        float S = 0.f;
-        int p = d.y >> 2;
-        const int pe = d.z >> 2;
-        for (; p + 4 <= pe; p += 4) {
-            float4 t[4];
-            #pragma unroll
-            for (int j = 0; j < 4; ++j) t[j] = __ldcg(src + p + j);
-            #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                S = __fadd_rn(S, t[j].x);
-                S = __fadd_rn(S, t[j].y);
-                S = __fadd_rn(S, t[j].z);
-                S = __fadd_rn(S, t[j].w);
-            }
-        }
-        for (; p < pe; ++p) {
-            const float4 t = __ldcg(src + p);
-            S = __fadd_rn(S, t.x);
-            S = __fadd_rn(S, t.y);
-            S = __fadd_rn(S, t.z);
-            S = __fadd_rn(S, t.w);
-        }
+        const float S = __fmul_rn(__ll2float_rn(__ldcg(src + d.x)), kTileFixInv);
         const int s = i / 3, q = i - 3 * s, o = 4 * s + q;
         const float zo = zt[o];
         const float zn = __fadd_rn(zo, __fdiv_rn(S, zden[i]));
@@ -182,11 +163,15 @@ static __device__ __forceinline__ void tile_gather(const TileArgs &a, int nsv, c
             ypt[o] = yt[o];
             yt[o] = __fmaf_rn(2.f, zn, -zo);
         }
-        if (CHK && d.w < 0) {
-            a.zout[d.x] = zn;
-            if (A1) a.zpout[d.x] = zo;
-            const double dz = (double)zn - (double)zo;
-            dual += __ldg(a.srho2 + d.x) * dz * dz;
+        if (d.w < 0) {
+            // the owner clears the accumulator read in the previous pass
+            __stcg(clr + d.x, 0ll);
+            if (CHK) {
+                a.zout[d.x] = zn;
+                if (A1) a.zpout[d.x] = zo;
+                const double dz = (double)zn - (double)zo;
+                dual += __ldg(a.srho2 + d.x) * dz * dz;
+            }
         }
     }
 }
@@ -612,8 +597,9 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
         const bool reload = it == 2 && !res1;
         double pri = 0.0, dual = 0.0;
         if (pend) {
-            if (chk) tile_gather<true, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, (int)((it - 1) & 1), dual);
-            else tile_gather<false, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, (int)((it - 1) & 1), dual);
+            const int rb = (int)((it - 1) % 3), cb = (int)((it + 1) % 3);
+            if (chk) tile_gather<true, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, rb, cb, dual);
+            else tile_gather<false, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, rb, cb, dual);
         }
         __syncthreads();
 #define TILE_PASS2(M, LM, R, S) \
@@ -645,14 +631,20 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
 #undef TILE_PASS2
         __syncthreads();
         if (!fin) {
-            // one partial per (CTA, variable): staged contributions in list order
-            float *dst = a.tpart + (size_t)(it & 1) * a.ptot;
+            // one partial per (CTA, variable): staged contributions in list
+            // order, added in fixed point into the variable's accumulator
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.acc + (size_t)(it % 3) * a.ptot);
+            bool ovf = false;
             for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) {
                 const int j1 = cptr[i + 1];
                 float S = 0.f;
                 for (int j = cptr[i]; j < j1; ++j) S = __fadd_rn(S, stg[clist[j]]);
-                __stcg(dst + (sv[i].w & 0x7fffffff), S);
+                long long q = 0;
+                if (fabsf(S) < kTileFixMax) q = __float2ll_rn(__fmul_rn(S, kTileFixScale));
+                else ovf = true;
+                atomicAdd(dst + sv[i].x, (unsigned long long)q);
             }
+            if (ovf) atomicOr(&a.sync->overflow, 1);
         }
         if (chk) {
             const double sp = block_sum(pri);
@@ -680,7 +672,7 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
             CheckOut c;
             c.rp = s_res[0];
             c.rd = s_res[1];
-            const bool finite = isfinite(c.rp) && isfinite(c.rd);
+            const bool finite = isfinite(c.rp) && isfinite(c.rd) && *(volatile int *)&a.sync->overflow == 0;
             c.status = finite ? 0 : kENonFinite;
             c.stop = !finite || (c.rp <= a.tol_pri && c.rd <= a.tol_dual);
             if (c.stop || fin) {

@@ -27,6 +27,16 @@ constexpr int kTileCols = 8;                                // disks per column 
 constexpr int kUnitEdges = kTileRows * kTileCols * 6;       // storage slots of one unit
 constexpr int kUnitStage = 3 * kTileRows + 3 * kTileCols;   // staged partial sums of one unit
 constexpr int kTileMaxWarps = 16;                           // units (warps) per CTA, at most
+constexpr int kTileMaxHolders = 256;                        // CTAs holding one variable, at most
+// Per-CTA partial sums are added into one 64-bit fixed-point accumulator per
+// variable (scale 2^32): integer addition is exact and associative, so the
+// sum does not depend on the order in which the CTAs' additions land.  A
+// partial of magnitude 2^22 or more (or not finite) is reported as a
+// non-finite residual; with at most kTileMaxHolders partials the sum stays
+// below 2^62.
+constexpr float kTileFixScale = 4294967296.0f;              // 2^32
+constexpr float kTileFixInv = 2.3283064365386963e-10f;      // 2^-32
+constexpr float kTileFixMax = 4194304.0f;                   // 2^22
 
 // A wall or radius factor, processed by one thread of the CTA it is given
 // to.  p: wall Qx, Qy, Vx, Vy, 1 / (|Q|^2 + 1); linear reward w / rho;
@@ -55,7 +65,7 @@ struct TileCta {
 struct TileSync {
     unsigned long long count;
     int error;
-    int pad;
+    int overflow;   // a partial sum out of the fixed-point range
 };
 static_assert(sizeof(TileSync) == sizeof(Barrier), "TileSync and Barrier share one buffer");
 static_assert(offsetof(TileSync, error) == offsetof(Barrier, error), "error words must coincide");
@@ -110,7 +120,7 @@ struct TileArgs {
     const unsigned short *rowslot;   // [U][32] slot of each lane's row disk
     const unsigned short *colslot;   // [U][8]  slot of each column disk
     const unsigned char *mask;       // [U][32] bit j: the pair of register slot j exists
-    const int4 *sv;                  // per slot-var: var, first partial, end, this CTA's partial | owner << 31
+    const int4 *sv;                  // per slot-var: var, holders, unused, owner << 31
     const float *zden;               // per slot-var: number of edges of the variable
     const int *cptr;                 // per slot-var: contributions cptr[i] .. cptr[i + 1] in clist
     const int *clist;                // staging positions (relative to the CTA's staging area)
@@ -125,9 +135,10 @@ struct TileArgs {
     float *xout;                     // x buffer written at checks and at the end
     const float *zin;                // z at the start of the call
     float *zout;                     // z written at checks and at the end
-    float *tpart;                    // [2][ptot] per-CTA partial sums, variable-major,
-                                     // each variable's row padded to a multiple of 4
-    int ptot;
+    long long *acc;                  // [3][ptot] fixed-point sums per variable; pass p adds
+                                     // into buffer p % 3, pass p + 1 reads it, the owners
+                                     // clear it during pass p + 2
+    int ptot;                        // scalar variables
     double *res;                     // [2][2][G] residual partial sums (pri, dual)
     int pair_ebase;                  // storage index of unit 0
     float alpha;
@@ -161,7 +172,8 @@ struct TileInput {
 };
 
 struct TilePlan {
-    int U = 0, W = 0, G = 0, smax = 0, stgmax = 0, svmax = 0, locmax = 0, clmax = 0, ptot = 0;
+    int U = 0, W = 0, G = 0, smax = 0, stgmax = 0, svmax = 0, locmax = 0, clmax = 0;
+    int ptot = 0;                       // accumulators per buffer (scalar variables)
     std::vector<int32_t> pair_pos;      // per disk pair (bucket order): unit * 256 + slot * 32 + lane
     std::vector<TileCta> cta;
     std::vector<uint16_t> rowslot, colslot;
