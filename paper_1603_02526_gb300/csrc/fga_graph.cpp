@@ -143,7 +143,7 @@ struct fga_graph {
     // disk-tile order (zorder 2): the plan and its device copies
     TilePlan tile;
     DevBuf t_cta, t_rowslot, t_colslot, t_mask, t_sv, t_zden, t_cptr, t_clist, t_loc, t_part, t_res, t_dsave;
-    DevBuf t_dres, t_zprev;
+    DevBuf t_dres, t_zprev, t_lres;
     bool tile_resume = false;   // alpha = 1: the last call left its displacements to resume from
     int64_t tile_pair_ebase = 0;
     bool uniform_rho = true, uniform_alpha = true;
@@ -449,6 +449,7 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         CUDA_TRY(cudaMemset(g->t_part.p, 0, g->t_part.bytes));
         CUDA_TRY(g->t_dsave.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
         CUDA_TRY(g->t_dres.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
+        CUDA_TRY(g->t_lres.alloc((size_t)std::max<size_t>(T.loc.size(), 1) * sizeof(float)));
         CUDA_TRY(g->t_zprev.alloc((size_t)std::max<int64_t>(g->nz, 1) * sizeof(float)));
     } else if (g->zorder == 0) {
         // canonical order: per-edge variable ids and positions in the
@@ -1190,6 +1191,7 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     a.u = g->u.as<float>();
     a.dsave = g->t_dsave.as<float>();
     a.dres = g->t_dres.as<float>();
+    a.lres = g->t_lres.as<float>();
     a.zpin = g->t_zprev.as<float>();
     a.zpout = g->t_zprev.as<float>();
     a.resume = g->tile_resume ? 1 : 0;

@@ -49,6 +49,18 @@ namespace fga {
 //  T_FINAL: only the residual and the stored state of the last iteration.
 enum TileMode : int { T_FIRST = 0, T_MID = 1, T_CHK = 2, T_FINAL = 3 };
 
+// One pass: its mode; RELOAD: the previous pass was the call's first (a
+// check reads the stored u again); SAVE: the next pass checks (keep the
+// displacements this pass replaces).  The pass functions are compiled
+// twice: GEN = false for the plain pass (T_MID, neither flag, all folded at
+// compile time, the code of every iteration) and GEN = true for the others,
+// which test the fields at run time -- one copy of the rarely run code
+// rather than one per combination keeps the kernel's instructions few.
+struct PassMode {
+    int mode;
+    bool reload, save;
+};
+
 // ---------------------------------------------------------------------------
 // operators (Appendix A), FP32, one rho; explicit round-to-nearest
 // intrinsics pin every rounding.
@@ -93,6 +105,10 @@ static __device__ __forceinline__ float radius_disp(int type, float n, float p0)
 // ---------------------------------------------------------------------------
 static __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Fire-and-forget integer addition at L2 (no value returned to the thread).
+static __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 static __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
     unsigned long long v;
@@ -227,12 +243,15 @@ static __device__ __forceinline__ void stage_unit(int lane, float ar0, float ar1
 // the pass before stores it to a.dsave (SAVE); when the previous pass was
 // the call's first, the stored u is read again instead (RELOAD).
 // ---------------------------------------------------------------------------
-template <int MODE, bool RELOAD, bool SAVE>
-static __device__ __forceinline__ void tile_unit_a1(const TileArgs &a, int unit, int lane, int rs, unsigned msk,
+template <bool GEN>
+static __device__ __forceinline__ void tile_unit_a1(const TileArgs &a, const PassMode pm, int unit, int lane, int rs, unsigned msk,
                                                     const unsigned (&csp)[4], float (&D)[8][3], const float4 *z4,
                                                     const float4 *zp4, const float4 *y4, const float4 *yp4,
                                                     float *stg_w, double &pri) {
-    constexpr bool CHK = MODE == T_CHK || MODE == T_FINAL;
+    const int MODE = GEN ? pm.mode : (int)T_MID;
+    const bool RELOAD = GEN && pm.reload;
+    const bool SAVE = GEN && pm.save;
+    const bool CHK = MODE == T_CHK || MODE == T_FINAL;
     const size_t ubase = (size_t)a.pair_ebase + (size_t)unit * kUnitEdges + lane;
     const size_t dbase = (size_t)unit * (kUnitEdges / 2) + lane;
     float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zpr = zr, yr = zr, ypr = zr;
@@ -246,7 +265,7 @@ static __device__ __forceinline__ void tile_unit_a1(const TileArgs &a, int unit,
     for (int c = 0; c < 8; ++c) {
         const unsigned slot = col_slot(csp, c);
         const float w = ((msk >> c) & 1u) ? 1.f : 0.f;
-        if constexpr (CHK) {
+        if (CHK) {
             // iteration it-1: x = n^{it-2} + Delta^{it-1}, u = z_prev - z + Delta^{it-1}
             const float4 zc = z4[slot], zpc = zp4[slot];
             const float z[6] = {zr.x, zr.y, zr.z, zc.x, zc.y, zc.z};
@@ -326,10 +345,11 @@ static __device__ __forceinline__ void tile_unit_a1(const TileArgs &a, int unit,
 // ---------------------------------------------------------------------------
 // one unit, any alpha: state u[c][k]; x^{it-1} recomputed from u and z_prev
 // ---------------------------------------------------------------------------
-template <int MODE>
-static __device__ __forceinline__ void tile_unit_u(const TileArgs &a, int unit, int lane, int rs, unsigned msk,
+template <bool GEN>
+static __device__ __forceinline__ void tile_unit_u(const TileArgs &a, const PassMode pm, int unit, int lane, int rs, unsigned msk,
                                                    const unsigned (&csp)[4], float (&u)[8][6], const float4 *z4,
                                                    const float4 *zp4, float *stg_w, double &pri) {
+    const int MODE = GEN ? pm.mode : (int)T_MID;
     const float4 zr = z4[rs];
     float4 zrp = make_float4(0.f, 0.f, 0.f, 0.f);
     if (MODE != T_FIRST) zrp = zp4[rs];
@@ -389,9 +409,10 @@ static __device__ __forceinline__ void tile_unit_u(const TileArgs &a, int unit, 
 // ---------------------------------------------------------------------------
 // walls and radius rewards (one thread each, u in shared memory, any alpha)
 // ---------------------------------------------------------------------------
-template <int MODE>
-static __device__ __forceinline__ void tile_local(const TileArgs &a, const TileLocal &L, float *ul, const float *zt,
+template <bool GEN>
+static __device__ __forceinline__ void tile_local(const TileArgs &a, const PassMode pm, const TileLocal &L, float *ul, const float *zt,
                                                   const float *zpt, float *stg, double &pri) {
+    const int MODE = GEN ? pm.mode : (int)T_MID;
     const float al = a.alpha;
     if (L.type == 1) {
         float u[3], z[3];
@@ -451,16 +472,109 @@ static __device__ __forceinline__ void tile_local(const TileArgs &a, const TileL
     }
 }
 
+// The same for alpha = 1 in displacement form.  A wall's displacement is
+// g (Qx, Qy, -1): its state is g; the linear reward's is the constant
+// w / rho (no state); the area reward's is n / (rho - 1): its state is that
+// value.  ul: [0..2] the u stored at the start of the call (read again by
+// the first check, RELOAD), [3] the state, [4] the state kept for the next
+// check (SAVE).  Check passes store x, u and the state as in tile_unit_a1.
+template <bool GEN>
+static __device__ __forceinline__ void tile_local_a1(const TileArgs &a, const PassMode pm, const TileLocal &L, int li, float *ul,
+                                                     const float *zt, const float *zpt, const float *yt,
+                                                     const float *ypt, float *stg, double &pri) {
+    const int MODE = GEN ? pm.mode : (int)T_MID;
+    const bool RELOAD = GEN && pm.reload;
+    const bool SAVE = GEN && pm.save;
+    const bool CHK = MODE == T_CHK || MODE == T_FINAL;
+    const int o = 4 * L.slot;
+    if (L.type == 1) {
+        const float *p = L.p;
+        if (CHK) {
+            const float g = ul[3];
+            const float dl[3] = {__fmul_rn(g, p[0]), __fmul_rn(g, p[1]), -g};
+            float no[3];
+            if (RELOAD) {
+                #pragma unroll
+                for (int k = 0; k < 3; ++k) no[k] = __fsub_rn(zpt[o + k], ul[k]);
+            } else {
+                const float gp = ul[4];
+                no[0] = __fsub_rn(ypt[o], __fmul_rn(gp, p[0]));
+                no[1] = __fsub_rn(ypt[o + 1], __fmul_rn(gp, p[1]));
+                no[2] = __fadd_rn(ypt[o + 2], gp);
+            }
+            #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float xo = __fadd_rn(no[k], dl[k]);
+                const float uo = __fadd_rn(__fsub_rn(zpt[o + k], zt[o + k]), dl[k]);
+                const float d = __fsub_rn(xo, zt[o + k]);
+                pri += (double)__fmul_rn(d, d);
+                a.xout[L.e0 + k] = xo;
+                a.u[L.e0 + k] = uo;
+            }
+            a.lres[li] = g;
+        }
+        if (MODE == T_FINAL) return;
+        if (SAVE) ul[4] = ul[3];
+        float n[3];
+        if (MODE == T_FIRST) {
+            #pragma unroll
+            for (int k = 0; k < 3; ++k) n[k] = __fsub_rn(zt[o + k], ul[k]);
+        } else {
+            const float g = ul[3];
+            n[0] = __fsub_rn(yt[o], __fmul_rn(g, p[0]));
+            n[1] = __fsub_rn(yt[o + 1], __fmul_rn(g, p[1]));
+            n[2] = __fadd_rn(yt[o + 2], g);
+        }
+        float dl[3];
+        wall_disp(n, p, dl);
+        ul[3] = -dl[2];
+        #pragma unroll
+        for (int k = 0; k < 3; ++k) stg[L.stg + k] = dl[k];
+    } else {
+        const bool quad = L.type == 3;
+        if (CHK) {
+            const float dl = quad ? ul[3] : L.p[0];
+            float no;
+            if (RELOAD) no = __fsub_rn(zpt[o + 2], ul[0]);
+            else no = __fsub_rn(ypt[o + 2], quad ? ul[4] : L.p[0]);
+            const float xo = __fadd_rn(no, dl);
+            const float uo = __fadd_rn(__fsub_rn(zpt[o + 2], zt[o + 2]), dl);
+            const float d = __fsub_rn(xo, zt[o + 2]);
+            pri += (double)__fmul_rn(d, d);
+            a.xout[L.e0] = xo;
+            a.u[L.e0] = uo;
+            a.lres[li] = ul[3];
+        }
+        if (MODE == T_FINAL) return;
+        if (!quad) {
+            stg[L.stg] = L.p[0];
+            return;
+        }
+        if (SAVE) ul[4] = ul[3];
+        const float n = MODE == T_FIRST ? __fsub_rn(zt[o + 2], ul[0]) : __fsub_rn(yt[o + 2], ul[3]);
+        const float dl = __fmul_rn(L.p[0], n);
+        ul[3] = dl;
+        stg[L.stg] = dl;
+    }
+}
+
 // Walls and rewards go to every warp in turn (item i: warp i mod warps,
 // lane i / warps), after the warp's unit.
-template <int MODE>
-static __device__ __forceinline__ void tile_locals(const TileArgs &a, int nloc, const TileLocal *loc, float *uloc,
-                                                   int lane, const float4 *z4, const float4 *zp4, float *stg,
-                                                   double &pri) {
+template <bool GEN, bool A1>
+static __device__ __forceinline__ void tile_locals(const TileArgs &a, const PassMode pm, const TileCta &C, const TileLocal *loc,
+                                                   float *uloc, int lane, const float4 *z4, const float4 *zp4,
+                                                   const float4 *y4, const float4 *yp4, float *stg, double &pri) {
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const float *zt = reinterpret_cast<const float *>(z4);
     const float *zpt = reinterpret_cast<const float *>(zp4);
-    for (int i = lane * nw + warp; i < nloc; i += 32 * nw) tile_local<MODE>(a, loc[i], uloc + 4 * i, zt, zpt, stg, pri);
+    const float *yt = reinterpret_cast<const float *>(y4);
+    const float *ypt = reinterpret_cast<const float *>(yp4);
+    for (int i = lane * nw + warp; i < C.nloc; i += 32 * nw) {
+        if constexpr (A1)
+            tile_local_a1<GEN>(a, pm, loc[i], C.loc0 + i, uloc + 8 * i, zt, zpt, yt, ypt, stg, pri);
+        else
+            tile_local<GEN>(a, pm, loc[i], uloc + 8 * i, zt, zpt, stg, pri);
+    }
 }
 
 // Per-lane state of its pairs, for either form.
@@ -475,11 +589,8 @@ struct PairState<false> {
     float u[8][6];
 };
 
-// LMODE: the walls' and rewards' pass (differs from the pairs' only when a
-// call resumes: the pairs continue from their displacements, the walls and
-// rewards start from their stored u).
-template <int MODE, int LMODE, bool RELOAD, bool SAVE, bool A1>
-static __device__ __forceinline__ void tile_pass(const TileArgs &a, int nloc, const TileLocal *loc, float *uloc,
+template <bool GEN, bool A1>
+static __device__ __forceinline__ void tile_pass(const TileArgs &a, const PassMode pm, const TileCta &C, const TileLocal *loc, float *uloc,
                                                  bool has_unit, int unit, int lane, int rs, unsigned msk,
                                                  const unsigned (&csp)[4], PairState<A1> &ps, const float4 *z4,
                                                  const float4 *zp4, const float4 *y4, const float4 *yp4, float *stg,
@@ -487,11 +598,11 @@ static __device__ __forceinline__ void tile_pass(const TileArgs &a, int nloc, co
     float *stg_w = stg + (threadIdx.x >> 5) * kUnitStage;
     if (has_unit) {
         if constexpr (A1)
-            tile_unit_a1<MODE, RELOAD, SAVE>(a, unit, lane, rs, msk, csp, ps.D, z4, zp4, y4, yp4, stg_w, pri);
+            tile_unit_a1<GEN>(a, pm, unit, lane, rs, msk, csp, ps.D, z4, zp4, y4, yp4, stg_w, pri);
         else
-            tile_unit_u<MODE>(a, unit, lane, rs, msk, csp, ps.u, z4, zp4, stg_w, pri);
+            tile_unit_u<GEN>(a, pm, unit, lane, rs, msk, csp, ps.u, z4, zp4, stg_w, pri);
     }
-    tile_locals<LMODE>(a, nloc, loc, uloc, lane, z4, zp4, stg, pri);
+    tile_locals<GEN, A1>(a, pm, C, loc, uloc, lane, z4, zp4, y4, yp4, stg, pri);
 }
 
 // ---------------------------------------------------------------------------
@@ -575,11 +686,13 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     for (int i = threadIdx.x; i < C.nloc; i += blockDim.x) {
         const TileLocal l = a.loc[C.loc0 + i];
         loc[i] = l;
-        uloc[4 * i] = a.u[l.e0];
+        uloc[8 * i] = a.u[l.e0];
         if (l.type == 1) {
-            uloc[4 * i + 1] = a.u[l.e0 + 1];
-            uloc[4 * i + 2] = a.u[l.e0 + 2];
+            uloc[8 * i + 1] = a.u[l.e0 + 1];
+            uloc[8 * i + 2] = a.u[l.e0 + 2];
         }
+        uloc[8 * i + 3] = (A1 && a.resume) ? a.lres[C.loc0 + i] : 0.f;
+        uloc[8 * i + 4] = 0.f;
     }
     __syncthreads();
 
@@ -602,33 +715,14 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
             else tile_gather<false, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, rb, cb, dual);
         }
         __syncthreads();
-#define TILE_PASS2(M, LM, R, S) \
-    tile_pass<M, LM, R, S, A1>(a, C.nloc, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg, pri)
-#define TILE_PASS(M, R, S) TILE_PASS2(M, M, R, S)
-        if (!pend) {
-            if (res1) {
-                if (save) TILE_PASS2(T_MID, T_FIRST, false, true);
-                else TILE_PASS2(T_MID, T_FIRST, false, false);
-            } else {
-                TILE_PASS(T_FIRST, false, false);
-            }
-        } else if (fin) {
-            if (reload) TILE_PASS(T_FINAL, true, false);
-            else TILE_PASS(T_FINAL, false, false);
-        } else if (chk) {
-            if (reload) {
-                if (save) TILE_PASS(T_CHK, true, true);
-                else TILE_PASS(T_CHK, true, false);
-            } else {
-                if (save) TILE_PASS(T_CHK, false, true);
-                else TILE_PASS(T_CHK, false, false);
-            }
-        } else {
-            if (save) TILE_PASS(T_MID, false, true);
-            else TILE_PASS(T_MID, false, false);
-        }
-#undef TILE_PASS
-#undef TILE_PASS2
+        PassMode pm;
+        pm.mode = !pend ? (res1 ? T_MID : T_FIRST) : fin ? T_FINAL : chk ? T_CHK : T_MID;
+        pm.reload = reload && (chk || fin);
+        pm.save = save;
+        if (pm.mode == T_MID && !pm.save)
+            tile_pass<false, A1>(a, pm, C, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg, pri);
+        else
+            tile_pass<true, A1>(a, pm, C, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg, pri);
         __syncthreads();
         if (!fin) {
             // one partial per (CTA, variable): staged contributions in list
@@ -638,11 +732,22 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
             for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) {
                 const int j1 = cptr[i + 1];
                 float S = 0.f;
-                for (int j = cptr[i]; j < j1; ++j) S = __fadd_rn(S, stg[clist[j]]);
+                // eight list entries, then eight staged values, then the
+                // adds (two dependent loads per eight contributions)
+                for (int j = cptr[i]; j < j1; j += 8) {
+                    int idx[8];
+                    #pragma unroll
+                    for (int t = 0; t < 8; ++t) idx[t] = j + t < j1 ? clist[j + t] : -1;
+                    float v[8];
+                    #pragma unroll
+                    for (int t = 0; t < 8; ++t) v[t] = idx[t] >= 0 ? stg[idx[t]] : 0.f;
+                    #pragma unroll
+                    for (int t = 0; t < 8; ++t) S = __fadd_rn(S, v[t]);
+                }
                 long long q = 0;
                 if (fabsf(S) < kTileFixMax) q = __float2ll_rn(__fmul_rn(S, kTileFixScale));
                 else ovf = true;
-                atomicAdd(dst + sv[i].x, (unsigned long long)q);
+                red_add_u64(dst + sv[i].x, (unsigned long long)q);
             }
             if (ovf) atomicOr(&a.sync->overflow, 1);
         }

@@ -95,7 +95,7 @@ inline __host__ __device__ TileSmem tile_smem_layout(int smax, int svmax, int lo
     L.loc = o;
     o = tile_align16(o + locmax * (int)sizeof(TileLocal));
     L.uloc = o;
-    o = tile_align16(o + locmax * 16);
+    o = tile_align16(o + locmax * 32);
     L.zden = o;
     o = tile_align16(o + svmax * 4);
     L.cptr = o;
@@ -129,6 +129,8 @@ struct TileArgs {
     float *u;                        // per edge (storage order)
     float *dsave;                    // alpha = 1: [U][24][32] displacements kept for the next check
     float *dres;                     // alpha = 1: [U][24][32] displacements of the stored state
+    float *lres;                     // alpha = 1: per wall / reward, its displacement parameter
+                                     // of the stored state
     const float *zpin;               // alpha = 1: z before the stored state (resume)
     float *zpout;                    // alpha = 1: written at checks with the state
     int resume;                      // alpha = 1: dres / zpin hold the state this call starts from

@@ -185,17 +185,26 @@ def test_tile_deterministic():
     assert np.array_equal(a.fga_read_edge_state(_lib.FGA_EDGE_U), b.fga_read_edge_state(_lib.FGA_EDGE_U))
 
 
-def test_tile_area_reward_and_alpha():
-    """The area reward -r^2/2 (rho 25) and a dual step alpha 0.7 through the
-    tile kernel: 200 iterations, z within 1e-4 S of the oracle."""
+@pytest.mark.parametrize("alpha", [1.0, 0.7])
+def test_tile_area_reward_and_alpha(alpha):
+    """The area reward -r^2/2 (rho 25) through the tile kernel, in the
+    displacement form (alpha 1) and the u form (alpha 0.7): 200 iterations
+    in calls of 70, 70 and 60 (resume, a check every 9), z within 1e-4 S of
+    the oracle, and the same bits as one call."""
     p = inputs.packing_problem(30, reward="quad", rho=25.0)
-    p.alpha = 0.7
+    p.alpha = alpha
     g = _tile(p)
     g.fga_iterate(200)
     o = oracle_from_problem(p)
     o.iterate(200)
     S = float(np.max(np.abs(o.z())))
     assert np.max(np.abs(g.fga_read_z() - o.z())) <= 1e-4 * S
+    h = _tile(p)
+    for k in (70, 70, 60):
+        h.fga_iterate(k, check_every=9)
+    assert np.array_equal(g.fga_read_z(), h.fga_read_z())
+    for x, y in zip(_edges(g), _edges(h)):
+        assert np.array_equal(x, y)
 
 
 def test_tile_rejections():
