@@ -34,7 +34,7 @@ SEED = 1000 * 1 + 0       # config index x 1000 + replicate
 BYTES_PER_EDGE_ITER = 20  # algorithmic: read u, read m|x, write u, write m|x, read m (FP32)
 METRIC = "edge-updates/s"
 UNIT = "scalar edge-updates/s"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_packing_n1000_f32.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_tile_packing_n1000_f32.md")
 SWEEP_SOURCES = ["sweep_tile.cu", "tile_internal.h", "fga_tile.cpp", "sweep.cuh", "fga_internal.h"]
 
 
