@@ -36,11 +36,13 @@ def _units():
         ("sweep_f32.cu", nv),
         ("sweep_f64.cu", nv + ["-fmad=false"]),
         ("sweep_tile.cu", nv),
+        ("sweep_hinge.cu", nv),
         ("mpc_batch.cu", nv),
         ("mpc_noalloc.cu", nv),
         ("mlp.cu", nv),
         ("fga_graph.cpp", None),
         ("fga_tile.cpp", None),
+        ("fga_hinge.cpp", None),
         ("fga_batch.cpp", None),
         ("fga_mlp.cpp", None),
     ]

@@ -18,6 +18,7 @@
 #include "fga_internal.h"
 #include "fga_host.h"
 #include "tile_internal.h"
+#include "hinge_internal.h"
 
 using namespace fga;
 
@@ -144,6 +145,11 @@ struct fga_graph {
     TilePlan tile;
     DevBuf t_cta, t_rowslot, t_colslot, t_mask, t_sv, t_zden, t_cptr, t_clist, t_loc, t_part, t_res, t_dsave;
     DevBuf t_dres, t_zprev, t_lres;
+    // hinge bank (zorder 3)
+    HingePlan hinge;
+    HingeInput hin;
+    DevBuf h_cta, h_X, h_meta, h_gsave, h_gres, h_l2save, h_l2res, h_acc;
+    int64_t hinge_e0 = 0, l2_e0 = 0, l2_nf = 0;
     bool tile_resume = false;   // alpha = 1: the last call left its displacements to resume from
     int64_t tile_pair_ebase = 0;
     bool uniform_rho = true, uniform_alpha = true;
@@ -228,7 +234,7 @@ extern "C" int fga_set_option(fga_graph *g, int32_t option, int64_t value) {
     if (g->finalized) return fail(FGA_ESTATE, "fga_set_option: graph already finalized");
     switch (option) {
     case FGA_OPT_ZORDER:
-        if (value < 0 || value > 2) return fail(FGA_EINVAL, "FGA_OPT_ZORDER must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(FGA_EINVAL, "FGA_OPT_ZORDER must be 0, 1, 2 or 3");
         g->zorder = (int)value;
         return FGA_OK;
     case FGA_OPT_STORE_M:
@@ -434,7 +440,21 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
     // 64 spare elements: a bulk copy may read up to 16 bytes past the last edge
     const size_t eb = (size_t)(std::max<int64_t>(ES, 1) + 64) * sizeof(R);
     (void)E;
-    if (g->zorder == 2) {
+    if (g->zorder == 3) {
+        const HingePlan &H = g->hinge;
+        if ((rc = upload_vec(g->h_cta, H.cta))) return rc;
+        if ((rc = upload_vec(g->h_X, H.X))) return rc;
+        if ((rc = upload_vec(g->h_meta, H.meta))) return rc;
+        const size_t n = (size_t)std::max<int64_t>(g->hin.N, 1) * sizeof(float);
+        CUDA_TRY(g->h_gsave.alloc(2 * n));
+        CUDA_TRY(g->h_gres.alloc(n));
+        CUDA_TRY(g->h_l2save.alloc((size_t)kHingeMaxL2 * kHingeD * sizeof(float)));
+        CUDA_TRY(g->h_l2res.alloc((size_t)kHingeMaxL2 * kHingeD * sizeof(float)));
+        CUDA_TRY(cudaMemset(g->h_l2res.p, 0, g->h_l2res.bytes));
+        CUDA_TRY(g->h_acc.alloc((size_t)3 * (g->hin.D + 1) * kHingeAccStride * sizeof(long long)));
+        CUDA_TRY(cudaMemset(g->h_acc.p, 0, g->h_acc.bytes));
+        CUDA_TRY(g->t_zprev.alloc((size_t)std::max<int64_t>(g->nz, 1) * sizeof(float)));
+    } else if (g->zorder == 2) {
         const TilePlan &T = g->tile;
         if ((rc = upload_vec(g->t_cta, T.cta))) return rc;
         if ((rc = upload_vec(g->t_rowslot, T.rowslot))) return rc;
@@ -778,6 +798,86 @@ static int try_tile_plan(fga_graph *g, std::string &why) {
     return 0;
 }
 
+// Hinge bank: checks that the graph is a linear SVM the hinge kernel can
+// run (FP32, one rho, alpha = 1, m not kept, hinge factors on one shared
+// (w, b) and L2 factors on that w only) and builds the plan.  0: planned;
+// 1: not suitable (reason in `why`); < 0: error.
+static int try_hinge_plan(fga_graph *g, std::string &why) {
+    if (!g->rho_c.empty() || !g->alpha_c.empty() || g->alpha_u != 1.0) {
+        why = "rho or alpha set per edge, or alpha other than 1";
+        return 1;
+    }
+    if (g->store_m == 1) {
+        why = "m is kept (FGA_OPT_STORE_M)";
+        return 1;
+    }
+    const Bucket *hb = nullptr, *lb = nullptr;
+    for (const Bucket &bk : g->buckets) {
+        if (bk.type == FGA_SVM_HINGE && !hb) hb = &bk;
+        else if (bk.type == FGA_SVM_L2 && !lb) lb = &bk;
+        else {
+            why = "factor types other than one hinge bank and its L2 factors";
+            return 1;
+        }
+    }
+    if (!hb) {
+        why = "no hinge factors";
+        return 1;
+    }
+    HingeInput &in = g->hin;
+    in = HingeInput();
+    const int D = hb->dims[0];
+    in.D = D;
+    in.N = (int64_t)hb->members.size();
+    int64_t w = -1, b = -1;
+    try {
+        in.X.resize((size_t)in.N * D);
+        in.yl.resize((size_t)in.N);
+        in.cl.resize((size_t)in.N);
+        for (int64_t f = 0; f < in.N; ++f) {
+            const FactorBatch &fb = g->batches[hb->members[f].first];
+            const int64_t fi = hb->members[f].second;
+            const int64_t *v = fb.vars.data() + fi * fb.nv;
+            if (f == 0) {
+                w = v[0];
+                b = v[1];
+            } else if (v[0] != w || v[1] != b) {
+                why = "hinge factors on different variables";
+                return 1;
+            }
+            const double *pp = fb.param(fi);
+            for (int j = 0; j < D; ++j) in.X[(size_t)f * D + j] = (float)pp[j];
+            in.yl[f] = (float)pp[D];
+            in.cl[f] = (float)pp[D + 1];
+        }
+        if (lb) {
+            for (int64_t f = 0; f < (int64_t)lb->members.size(); ++f) {
+                const FactorBatch &fb = g->batches[lb->members[f].first];
+                const int64_t fi = lb->members[f].second;
+                if (fb.vars[fi * fb.nv] != w) {
+                    why = "an L2 factor on a variable other than the hinges' w";
+                    return 1;
+                }
+                in.lam.push_back((float)fb.param(fi)[0]);
+            }
+        }
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
+    }
+    in.vw = (int)g->voff[w];
+    in.vb = (int)g->voff[b];
+    in.rho = g->rho_u;
+    CUDA_TRY(cudaDeviceGetAttribute(&in.sms, cudaDevAttrMultiProcessorCount, g->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&in.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
+    int rc;
+    try {
+        rc = hinge_plan(in, g->hinge, why);
+    } catch (...) {
+        return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
+    }
+    return rc;
+}
+
 extern "C" int fga_finalize(fga_graph *g) {
     if (!g) return fail(FGA_EINVAL, "fga_finalize: NULL graph");
     if (g->finalized) return fail(FGA_ESTATE, "fga_finalize: graph already finalized");
@@ -835,7 +935,19 @@ extern "C" int fga_finalize(fga_graph *g) {
         else if (zreq == 2)
             return fail(FGA_EINVAL, "fga_finalize: the disk-tile order does not apply: %s", why.c_str());
     }
+    // 1a'. hinge bank for a linear SVM (FP32 default when it qualifies)
+    if (g->precision == FGA_F32 && g->zorder != 2 && (zreq < 0 || zreq == 3)) {
+        std::string why;
+        const int r = try_hinge_plan(g, why);
+        if (r < 0) return r;
+        if (r == 0) g->zorder = 3;
+        else if (zreq == 3)
+            return fail(FGA_EINVAL, "fga_finalize: the hinge-bank order does not apply: %s", why.c_str());
+    }
+    if (zreq == 3 && g->precision != FGA_F32)
+        return fail(FGA_EINVAL, "fga_finalize: FGA_OPT_ZORDER 3 (hinge bank) needs FGA_F32");
     const bool tile = g->zorder == 2;
+    const bool hinge = g->zorder == 3;
     const int64_t tile_span = (int64_t)g->tile.U * kUnitEdges;
     // 1b. fast order: inside a bucket, factors that touch nearby variables
     // are stored together (stable sort by the blocks of the first and last
@@ -941,7 +1053,19 @@ extern "C" int fga_finalize(fga_graph *g) {
         g->blk = g->tile.W * 32;
         g->smem = tile_smem_bytes(g->tile);
     }
-    const int bps = tile ? 1
+    if (hinge) {
+        g->blk = kHingeWarps * 32;
+        g->smem = hinge_smem_bytes(g->hinge.rows_max);
+        for (const Bucket &bk : g->buckets) {
+            if (bk.type == FGA_SVM_HINGE) g->hinge_e0 = bk.ebase;
+            if (bk.type == FGA_SVM_L2) {
+                g->l2_e0 = bk.ebase;
+                g->l2_nf = (int64_t)bk.members.size();
+            }
+        }
+        if (es > (int64_t)INT32_MAX / 2) return fail(FGA_EINVAL, "fga_finalize: too many edges for the hinge bank");
+    }
+    const int bps = (tile || hinge) ? 1
                     : g->precision == FGA_F32 ? sweep_max_blocks_per_sm<float>(g->blk, g->smem, g->kind)
                                               : sweep_max_blocks_per_sm<double>(g->blk, g->smem, g->kind);
     if (bps < 1) return fail(FGA_ECUDA, "fga_finalize: the sweep kernel cannot be resident at %d threads", g->blk);
@@ -971,14 +1095,16 @@ extern "C" int fga_finalize(fga_graph *g) {
     int64_t work;
     if (tile)
         work = (int64_t)g->tile.G * g->blk;
+    else if (hinge)
+        work = (int64_t)g->hinge.G * g->blk;
     else if (g->zorder == 1)
         work = std::max<int64_t>(std::max<int64_t>((int64_t)g->nchunks * g->blk, g->n_small),
                                  (int64_t)g->n_witems * 32);
     else
         work = std::max<int64_t>(g->nitems_f, Z);
     g->grid = (int)std::max<int64_t>(1, std::min<int64_t>(full, (work + g->blk - 1) / g->blk));
-    if (tile) {
-        g->grid = g->tile.G;
+    if (tile || hinge) {
+        g->grid = tile ? g->tile.G : g->hinge.G;
         CUDA_TRY(g->t_res.alloc((size_t)4 * g->grid * sizeof(double)));
         CUDA_TRY(cudaMemset(g->t_res.p, 0, g->t_res.bytes));
     }
@@ -1263,6 +1389,101 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     return FGA_OK;
 }
 
+// Hinge bank: one cooperative launch for the whole call (FP32, alpha = 1).
+static int iterate_hinge(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
+    const HingePlan &H = g->hinge;
+    const HingeInput &in = g->hin;
+    HingeArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.G = H.G;
+    a.N = (int)in.N;
+    a.D = in.D;
+    a.nl2 = (int)in.lam.size();
+    a.cta = g->h_cta.as<HingeCta>();
+    a.X = g->h_X.as<float>();
+    a.meta = g->h_meta.as<float4>();
+    for (int f = 0; f < a.nl2; ++f) a.lam[f] = in.lam[f];
+    a.rho = (float)g->rho_u;
+    a.inv_rho = (float)(1.0 / g->rho_u);
+    a.deg_w = (int)(in.N + (int64_t)in.lam.size());
+    a.deg_b = (int)in.N;
+    a.rows_max = H.rows_max;
+    a.u = g->u.as<float>();
+    a.xw = g->xpar ^ 1;
+    a.zw = g->zpar ^ 1;
+    a.xout = g->x[a.xw].as<float>();
+    a.zin = g->z[g->zpar].as<float>();
+    a.zout = g->z[a.zw].as<float>();
+    a.zpin = g->t_zprev.as<float>();
+    a.zpout = g->t_zprev.as<float>();
+    a.vw = in.vw;
+    a.vb = in.vb;
+    a.hb_e0 = (int)g->hinge_e0;
+    a.l2_e0 = (int)g->l2_e0;
+    a.l2_nf = (int)g->l2_nf;
+    a.acc = g->h_acc.as<long long>();
+    a.gsave = g->h_gsave.as<float>();
+    a.gres = g->h_gres.as<float>();
+    a.l2save = g->h_l2save.as<float>();
+    a.l2res = g->h_l2res.as<float>();
+    a.resume = g->tile_resume ? 1 : 0;
+    a.res = g->t_res.as<double>();
+    a.E = g->ne;
+    a.ctl = g->ctl.as<Ctl>();
+    a.sync = g->bar.as<TileSync>();
+    a.k0 = g->iters_done;
+    a.K = o.max_iters;
+    a.check_every = o.check_every;
+    a.tol_pri = o.tol_pri;
+    a.tol_dual = o.tol_dual;
+    a.timeout_ns = o.barrier_timeout_ns > 0 ? o.barrier_timeout_ns : 2000000000LL;
+    a.skip_block = o.fault_skip_block;
+    cudaStream_t s = g->stream;
+    if (a.K <= 0) {
+        res.iters = 0;
+        res.r_pri = g->last_rp;
+        res.r_dual = g->last_rd;
+        res.status = FGA_OK;
+        res.ms = 0.f;
+        return FGA_OK;
+    }
+    CUDA_TRY(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), s));
+    CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
+    CUDA_TRY(cudaMemsetAsync(g->h_acc.p, 0, g->h_acc.bytes, s));   // the fixed-point accumulators
+    CUDA_TRY(cudaMemcpyAsync(a.zout, a.zin, (size_t)g->nz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaEventRecord(g->ev0, s));
+    CUDA_TRY(hinge_sweep_launch(a, g->smem, s));
+    CUDA_TRY(cudaEventRecord(g->ev1, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    Ctl c;
+    TileSync b;
+    CUDA_TRY(cudaMemcpy(&c, g->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&b, g->bar.p, sizeof b, cudaMemcpyDeviceToHost));
+    res.ms = ms;
+    if (b.error) {
+        g->initialized = false;
+        res.iters = 0;
+        res.r_pri = res.r_dual = std::numeric_limits<double>::quiet_NaN();
+        res.status = b.error;
+        return fail(b.error, "fga_iterate: a grid-wide wait timed out (status %d)", b.error);
+    }
+    if (!c.done) return fail(FGA_ECUDA, "fga_iterate: the sweep ended without reporting");
+    g->iters_done += c.iters;
+    g->xpar = c.xpar;
+    g->zpar = c.zpar;
+    g->last_rp = c.r_pri;
+    g->last_rd = c.r_dual;
+    g->tile_resume = true;
+    res.iters = c.iters;
+    res.r_pri = c.r_pri;
+    res.r_dual = c.r_dual;
+    res.status = c.status;
+    if (c.status == FGA_ENONFINITE) return fail(FGA_ENONFINITE, "fga_iterate: residual became non-finite");
+    return FGA_OK;
+}
+
 template <typename R>
 static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
     SweepArgs<R> a;
@@ -1346,14 +1567,15 @@ extern "C" int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_res
         return fail(FGA_EINVAL, "fga_iterate: bad options");
     if (opts->fault_skip_block >= 0 && !opts->fused)
         return fail(FGA_EINVAL, "fga_iterate: fault_skip_block needs the fused kernel");
-    if (g->zorder == 2 && !opts->fused)
-        return fail(FGA_EINVAL, "fga_iterate: the disk-tile order runs as one persistent launch (fused = 1); "
-                                "set FGA_OPT_ZORDER 1 for one launch per phase");
+    if ((g->zorder == 2 || g->zorder == 3) && !opts->fused)
+        return fail(FGA_EINVAL, "fga_iterate: the disk-tile and hinge-bank orders run as one persistent launch "
+                                "(fused = 1); set FGA_OPT_ZORDER 1 for one launch per phase");
     int rc = set_device(g);
     if (rc) return rc;
     fga_iter_result r;
     std::memset(&r, 0, sizeof r);
     rc = g->zorder == 2                ? iterate_tile(g, *opts, r)
+         : g->zorder == 3              ? iterate_hinge(g, *opts, r)
          : g->precision == FGA_F32 ? iterate_typed<float>(g, *opts, r)
                                    : iterate_typed<double>(g, *opts, r);
     *result = r;   // also on timeout / non-finite, so the caller sees the status
@@ -1367,7 +1589,7 @@ extern "C" int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n) {
     info[1] = g->blk;
     info[2] = g->smem;
     info[3] = g->bps;
-    info[4] = g->zorder == 1 ? g->nchunks : g->zorder == 2 ? g->tile.U : 0;
+    info[4] = g->zorder == 1 ? g->nchunks : g->zorder == 2 ? g->tile.U : g->zorder == 3 ? g->hinge.G : 0;
     info[5] = (int64_t)g->buckets.size();
     if (n >= 7) info[6] = g->zorder;
     return FGA_OK;
