@@ -35,7 +35,7 @@ BYTES_PER_EDGE_ITER = 20  # algorithmic: read u, read m|x, write u, write m|x, r
 METRIC = "edge-updates/s"
 UNIT = "scalar edge-updates/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_tile_packing_n1000_f32.md")
-SWEEP_SOURCES = ["sweep_tile.cu", "tile_internal.h", "fga_tile.cpp", "sweep.cuh", "fga_internal.h"]
+SWEEP_SOURCES = ["sweep_tile.cu", "tile_internal.h", "fga_tile.cpp", "persist.cuh", "sweep.cuh", "fga_internal.h"]
 
 
 def _peaks():
@@ -310,10 +310,18 @@ def run_extras(log=None):
     g.fga_iterate(50, check_every=50)
     g.fga_init(p.z0)
     r = g.fga_iterate(50000, 1e-4, 1e-4, check_every=10)
+    peak, peak_kind = _peaks()
+    # algorithmic bytes per iteration: 20 B per scalar edge plus the 4 B data
+    # value of every w edge
+    svm_bytes = 20 * p.num_edges + 4 * 100000 * 64
     out["svm"] = {"workload": "soft-margin SVM, 100,000 points x 64, hinge + L2 (lambda 1e-3), rho 1, FP32, "
                               "residual 1e-4 checked every 10", "scalar_edges": p.num_edges, "iters": r["iters"],
                   "status": r["status"], "ms": r["ms"],
-                  "edge_updates_per_s": p.num_edges * r["iters"] / (r["ms"] * 1e-3)}
+                  "edge_updates_per_s": p.num_edges * r["iters"] / (r["ms"] * 1e-3),
+                  "kernel": "k_hinge_sweep" if g.fga_launch_info()["zorder"] == 3 else "k_sweep_persistent<float>",
+                  "algorithmic_bytes_per_iter": svm_bytes,
+                  "algorithmic_gbs": svm_bytes * r["iters"] / (r["ms"] * 1e-3) / 1e9,
+                  "frac_of_hbm": svm_bytes * r["iters"] / (r["ms"] * 1e-3) / 1e9 / peak, "peak_kind": peak_kind}
     del g
     # batched ragged MPC
     d = inputs.mpc_batch_inputs(4096, seed=4000)
@@ -328,11 +336,20 @@ def run_extras(log=None):
         res = b.fga_mpc_batch_solve(20000, tol=1e-4, use_graph=True)
         times.append(res["ms"])
     it = b.fga_mpc_batch_read()["iters"]
+    # the dynamics operator is a 28 x 28 matrix-vector product per factor
+    # (T per instance): the FP32 FMA count of a solve, against the SMs' FMA
+    # rate at the maximum SM clock
+    fmas = float(np.sum(it.astype(np.float64) * d["T"].astype(np.float64))) * 28 * 28
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fma_peak = sms * 128 * 2070e6
     out["mpc_batch"] = {"workload": "4096 linear MPC instances, nx 12, nu 4, horizons U{10..50}, one system each, "
                                     "box |u| <= 1, FP32 messages, FP64 residual 1e-4, one CUDA-graph launch",
                         "solves_per_s": 4096 / (min(times) * 1e-3), "ms": min(times), "threads": th,
                         "check_every": ce, "iters_mean": float(it.mean()), "iters_p50": float(np.median(it)),
-                        "iters_p99": float(np.percentile(it, 99)), "converged": res["n_converged"]}
+                        "iters_p99": float(np.percentile(it, 99)), "converged": res["n_converged"],
+                        "dynamics_fma_per_s": fmas / (min(times) * 1e-3),
+                        "frac_of_fp32_fma_peak": fmas / (min(times) * 1e-3) / fma_peak,
+                        "fma_peak_basis": "%d SMs x 128 lanes x 2070 MHz" % sms}
     del b
     # learned warm start
     t0 = time.perf_counter()
@@ -357,12 +374,16 @@ def run_extras(log=None):
 
 def run_profile(args):
     """One warm-up and one solve of --profile-iters iterations (the workload
-    of the benchmark at a length that suits an ncu capture)."""
+    of the benchmark, or with --profile-workload svm the SVM of the extras,
+    at a length that suits an ncu capture)."""
     import torch
     from paper_1603_02526_gb300 import build, inputs, _lib
     from paper_1603_02526_gb300.graph import graph_from_problem
     build.build()
-    p = inputs.packing_problem(N_DISKS, seed=SEED)
+    if args.profile_workload == "svm":
+        p = inputs.svm_problem(100000, 64, seed=3000)
+    else:
+        p = inputs.packing_problem(N_DISKS, seed=SEED)
     opts = {_lib.FGA_OPT_STORE_M: 0}
     if args.zorder is not None:
         opts[_lib.FGA_OPT_ZORDER] = args.zorder
@@ -385,7 +406,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the packing sweep (no SVM / MPC / warm start)")
-    ap.add_argument("--zorder", type=int, default=None, help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 tiles)")
+    ap.add_argument("--zorder", type=int, default=None,
+                    help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 disk tiles, 3 hinge bank)")
+    ap.add_argument("--profile-workload", default="packing", choices=["packing", "svm"])
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")
     args = ap.parse_args()
