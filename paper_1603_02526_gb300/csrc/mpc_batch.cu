@@ -86,21 +86,34 @@ __device__ __forceinline__ int var_edges(const Shape &g, int b, int *ed) {
     return 3;
 }
 
+// Deterministic block sums of two doubles per thread (fixed shuffle tree,
+// then warps in order), broadcast to every thread; red holds 2 x 33 doubles.
 template <int NT>
-__device__ __forceinline__ double block_sum_bcast(double v, double *red) {
+__device__ __forceinline__ void block_sum2_bcast(double &v0, double &v1, double *red) {
     #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
     const int w = threadIdx.x >> 5;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < NT / 32; ++i) t += red[i];
-        red[32] = t;
+    if ((threadIdx.x & 31) == 0) {
+        red[w] = v0;
+        red[33 + w] = v1;
     }
     __syncthreads();
-    return red[32];
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int i = 0; i < NT / 32; ++i) {
+            t0 += red[i];
+            t1 += red[33 + i];
+        }
+        red[32] = t0;
+        red[65] = t1;
+    }
+    __syncthreads();
+    v0 = red[32];
+    v1 = red[65];
 }
 
 }  // namespace
@@ -112,14 +125,17 @@ int mpc_smem_bytes(int rsize, int nx, int nu, int tmax, int threads) {
     const int V = (nx + nu) * tmax + nx;
     int b = (3 * E + V + A * (A + 1) + 2 * nx + nu) * rsize;
     b = (b + 15) & ~15;
-    return b + 40 * (int)sizeof(double);
+    return b + 72 * (int)sizeof(double);
 }
 
-template <typename R, int NT>
+// NXC, NUC: the state and input sizes when known at compile time (the
+// index arithmetic then divides by constants and the dynamics rows unroll),
+// 0 for sizes given at run time.
+template <typename R, int NT, int NXC, int NUC>
 __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_k;
-    const int nx = a.nx, nu = a.nu, A = 2 * nx + nu, LP = A + 1;
+    const int nx = NXC ? NXC : a.nx, nu = NUC ? NUC : a.nu, A = 2 * nx + nu, LP = A + 1;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_k = (int)atomicAdd(a.queue, 1u);
@@ -161,25 +177,31 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
         double dual = 0.0;               // this thread's share of the last checked dual residual
         bool pend = a.first_pending != 0;
         const long long K = a.max_iters;
+        const int ce = a.check_every;
+        int rm = 1 % ce;   // it mod check_every, kept by counting (no 64-bit division per iteration)
+        int rm_prev = 0;   // (it - 1) mod check_every
         for (long long it = 1; K > 0 && it <= K + 1; ++it) {
             const bool last = it == K + 1;
-            const bool chk = pend && (((it - 1) % a.check_every) == 0 || last);
-            // F1: u-update of iteration it-1, n-update
-            double pri = 0.0;
+            const bool chk = pend && (rm_prev == 0 || last);
+            // F1: u-update of iteration it-1, n-update.  The thread's
+            // squared differences are summed in the working precision, the
+            // threads' sums in FP64 (the FP64 pipe is narrow on this part).
+            R pri_r = R(0);
             for (int e = threadIdx.x; e < g.E; e += NT) {
                 const R zb = z[edge_var(g, e)];
                 R ue = u[e];
                 if (pend) {
                     const R d = x[e] - zb;
-                    if (chk) pri += (double)d * (double)d;
+                    if (chk) pri_r += d * d;
                     ue = ue + alpha * d;
                     u[e] = ue;
                 }
                 nb[e] = zb - ue;
             }
+            double pri = (double)pri_r;
             if (chk) {
-                const double sp = block_sum_bcast<NT>(pri, red);
-                const double sd = block_sum_bcast<NT>(dual, red);
+                double sp = pri, sd = dual;
+                block_sum2_bcast<NT>(sp, sd, red);
                 rp = sqrt(sp / E);
                 rd = sqrt(sd / E);
                 const bool finite = isfinite(rp) && isfinite(rd);
@@ -202,6 +224,7 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
                     const R *n = nb + g.dyn(t);
                     const R *Pr = P + row * LP;
                     R acc = R(0);
+                    #pragma unroll
                     for (int j = 0; j < A; ++j) acc += Pr[j] * n[j];
                     x[g.dyn(t) + row] = acc;
                 } else {
@@ -229,8 +252,8 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
             }
             __syncthreads();
             // Z: rho-weighted mean over each variable's edges
-            const bool chkz = (it % a.check_every) == 0 || it == K;
-            dual = 0.0;
+            const bool chkz = rm == 0 || it == K;
+            R dual_r = R(0);
             for (int b = threadIdx.x; b < g.V; b += NT) {
                 int ed[3];
                 const int ne = var_edges(g, b, ed);
@@ -243,11 +266,14 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
                 const R znew = S / Rs;
                 z[b] = znew;
                 if (chkz) {
-                    const double dz = (double)znew - (double)zold;
-                    dual += (double)ne * (double)rho * (double)rho * dz * dz;
+                    const R dz = znew - zold;
+                    dual_r += (R)ne * rho * rho * dz * dz;
                 }
             }
+            dual = (double)dual_r;
             pend = true;
+            rm_prev = rm;
+            rm = rm + 1 == ce ? 0 : rm + 1;
             __syncthreads();
         }
         // store the state of the instance
@@ -267,22 +293,40 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
 }
 
 template <typename R>
-cudaError_t mpc_launch(const MpcArgs<R> &a, int threads, int grid, int smem, cudaStream_t s) {
-    if (threads == 64) k_mpc_batch<R, 64><<<grid, 64, smem, s>>>(a);
-    else if (threads == 128) k_mpc_batch<R, 128><<<grid, 128, smem, s>>>(a);
-    else k_mpc_batch<R, 256><<<grid, 256, smem, s>>>(a);
-    return cudaGetLastError();
+static const void *mpc_kernel(int threads, bool fixed) {
+    if (fixed)
+        return threads == 64    ? (const void *)k_mpc_batch<R, 64, 12, 4>
+               : threads == 128 ? (const void *)k_mpc_batch<R, 128, 12, 4>
+                                : (const void *)k_mpc_batch<R, 256, 12, 4>;
+    return threads == 64    ? (const void *)k_mpc_batch<R, 64, 0, 0>
+           : threads == 128 ? (const void *)k_mpc_batch<R, 128, 0, 0>
+                            : (const void *)k_mpc_batch<R, 256, 0, 0>;
 }
 
 template <typename R>
+cudaError_t mpc_launch(const MpcArgs<R> &a, int threads, int grid, int smem, cudaStream_t s) {
+    // the benchmark's sizes (12 states, 4 inputs) have their own instance
+    const bool fixed = a.nx == 12 && a.nu == 4;
+    const void *fn = mpc_kernel<R>(threads, fixed);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem, s);
+}
+
+// Resident CTAs per SM, the smaller of the two instances' (the grid takes
+// work from a counter, so a grid larger than the resident one only waits).
+template <typename R>
 int mpc_max_blocks_per_sm(int threads, int smem) {
-    const void *fn = threads == 64 ? (const void *)k_mpc_batch<R, 64>
-                     : threads == 128 ? (const void *)k_mpc_batch<R, 128>
-                                      : (const void *)k_mpc_batch<R, 256>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, (size_t)smem) != cudaSuccess) return 0;
-    return n;
+    int best = -1;
+    for (bool fixed : {true, false}) {
+        const void *fn = mpc_kernel<R>(threads, fixed);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, (size_t)smem) != cudaSuccess) return 0;
+        best = best < 0 ? n : (n < best ? n : best);
+    }
+    return best;
 }
 
 // ---------------------------------------------------------------------------
