@@ -343,11 +343,16 @@ int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t nx, int32_t 
 
 /* ==========================================================================
  * Learned warm start: a ReLU MLP in -> h1 -> h2 -> out, BF16 weights and
- * activations on tensor cores with FP32 accumulation, FP32 master weights
- * and Adam (beta 0.9, 0.999, eps 1e-8), MSE loss on standardised targets.
- * Not in the paper; it supplies fga_mpc_batch_warm_start's prediction.
- * Parameters are packed as W1 (h1 x in, row-major), b1, W2 (h2 x h1), b2,
- * W3 (out x h2), b3.  h1, h2, out and every batch: multiples of 8.
+ * activations on the tcgen05 tensor cores with FP32 accumulation in tensor
+ * memory, FP32 master weights and Adam (beta 0.9, 0.999, eps 1e-8), MSE loss
+ * on standardised targets.  Not in the paper; it supplies
+ * fga_mpc_batch_warm_start's prediction.  Parameters are packed as W1 (h1 x
+ * in, row-major), b1, W2 (h2 x h1), b2, W3 (out x h2), b3.  h1, h2, out and
+ * every batch: multiples of 8.  Every wait inside a GEMM is bounded (about
+ * one second); a call that synchronises (fga_mlp_forward,
+ * fga_mlp_gradients, fga_mlp_train_step with a loss) returns FGA_ETIMEOUT
+ * if a GEMM since the previous such call gave up, and its outputs are then
+ * not valid.
  * ========================================================================== */
 typedef struct fga_mlp fga_mlp; /* opaque, library-owned */
 

@@ -77,6 +77,7 @@ struct fga_mlp {
     int in = 0, in_pad = 0, h1 = 0, h2 = 0, out = 0, max_batch = 0;
     Layer L[3];
     DBuf xb, a1, a2, y, dyf, dyb, d2, d1, loss_part, mean, stdv;
+    DBuf err;                 // int: a tensor-core wait of a GEMM timed out
     bool normalized = false;
     long long step = 0;
     int nparts = 256;
@@ -137,6 +138,7 @@ extern "C" int fga_mlp_create(fga_mlp **outp, int32_t in, int32_t h1, int32_t h2
     MCUDA(m->loss_part.alloc((size_t)m->nparts * 8));
     MCUDA(m->mean.alloc((size_t)out * 4));
     MCUDA(m->stdv.alloc((size_t)out * 4));
+    MCUDA(m->err.alloc(sizeof(int)));
     // He initialisation (seeded), zero biases, zero padding columns
     Rng rng{seed};
     int dims[3][2] = {{h1, in}, {h2, h1}, {out, h2}};
@@ -225,10 +227,23 @@ extern "C" int fga_mlp_get_normalization(fga_mlp *m, float *mean, float *stdv) {
     return FGA_OK;
 }
 
-static GemmEpi epi0() {
+static GemmEpi epi0(fga_mlp *m) {
     GemmEpi e;
     std::memset(&e, 0, sizeof e);
+    e.err = m->err.as<int>();
     return e;
+}
+
+// After a stream synchronisation: FGA_ETIMEOUT (and the word cleared) if a
+// GEMM since the last check gave up waiting for its tensor-core work.
+static int check_gemm_err(fga_mlp *m) {
+    int h = 0;
+    MCUDA(cudaMemcpy(&h, m->err.p, sizeof h, cudaMemcpyDeviceToHost));
+    if (h) {
+        MCUDA(cudaMemset(m->err.p, 0, sizeof(int)));
+        return mfail(FGA_ETIMEOUT, "MLP GEMM: a tensor-core wait timed out; outputs are not valid");
+    }
+    return FGA_OK;
 }
 
 // forward through the three layers; last = output epilogue
@@ -236,19 +251,19 @@ static int forward(fga_mlp *m, const float *X, int B, int last_epi, float *yout)
     cudaStream_t s = m->stream;
     const __nv_bfloat16 *xb = m->xb.as<__nv_bfloat16>();
     MCUDA(mlp_to_bf16_pad(X, B, m->in, m->in_pad, m->xb.as<__nv_bfloat16>(), s));
-    GemmEpi e = epi0();
+    GemmEpi e = epi0(m);
     e.bias = m->L[0].b.as<float>();
     e.outb = m->a1.as<__nv_bfloat16>();
     e.ldc = m->h1;
     MCUDA(mlp_gemm(3, EPI_BIAS_RELU, B, m->h1, m->in_pad, xb, m->in_pad, m->L[0].wb.as<__nv_bfloat16>(), m->in_pad,
                    e, s));
-    e = epi0();
+    e = epi0(m);
     e.bias = m->L[1].b.as<float>();
     e.outb = m->a2.as<__nv_bfloat16>();
     e.ldc = m->h2;
     MCUDA(mlp_gemm(3, EPI_BIAS_RELU, B, m->h2, m->h1, m->a1.as<__nv_bfloat16>(), m->h1,
                    m->L[1].wb.as<__nv_bfloat16>(), m->h1, e, s));
-    e = epi0();
+    e = epi0(m);
     e.bias = m->L[2].b.as<float>();
     e.scale = m->stdv.as<float>();
     e.shift = m->mean.as<float>();
@@ -269,25 +284,25 @@ static int backward(fga_mlp *m, const float *X, const float *T, int B, double *l
                   m->loss_part.as<double>(), m->nparts, s));
     const __nv_bfloat16 *dyb = m->dyb.as<__nv_bfloat16>();
     // layer 3
-    GemmEpi e = epi0();
+    GemmEpi e = epi0(m);
     e.outf = m->L[2].gw.as<float>();
     e.ldc = m->h2;
     MCUDA(mlp_gemm(0, EPI_STORE, m->out, m->h2, B, dyb, m->out, m->a2.as<__nv_bfloat16>(), m->h2, e, s));
     MCUDA(mlp_colsum_f32(m->dyf.as<float>(), B, m->out, m->L[2].gb.as<float>(), s));
-    e = epi0();
+    e = epi0(m);
     e.mask = m->a2.as<__nv_bfloat16>();
     e.ldm = m->h2;
     e.outb = m->d2.as<__nv_bfloat16>();
     e.ldc = m->h2;
     MCUDA(mlp_gemm(3, EPI_RELU_MASK, B, m->h2, m->out, dyb, m->out, m->L[2].wt.as<__nv_bfloat16>(), m->out, e, s));
     // layer 2
-    e = epi0();
+    e = epi0(m);
     e.outf = m->L[1].gw.as<float>();
     e.ldc = m->h1;
     MCUDA(mlp_gemm(0, EPI_STORE, m->h2, m->h1, B, m->d2.as<__nv_bfloat16>(), m->h2, m->a1.as<__nv_bfloat16>(), m->h1,
                    e, s));
     MCUDA(mlp_colsum_bf16(m->d2.as<__nv_bfloat16>(), B, m->h2, m->L[1].gb.as<float>(), s));
-    e = epi0();
+    e = epi0(m);
     e.mask = m->a1.as<__nv_bfloat16>();
     e.ldm = m->h1;
     e.outb = m->d1.as<__nv_bfloat16>();
@@ -295,7 +310,7 @@ static int backward(fga_mlp *m, const float *X, const float *T, int B, double *l
     MCUDA(mlp_gemm(3, EPI_RELU_MASK, B, m->h1, m->h2, m->d2.as<__nv_bfloat16>(), m->h2, m->L[1].wt.as<__nv_bfloat16>(),
                    m->h2, e, s));
     // layer 1
-    e = epi0();
+    e = epi0(m);
     e.outf = m->L[0].gw.as<float>();
     e.ldc = m->in_pad;
     MCUDA(mlp_gemm(0, EPI_STORE, m->h1, m->in_pad, B, m->d1.as<__nv_bfloat16>(), m->h1, m->xb.as<__nv_bfloat16>(),
@@ -325,6 +340,7 @@ extern "C" int fga_mlp_gradients(fga_mlp *m, const float *X, const float *Y, int
     MCUDA(cudaSetDevice(m->device));
     if ((rc = backward(m, X, Y, batch, loss))) return rc;
     MCUDA(cudaStreamSynchronize(m->stream));
+    if ((rc = check_gemm_err(m))) return rc;
     return copy_params(m, grads, false, true);
 }
 
@@ -334,6 +350,7 @@ extern "C" int fga_mlp_train_step(fga_mlp *m, const float *X, const float *Y, in
     if (rc) return rc;
     MCUDA(cudaSetDevice(m->device));
     if ((rc = backward(m, X, Y, batch, loss))) return rc;
+    if (loss && (rc = check_gemm_err(m))) return rc;   // the loss read synchronised the stream
     m->step += 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - std::pow(b1, (float)m->step), c2 = 1.f - std::pow(b2, (float)m->step);
@@ -353,7 +370,7 @@ extern "C" int fga_mlp_forward(fga_mlp *m, const float *X, float *Y, int32_t bat
     MCUDA(cudaSetDevice(m->device));
     if ((rc = forward(m, X, batch, EPI_BIAS_DENORM, Y))) return rc;
     MCUDA(cudaStreamSynchronize(m->stream));
-    return FGA_OK;
+    return check_gemm_err(m);
 }
 
 extern "C" int fga_mlp_destroy(fga_mlp *m) {

@@ -1,142 +1,216 @@
 // mlp.cu -- the learned warm start's network: a 3-layer ReLU MLP
-// (in -> h1 -> h2 -> out) trained and evaluated with BF16 tensor-core GEMMs
-// (mma.sync m16n8k16, FP32 accumulation), FP32 master weights and Adam.
+// (in -> h1 -> h2 -> out) trained and evaluated with BF16 GEMMs on the
+// 5th-generation tensor cores (tcgen05.mma, FP32 accumulation in tensor
+// memory), FP32 master weights and Adam.
 //
 // GEMM convention: C(m, n) = epilogue( sum_k A(m, k) B(n, k) ), where
 // A(m, k) = A[m*lda + k] (K-major) or A[k*lda + m] (M-major), and likewise B.
-// Tiles of 64 x 64 x 32 are staged through shared memory (transposed on the
-// way in when the operand is not K-major), 4 warps each own 32 x 32.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "mlp_internal.h"
+#include "tc05.cuh"
 
 namespace fga {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
-
-__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// Epilogue of one element: v = sum_k A(m, k) B(nn, k).
+template <int EPI>
+__device__ __forceinline__ float epi_value(const GemmEpi &ep, int m, int nn, float v) {
+    if (EPI == EPI_BIAS_RELU || EPI == EPI_BIAS || EPI == EPI_BIAS_DENORM) {
+        v += ep.bias[nn];
+        if (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
+        if (EPI == EPI_BIAS_DENORM) v = v * ep.scale[nn] + ep.shift[nn];
+    } else if (EPI == EPI_RELU_MASK) {
+        v = __bfloat162float(ep.mask[(long long)m * ep.ldm + nn]) > 0.f ? v : 0.f;
+    }
+    return v;
 }
 
-// Loads a 64 x 32 tile of X(row, k) (row in [r0, r0+64), k in [k0, k0+32))
-// into S[row][k].  KMAJ: X(row, k) = X[row*ld + k], else X[k*ld + row].
-// Out-of-range elements read as zero.  ld and the contiguous extent must be
-// multiples of 8 (16-byte vector loads).
+// ---------------------------------------------------------------------------
+// 5th-generation tensor-core path.  One CTA of 128 threads computes a
+// 128 x 128 tile of C with its FP32 accumulator in tensor memory (128 lanes x
+// 128 columns).  K advances in blocks of 64 through two shared-memory stages:
+// the threads copy a block of A and of B into the no-swizzle K-major
+// core-matrix layout, then thread 0 issues four MMAs of K = 16 and commits
+// them to the stage's mbarrier; the threads wait on that mbarrier before
+// they refill the stage two blocks later, so the copy of block k + 1
+// overlaps the MMAs of block k.  The epilogue reads the accumulator back
+// with tcgen05.ld, each thread one row of 16 columns at a time.
+// ---------------------------------------------------------------------------
+constexpr int TBM = 128, TBN = 128, TBK = 64;
+constexpr int T_TILE = TBM * TBK * 2;        // bytes of one operand block (A and B alike)
+constexpr int T_LBO = TBM * 16;              // K-direction distance of core matrices
+constexpr int T_SBO = 128;                   // M/N-direction distance of core matrices
+constexpr int T_HDR = 1024;                  // mbarriers and the tensor-memory address
+// Slack after the four blocks, larger than the furthest byte a descriptor of
+// these tiles can address under either reading of its two byte offsets.
+constexpr int T_GUARD = 32768;
+constexpr int T_SMEM = T_HDR + 4 * T_TILE + T_GUARD;
+constexpr unsigned long long T_TIMEOUT_NS = 1000000000ull;
+
+// Copies rows [r0, r0 + 128) x k [k0, k0 + 64) of X into the block at S
+// (element (r, k) at byte (k / 8) T_LBO + (r / 8) T_SBO + (r % 8) 16 + (k % 8) 2).
+// KMAJ: X(r, k) = X[r*ld + k], else X[k*ld + r].  Rows >= rows and k >= K read
+// as zero; K and ld are multiples of 8, and so is rows for an M-major X.
 template <bool KMAJ>
-__device__ __forceinline__ void load_tile(__nv_bfloat16 (*S)[BK + PADK], const __nv_bfloat16 *X, int ld, int rows,
-                                          int K, int r0, int k0) {
+__device__ __forceinline__ void tc_stage(unsigned char *S, const __nv_bfloat16 *X, int ld, int rows, int K, int r0,
+                                         int k0) {
     const int t = threadIdx.x;
     if (KMAJ) {
-        // 64 rows x 4 vectors of 8 along k
-        for (int v = t; v < 64 * 4; v += 128) {
-            const int row = v >> 2, kk = (v & 3) * 8;
-            const int gr = r0 + row, gk = k0 + kk;
+        // v: bits 0..2 row within a group of 8, bits 3..5 16-byte chunk along
+        // k, bits 6..9 group of 8 rows.  A warp reads 64 contiguous bytes of
+        // each of 8 rows and writes four whole core matrices.
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int v = t + 128 * i;
+            const int row = (v >> 6) * 8 + (v & 7), c = (v >> 3) & 7;
+            const int gr = r0 + row, gk = k0 + c * 8;
             uint4 val = make_uint4(0, 0, 0, 0);
-            if (gr < rows && gk < K) val = *reinterpret_cast<const uint4 *>(X + (long long)gr * ld + gk);
-            *reinterpret_cast<uint4 *>(&S[row][kk]) = val;
+            if (gr < rows && gk < K) val = __ldg(reinterpret_cast<const uint4 *>(X + (long long)gr * ld + gk));
+            *reinterpret_cast<uint4 *>(S + c * T_LBO + (row >> 3) * T_SBO + (row & 7) * 16) = val;
         }
     } else {
-        // 32 k x 8 vectors of 8 along rows
-        for (int v = t; v < 32 * 8; v += 128) {
-            const int kk = v >> 3, row = (v & 7) * 8;
-            const int gr = r0 + row, gk = k0 + kk;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (gr < rows && gk < K) val = *reinterpret_cast<const uint4 *>(X + (long long)gk * ld + gr);
-            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&val);
+        // p: bits 0..2 and 5 group of 8 rows (rc), bits 3..4 pair of k (kp),
+        // bits 6..8 group of 8 k (kc).  Each thread reads rows 8 rc .. 8 rc + 7
+        // at k and k + 1 (16 bytes each) and stores the 8 (k, k + 1) pairs as
+        // 32-bit words, in an order rotated by rc so that the 32 lanes of a
+        // warp hit 32 distinct banks.
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int p = t + 128 * i;
+            const int rc = (p & 7) | (((p >> 5) & 1) << 3), kp = (p >> 3) & 3, kc = p >> 6;
+            const int k = k0 + kc * 8 + 2 * kp, gr = r0 + rc * 8;
+            uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0, 0, 0);
+            if (gr < rows) {
+                if (k < K) a = __ldg(reinterpret_cast<const uint4 *>(X + (long long)k * ld + gr));
+                if (k + 1 < K) b = __ldg(reinterpret_cast<const uint4 *>(X + (long long)(k + 1) * ld + gr));
+            }
+            const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+            uint32_t pr[8];
             #pragma unroll
-            for (int j = 0; j < 8; ++j) S[row + j][kk] = e[j];
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t lo = (j & 1) ? (aw[j >> 1] >> 16) : (aw[j >> 1] & 0xFFFFu);
+                const uint32_t hi = (j & 1) ? (bw[j >> 1] >> 16) : (bw[j >> 1] & 0xFFFFu);
+                pr[j] = lo | (hi << 16);
+            }
+            // pr[jj] <- pr[(jj + rc) % 8], by three conditional rotations
+            #pragma unroll
+            for (int sh = 0; sh < 3; ++sh) {
+                const bool f = (rc >> sh) & 1;
+                uint32_t q[8];
+                #pragma unroll
+                for (int jj = 0; jj < 8; ++jj) q[jj] = f ? pr[(jj + (1 << sh)) & 7] : pr[jj];
+                #pragma unroll
+                for (int jj = 0; jj < 8; ++jj) pr[jj] = q[jj];
+            }
+            unsigned char *base = S + kc * T_LBO + rc * T_SBO + kp * 4;
+            #pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                *reinterpret_cast<uint32_t *>(base + ((jj + rc) & 7) * 16) = pr[jj];
         }
     }
 }
 
 template <bool AK, bool BKM, int EPI>
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bfloat16 *A, int lda,
-                                              const __nv_bfloat16 *B, int ldb, GemmEpi ep) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PADK];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-    #pragma unroll
-    for (int i = 0; i < 2; ++i)
-        #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            #pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        load_tile<AK>(As, A, lda, M, K, m0, k0);
-        load_tile<BKM>(Bs, B, ldb, N, K, n0, k0);
-        __syncthreads();
-        #pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-            #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + gid;
-                const int c = kk + 2 * tig;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][c]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][c + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c + 8]);
-            }
-            #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = wn + j * 8 + gid;
-                const int c = kk + 2 * tig;
-                bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][c]);
-                bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][c + 8]);
-            }
-            #pragma unroll
-            for (int i = 0; i < 2; ++i)
-                #pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
-        }
-        __syncthreads();
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda,
+                                                   const __nv_bfloat16 *B, int ldb, GemmEpi ep) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tsm);   // one per stage
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + 64);
+    unsigned char *tiles = tsm + T_HDR;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+    if (t == 0) {
+        tc05::mbar_init(&bar[0], 1);
+        tc05::mbar_init(&bar[1], 1);
     }
-    // epilogue
-    #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+    if (warp == 0) tc05::tmem_alloc(tslot, TBN);
+    tc05::fence_before_sync();
+    __syncthreads();
+    tc05::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = tc05::idesc_bf16_f32<TBM, TBN>();
+    const int nk = (K + TBK - 1) / TBK;
+    bool ok = true;
+    int issued = 0;   // K blocks committed
+    for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb & 1;
+        unsigned char *sa = tiles + s * 2 * T_TILE, *sb = sa + T_TILE;
+        if (kb >= 2) {
+            // the MMAs of block kb - 2 have finished reading this stage
+            const bool w = tc05::mbar_wait(&bar[s], ((kb - 2) >> 1) & 1, T_TIMEOUT_NS);
+            if (!__syncthreads_and(w)) {
+                ok = false;
+                break;
+            }
+        }
+        tc_stage<AK>(sa, A, lda, M, K, m0, kb * TBK);
+        tc_stage<BKM>(sb, B, ldb, N, K, n0, kb * TBK);
+        tc05::fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            tc05::fence_after_sync();
+            const uint32_t a0 = tc05::smem_addr(sa), b0 = tc05::smem_addr(sb);
             #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + wm + i * 16 + gid + h * 8;
-                const int n = n0 + wn + j * 8 + 2 * tig;
-                if (m >= M) continue;
+            for (int j = 0; j < TBK / 16; ++j)
+                tc05::mma_bf16(tmem, tc05::smem_desc(a0 + 2 * j * T_LBO, T_LBO, T_SBO),
+                               tc05::smem_desc(b0 + 2 * j * T_LBO, T_LBO, T_SBO), idesc, kb > 0 || j > 0);
+            tc05::commit(&bar[s]);
+        }
+        issued = kb + 1;
+    }
+    // the last commit covers every MMA issued before it
+    bool done = true;
+    if (issued > 0) done = tc05::mbar_wait(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, T_TIMEOUT_NS);
+    done = __syncthreads_and(done) != 0;
+    tc05::fence_after_sync();
+    if (ok && done && issued > 0) {
+        const int m = m0 + warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        const bool vf = ep.outf && (ep.ldc & 7) == 0 && (reinterpret_cast<uintptr_t>(ep.outf) & 15) == 0;
+        const bool vb = ep.outb && (ep.ldc & 7) == 0 && (reinterpret_cast<uintptr_t>(ep.outb) & 15) == 0;
+        #pragma unroll 1
+        for (int c = 0; c < TBN / 16; ++c) {
+            const int nb = n0 + c * 16;
+            if (nb >= N) break;   // uniform over the CTA
+            float v[16];
+            tc05::ld_32x32b_x16(trow + (uint32_t)(c * 16), v);
+            if (m >= M) continue;
+            const bool full = nb + 16 <= N;
+            #pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = (full || nb + q < N) ? epi_value<EPI>(ep, m, nb + q, v[q]) : 0.f;
+            const long long o = (long long)m * ep.ldc + nb;
+            if (full && vf) {
                 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int nn = n + q;
-                    if (nn >= N) continue;
-                    float v = acc[i][j][h * 2 + q];
-                    const long long o = (long long)m * ep.ldc + nn;
-                    if (EPI == EPI_BIAS_RELU || EPI == EPI_BIAS || EPI == EPI_BIAS_DENORM) {
-                        v += ep.bias[nn];
-                        if (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
-                        if (EPI == EPI_BIAS_DENORM) v = v * ep.scale[nn] + ep.shift[nn];
-                        if (ep.outf) ep.outf[o] = v;
-                        if (ep.outb) ep.outb[o] = __float2bfloat16_rn(v);
-                    } else if (EPI == EPI_RELU_MASK) {
-                        const float h_act = __bfloat162float(ep.mask[(long long)m * ep.ldm + nn]);
-                        v = h_act > 0.f ? v : 0.f;
-                        if (ep.outb) ep.outb[o] = __float2bfloat16_rn(v);
-                        if (ep.outf) ep.outf[o] = v;
-                    } else {   // EPI_STORE
-                        ep.outf[o] = v;
+                for (int q = 0; q < 16; q += 4)
+                    *reinterpret_cast<float4 *>(ep.outf + o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            } else if (ep.outf) {
+                for (int q = 0; q < 16 && nb + q < N; ++q) ep.outf[o + q] = v[q];
+            }
+            if (full && vb) {
+                #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t w[4];
+                    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const __nv_bfloat162 pq = __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
+                        w[q] = *reinterpret_cast<const uint32_t *>(&pq);
                     }
+                    *reinterpret_cast<uint4 *>(ep.outb + o + 8 * h) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
+            } else if (ep.outb) {
+                for (int q = 0; q < 16 && nb + q < N; ++q) ep.outb[o + q] = __float2bfloat16_rn(v[q]);
             }
         }
+    } else if (t == 0 && ep.err) {
+        atomicOr(ep.err, 1);
     }
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc05::tmem_dealloc(tmem, TBN);
 }
 
 __global__ void k_to_bf16_pad(const float *X, int rows, int cols, int ldo, __nv_bfloat16 *out) {
@@ -256,25 +330,38 @@ inline int nblk(long long n, int t) {
 }  // namespace
 
 template <bool AK, bool BKM, int EPI>
-static cudaError_t gemm_t(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
-                          const GemmEpi &ep, cudaStream_t s) {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    k_gemm<AK, BKM, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, ep);
+static cudaError_t gemm_tc_t(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
+                             const GemmEpi &ep, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AK, BKM, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
+    k_gemm_tc<AK, BKM, EPI><<<grid, 128, T_SMEM, s>>>(M, N, K, A, lda, B, ldb, ep);
     return cudaGetLastError();
+}
+
+// Operand rules of the tensor-core path: 16-byte aligned base, K and ld
+// multiples of 8, ld covering the contiguous extent; an M-major operand's
+// row count a multiple of 8 as well.
+static bool operand_ok(const __nv_bfloat16 *X, int ld, int rows, int K, bool kmaj) {
+    if (!X || (reinterpret_cast<uintptr_t>(X) & 15) || ld % 8) return false;
+    return kmaj ? ld >= K : (rows % 8 == 0 && ld >= rows);
 }
 
 cudaError_t mlp_gemm(int layout, int epi, int M, int N, int K, const __nv_bfloat16 *A, int lda,
                      const __nv_bfloat16 *B, int ldb, const GemmEpi &ep, cudaStream_t s) {
     // layout: bit 0 = A is K-major, bit 1 = B is K-major
-#define FGA_GEMM_CASE(L, AKv, BKv)                                                                       \
-    if (layout == L) {                                                                                   \
-        switch (epi) {                                                                                   \
-        case EPI_BIAS_RELU: return gemm_t<AKv, BKv, EPI_BIAS_RELU>(M, N, K, A, lda, B, ldb, ep, s);      \
-        case EPI_BIAS: return gemm_t<AKv, BKv, EPI_BIAS>(M, N, K, A, lda, B, ldb, ep, s);                \
-        case EPI_BIAS_DENORM: return gemm_t<AKv, BKv, EPI_BIAS_DENORM>(M, N, K, A, lda, B, ldb, ep, s);  \
-        case EPI_RELU_MASK: return gemm_t<AKv, BKv, EPI_RELU_MASK>(M, N, K, A, lda, B, ldb, ep, s);      \
-        default: return gemm_t<AKv, BKv, EPI_STORE>(M, N, K, A, lda, B, ldb, ep, s);                     \
-        }                                                                                                \
+    if (M < 1 || N < 1 || K < 8 || K % 8 || ep.ldc < N || !operand_ok(A, lda, M, K, layout & 1) ||
+        !operand_ok(B, ldb, N, K, (layout >> 1) & 1))
+        return cudaErrorInvalidValue;
+#define FGA_GEMM_CASE(L, AKv, BKv)                                                                          \
+    if (layout == L) {                                                                                      \
+        switch (epi) {                                                                                      \
+        case EPI_BIAS_RELU: return gemm_tc_t<AKv, BKv, EPI_BIAS_RELU>(M, N, K, A, lda, B, ldb, ep, s);      \
+        case EPI_BIAS: return gemm_tc_t<AKv, BKv, EPI_BIAS>(M, N, K, A, lda, B, ldb, ep, s);                \
+        case EPI_BIAS_DENORM: return gemm_tc_t<AKv, BKv, EPI_BIAS_DENORM>(M, N, K, A, lda, B, ldb, ep, s);  \
+        case EPI_RELU_MASK: return gemm_tc_t<AKv, BKv, EPI_RELU_MASK>(M, N, K, A, lda, B, ldb, ep, s);      \
+        default: return gemm_tc_t<AKv, BKv, EPI_STORE>(M, N, K, A, lda, B, ldb, ep, s);                     \
+        }                                                                                                   \
     }
     FGA_GEMM_CASE(3, true, true)
     FGA_GEMM_CASE(1, true, false)

@@ -23,6 +23,7 @@ struct GemmEpi {
     float *outf;            // FP32 output (may be null)
     __nv_bfloat16 *outb;    // BF16 output (may be null)
     int ldc;
+    int *err;               // device word: set to 1 when a wait of the tensor-core path timed out (may be null)
 };
 
 cudaError_t mlp_gemm(int layout, int epi, int M, int N, int K, const __nv_bfloat16 *A, int lda,

@@ -78,9 +78,10 @@ class MpcBatch:
                     n_budget=r.n_budget, n_nonfinite=r.n_nonfinite, ms=r.ms, threads=r.threads,
                     check_every=r.check_every)
 
-    def fga_mpc_batch_read(self):
-        z = np.empty(int(self.V.sum()))
-        u = np.empty(int(self.E.sum()))
+    def fga_mpc_batch_read(self, state=True):
+        """Readout; state=False skips z and u (per-instance counters only)."""
+        z = np.empty(int(self.V.sum())) if state else None
+        u = np.empty(int(self.E.sum())) if state else None
         it = np.empty(self.n, dtype=np.int64)
         st = np.empty(self.n, dtype=np.int32)
         rp = np.empty(self.n)

@@ -75,7 +75,9 @@ def evaluate(net, n_eval=16384, x0_seed=5003, system_seed=5000, T=30, tol=1e-4, 
     """Cold vs warm batched solves of n_eval fresh instances.  Warm: network
     inference, warm-start map, solve with an iteration budget (default: the
     99th percentile of cold iterations on a calibration set), then every
-    instance that missed the budget re-solved from cold; all of it timed."""
+    instance that missed the budget re-solved from cold; all of it timed.
+    Both timed regions end with the per-instance counters on the host; the
+    solutions (z, u) are read afterwards for the comparison."""
     import torch
     if budget is None:
         dc = inputs.mpc_warmstart_inputs(calib, system_seed=system_seed, x0_seed=x0_seed + 100, T=T)
@@ -89,8 +91,9 @@ def evaluate(net, n_eval=16384, x0_seed=5003, system_seed=5000, T=30, tol=1e-4, 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rc = bcold.fga_mpc_batch_solve(max_iters, tol=tol, check_every=1)
+    cold = bcold.fga_mpc_batch_read(state=False)
     t_cold = time.perf_counter() - t0
-    cold = bcold.fga_mpc_batch_read()
+    cold["z"] = bcold.fga_mpc_batch_read()["z"]
     # warm
     X = torch.tensor(d["x0"], dtype=torch.float32, device="cuda")
     pred = torch.empty((n_eval, ld), dtype=torch.float32, device="cuda")
@@ -100,17 +103,18 @@ def evaluate(net, n_eval=16384, x0_seed=5003, system_seed=5000, T=30, tol=1e-4, 
     net.fga_mlp_forward(X, pred)
     bwarm.fga_mpc_batch_warm_start(pred, ld)
     rw = bwarm.fga_mpc_batch_solve(budget, tol=tol, check_every=1)
-    warm = bwarm.fga_mpc_batch_read()
+    warm = bwarm.fga_mpc_batch_read(state=False)
     miss = np.nonzero(warm["status"] != 0)[0]
     fb_iters = np.zeros(n_eval, dtype=np.int64)
     if miss.size:
         dm = dict(d, x0=d["x0"][miss], T=d["T"][miss])
         bm = _batch(dm)
         bm.fga_mpc_batch_solve(max_iters, tol=tol, check_every=1)
-        fb = bm.fga_mpc_batch_read()
+        fb = bm.fga_mpc_batch_read(state=False)
         fb_iters[miss] = fb["iters"]
     torch.cuda.synchronize()
     t_warm = time.perf_counter() - t0
+    warm["z"] = bwarm.fga_mpc_batch_read()["z"]
     it_cold = cold["iters"]
     it_warm = warm["iters"] + fb_iters
     # the warm solutions are the cold ones (same optimum, same tolerance)
