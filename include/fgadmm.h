@@ -273,7 +273,7 @@ typedef struct {
     int64_t max_iters;          /* budget per instance                      */
     double tol_pri, tol_dual;   /* RMS residual tolerances per instance     */
     int32_t check_every;        /* 0 = autotuned value (default 1)          */
-    int32_t threads;            /* CTA size 64/128/256; 0 = autotuned (128) */
+    int32_t threads;            /* CTA size 64/128/256/512; 0 = autotuned (128) */
     int32_t use_graph;          /* 1 = launch from a cached CUDA graph      */
     int32_t reserved;
 } fga_mpc_opts;
@@ -301,7 +301,7 @@ int fga_mpc_batch_read(fga_mpc_batch *b, double *z, double *u, int64_t *iters, i
  * horizon, [4] tuned CTA size, [5] tuned check interval.  n >= 6. */
 int fga_mpc_batch_info(const fga_mpc_batch *b, int64_t *info, int32_t n);
 
-/* Autotuner: times CTA sizes {64,128,256} x check intervals {1,2,5,10} on
+/* Autotuner: times CTA sizes {64,128,256,512} x check intervals {1,2,5,10} on
  * the batch from its current start point (which it restores) and keeps the
  * fastest for later solves.  cache_path (may be NULL): a text file of
  * previous results keyed by GPU, precision and problem shape; a hit skips

@@ -5,15 +5,15 @@
 // keeps the instance's whole state (x, u, n per edge; z per variable; the
 // dynamics projector) in shared memory, and
 // iterates with CTA-local synchronisation only:
-//   F1  deferred u-update of the previous iteration, n = z - u
-//       (+ FP64 primal residual on check iterations)
-//   F2  x-update: dynamics rows v = P n, quadratic costs rho n / (w + rho),
+//   X   x-update: dynamics rows v = P n, quadratic costs rho n / (w + rho),
 //       boxes clamp, fixed x_0
-//   Z   z_b = sum rho (x + u) / sum rho over the variable's 2 or 3 edges
-//       (+ FP64 dual residual on check iterations)
-// and stops when both RMS residuals of a checked iteration meet the
-// tolerances, or at the iteration budget.  The stored state is then exactly
-// the state after the reported number of iterations.
+//   Z   per variable: z_b = sum rho (x + u) / sum rho over its 2 or 3 edges,
+//       then on those edges u += alpha (x - z_b), n = z_b - u (+ the primal
+//       and dual residual partials on check iterations)
+// and stops when both RMS residuals of a checked iteration (FP64 sums of
+// the threads' partials) meet the tolerances, or at the iteration budget.
+// The stored state is then exactly the state after the reported number of
+// iterations.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -86,34 +86,167 @@ __device__ __forceinline__ int var_edges(const Shape &g, int b, int *ed) {
     return 3;
 }
 
-// Deterministic block sums of two doubles per thread (fixed shuffle tree,
-// then warps in order), broadcast to every thread; red holds 2 x 33 doubles.
+// (h, l) += (h2, l2) for unevaluated float pairs h + l (TwoSum, then a fast
+// renormalisation): the pair keeps about 44 significant bits, and the sum
+// is commutative, so a butterfly leaves the same value in every lane.
+__device__ __forceinline__ void ff_add(float &h, float &l, float h2, float l2) {
+    const float s = h + h2;
+    const float bb = s - h;
+    float e = (h - (s - bb)) + (h2 - bb);
+    e += l + l2;
+    h = s + e;
+    l = e - (h - s);
+}
+
+struct CheckOut {
+    bool stop;
+    int status;
+    double rp, rd;
+};
+
+// sqrt(t / E) <= tol (the RMS residual test), decided without the FP64
+// divide and square root (long dependent sequences on this part's narrow
+// FP64 pipe) unless t lies close to tol^2 E, where the exact form decides:
+// within a relative 2^-40 for an FP64 t, within 2^-20 for a float pair
+// h + l (carried to about 2^-44), whose fast test compares h alone.
+struct ResidualTest {
+    double E, tol, lo, hi;
+    float lo32, hi32;
+    __device__ void init(double E_, double tol_) {
+        E = E_;
+        tol = tol_;
+        if (!(tol_ > 0.0)) {
+            lo = hi = 0.0;                        // only t = 0 can pass
+            lo32 = hi32 = 0.f;
+        } else {
+            const double t2 = tol_ * tol_ * E_;
+            const bool normal = t2 > 1e-30 && t2 < 1e30;
+            lo = normal ? t2 * (1.0 - 0x1p-40) : -INFINITY;   // else always the exact form
+            hi = normal ? t2 * (1.0 + 0x1p-40) : INFINITY;
+            lo32 = normal ? (float)(t2 * (1.0 - 0x1p-20)) : -INFINITY;
+            hi32 = normal ? (float)(t2 * (1.0 + 0x1p-20)) : INFINITY;
+        }
+    }
+    __device__ bool pass(double t) const {
+        if (t < lo) return true;
+        if (t > hi) return false;
+        return sqrt(t / E) <= tol;
+    }
+    __device__ bool pass(float h, float l) const {
+        if (h < lo32) return true;
+        if (h > hi32) return false;
+        return sqrt(((double)h + (double)l) / E) <= tol;
+    }
+};
+
+// Four consecutive values from a 16-byte aligned shared-memory address.
+__device__ __forceinline__ void ld4(const float *p, float *v) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double *v) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+// Residual check of one iteration.  Each thread's squared primal and dual
+// residual partials are summed by a fixed tree (warps by shuffles, then the
+// warps in order by thread 0, which alone decides); every thread returns
+// the same decision.  FP64 state sums in FP64.  FP32 state sums in float
+// pairs (TwoSum), which carry the sum to about 2^-44 relative: an FP64-class
+// sum without the FP64 pipe, whose dependent adds cost about 150 cycles
+// each here; the reported norms are formed in FP64 from the pair.  red
+// holds at least 34 doubles (up to 16 warps) and flag 2 ints.
 template <int NT>
-__device__ __forceinline__ void block_sum2_bcast(double &v0, double &v1, double *red) {
+__device__ __forceinline__ CheckOut block_check(float pri, float dual, const ResidualTest &tp_,
+                                                const ResidualTest &td_, double tol_pri, double tol_dual, bool last,
+                                                double *red, int *flag) {
+    float pl = 0.f, dl = 0.f;
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        const float ah = __shfl_xor_sync(0xffffffffu, pri, o), alo = __shfl_xor_sync(0xffffffffu, pl, o);
+        const float bh = __shfl_xor_sync(0xffffffffu, dual, o), blo = __shfl_xor_sync(0xffffffffu, dl, o);
+        ff_add(pri, pl, ah, alo);
+        ff_add(dual, dl, bh, blo);
     }
+    float *rf = reinterpret_cast<float *>(red);
     const int w = threadIdx.x >> 5;
-    __syncthreads();
     if ((threadIdx.x & 31) == 0) {
-        red[w] = v0;
-        red[33 + w] = v1;
+        rf[w] = pri;
+        rf[16 + w] = pl;
+        rf[32 + w] = dual;
+        rf[48 + w] = dl;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t0 = 0.0, t1 = 0.0;
-        for (int i = 0; i < NT / 32; ++i) {
-            t0 += red[i];
-            t1 += red[33 + i];
+        float ph = rf[0], plo = rf[16], dh = rf[32], dlo = rf[48];
+        for (int i = 1; i < NT / 32; ++i) {
+            ff_add(ph, plo, rf[i], rf[16 + i]);
+            ff_add(dh, dlo, rf[32 + i], rf[48 + i]);
         }
-        red[32] = t0;
-        red[65] = t1;
+        const bool finite = isfinite(ph) && isfinite(dh);
+        const bool conv = finite && tp_.pass(ph, plo) && td_.pass(dh, dlo);
+        const bool stop = !finite || conv || last;
+        if (stop) {
+            red[32] = sqrt(((double)ph + (double)plo) / tp_.E);
+            red[33] = sqrt(((double)dh + (double)dlo) / td_.E);
+        }
+        flag[0] = stop;
+        flag[1] = !finite ? kENonFinite : (conv || (tol_pri <= 0.0 && tol_dual <= 0.0)) ? 0 : kEBudget;
     }
     __syncthreads();
-    v0 = red[32];
-    v1 = red[65];
+    CheckOut c;
+    c.stop = flag[0] != 0;
+    c.status = flag[1];
+    c.rp = red[32];
+    c.rd = red[33];
+    return c;
+}
+
+template <int NT>
+__device__ __forceinline__ CheckOut block_check(double pri, double dual, const ResidualTest &tp_,
+                                                const ResidualTest &td_, double tol_pri, double tol_dual, bool last,
+                                                double *red, int *flag) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pri += __shfl_xor_sync(0xffffffffu, pri, o);
+        dual += __shfl_xor_sync(0xffffffffu, dual, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[w] = pri;
+        red[16 + w] = dual;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tp = 0.0, td = 0.0;
+        for (int i = 0; i < NT / 32; ++i) {
+            tp += red[i];
+            td += red[16 + i];
+        }
+        const bool finite = isfinite(tp) && isfinite(td);
+        const bool conv = finite && tp_.pass(tp) && td_.pass(td);
+        const bool stop = !finite || conv || last;
+        if (stop) {
+            red[32] = sqrt(tp / tp_.E);
+            red[33] = sqrt(td / td_.E);
+        }
+        flag[0] = stop;
+        flag[1] = !finite ? kENonFinite : (conv || (tol_pri <= 0.0 && tol_dual <= 0.0)) ? 0 : kEBudget;
+    }
+    __syncthreads();
+    CheckOut c;
+    c.stop = flag[0] != 0;
+    c.status = flag[1];
+    c.rp = red[32];
+    c.rd = red[33];
+    return c;
 }
 
 }  // namespace
@@ -123,18 +256,26 @@ int mpc_smem_bytes(int rsize, int nx, int nu, int tmax, int threads) {
     const int A = 2 * nx + nu;
     const int E = 2 * nx + (3 * nx + 3 * nu) * tmax;
     const int V = (nx + nu) * tmax + nx;
-    int b = (3 * E + V + A * (A + 1) + 2 * nx + nu) * rsize;
+    int b = (3 * E + V + A * (A + 1) + 3 * nx + 2 * nu) * rsize;
     b = (b + 15) & ~15;
     return b + 72 * (int)sizeof(double);
 }
 
 // NXC, NUC: the state and input sizes when known at compile time (the
-// index arithmetic then divides by constants and the dynamics rows unroll),
-// 0 for sizes given at run time.
+// index arithmetic then divides by constants, and each thread keeps one row
+// of the dynamics projector in registers), 0 for sizes given at run time.
 template <typename R, int NT, int NXC, int NUC>
 __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_k;
+    __shared__ int s_flag[2];
+    constexpr int AC = 2 * NXC + NUC;             // dynamics factor arity (compile time), 0 if unknown
+    constexpr int GC = AC ? NT / (AC ? AC : 1) : 0;   // dynamics factors a pass covers, one row per thread
+    // 16-byte loads of a dynamics factor's n: the factor starts at nx + t A
+    // within n, n at 2 E values from a 16-byte aligned base, E even when
+    // nx + nu is; so nx, nu multiples of 4 (float) or 2 (double) suffice
+    constexpr bool VEC = AC != 0 && AC % 4 == 0 &&
+                         (sizeof(R) == 4 ? (NXC % 4 == 0 && NUC % 4 == 0) : (NXC % 2 == 0 && NUC % 2 == 0));
     const int nx = NXC ? NXC : a.nx, nu = NUC ? NUC : a.nu, A = 2 * nx + nu, LP = A + 1;
     for (;;) {
         __syncthreads();
@@ -152,7 +293,8 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
         R *q = P + A * LP;
         R *r = q + nx;
         R *x0 = r + nu;
-        const int nvals = 3 * g.E + g.V + A * LP + 2 * nx + nu;
+        R *cw = x0 + nx;                 // rho / (w + rho) per cost component (nx states, nu inputs)
+        const int nvals = 3 * g.E + g.V + A * LP + 3 * nx + 2 * nu;
         double *red = reinterpret_cast<double *>(sm + ((nvals * (int)sizeof(R) + 15) & ~15));
         const long long eo = a.eoff[inst], zof = a.zoff[inst];
         const int sy = a.sys[inst];
@@ -167,113 +309,149 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
             x0[j] = a.x0[(long long)inst * nx + j];
         }
         for (int j = threadIdx.x; j < nu; j += NT) r[j] = a.r[sy * nu + j];
+        for (int j = threadIdx.x; j < nx + nu; j += NT) {
+            const R w = j < nx ? a.q[sy * nx + j] : a.r[sy * nu + j - nx];
+            cw[j] = a.rho / (w + a.rho);
+        }
+        __syncthreads();
+        // n = z - u of the stored state
+        for (int e = threadIdx.x; e < g.E; e += NT) nb[e] = z[edge_var(g, e)] - u[e];
+        // this thread's projector row (compile-time sizes): row prow of the
+        // dynamics factors pgrp, pgrp + GC, ...
+        const int prow = AC ? (int)threadIdx.x % (AC ? AC : 1) : 0;
+        const int pgrp = AC ? (int)threadIdx.x / (AC ? AC : 1) : 0;
+        R Pr[AC ? AC : 1];
+        if (AC) {
+            #pragma unroll
+            for (int j = 0; j < (AC ? AC : 1); ++j) Pr[j] = pgrp < GC ? P[prow * LP + j] : R(0);
+        }
         __syncthreads();
 
         const R rho = a.rho, alpha = a.alpha;
-        const double E = (double)g.E;
+        ResidualTest rtp, rtd;   // used by thread 0
+        if (threadIdx.x == 0) {
+            rtp.init((double)g.E, a.tol_pri);
+            rtd.init((double)g.E, a.tol_dual);
+        }
         long long done = 0;
         int status = 0;
         double rp = nan(""), rd = nan("");
-        double dual = 0.0;               // this thread's share of the last checked dual residual
-        bool pend = a.first_pending != 0;
         const long long K = a.max_iters;
         const int ce = a.check_every;
+        const int nrow = g.T * A;
+        const int new_ = g.E - nrow;   // elementwise edges: FIX (first nx), then costs and boxes
         int rm = 1 % ce;   // it mod check_every, kept by counting (no 64-bit division per iteration)
-        int rm_prev = 0;   // (it - 1) mod check_every
-        for (long long it = 1; K > 0 && it <= K + 1; ++it) {
-            const bool last = it == K + 1;
-            const bool chk = pend && (rm_prev == 0 || last);
-            // F1: u-update of iteration it-1, n-update.  The thread's
-            // squared differences are summed in the working precision, the
-            // threads' sums in FP64 (the FP64 pipe is narrow on this part).
-            R pri_r = R(0);
-            for (int e = threadIdx.x; e < g.E; e += NT) {
-                const R zb = z[edge_var(g, e)];
-                R ue = u[e];
-                if (pend) {
-                    const R d = x[e] - zb;
-                    if (chk) pri_r += d * d;
-                    ue = ue + alpha * d;
-                    u[e] = ue;
+        for (long long it = 1; it <= K; ++it) {
+            // X: x-update.  Dynamics rows v = P n, then the elementwise edges.
+            if (AC) {
+                if (pgrp < GC) {
+                    for (int t = pgrp; t < g.T; t += GC) {
+                        const R *n = nb + g.dyn(t);
+                        R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);
+                        if (VEC) {
+                            // n is 16-byte aligned here (see VEC): one vector load per 4 (float) or 2 (double) values
+                            #pragma unroll
+                            for (int j = 0; j < (AC ? AC : 4); j += 4) {
+                                R v[4];
+                                ld4(n + j, v);
+                                s0 += Pr[j] * v[0];
+                                s1 += Pr[j + 1] * v[1];
+                                s2 += Pr[j + 2] * v[2];
+                                s3 += Pr[j + 3] * v[3];
+                            }
+                        } else {
+                            #pragma unroll
+                            for (int j = 0; j + 3 < (AC ? AC : 1); j += 4) {
+                                s0 += Pr[j] * n[j];
+                                s1 += Pr[j + 1] * n[j + 1];
+                                s2 += Pr[j + 2] * n[j + 2];
+                                s3 += Pr[j + 3] * n[j + 3];
+                            }
+                            #pragma unroll
+                            for (int j = (AC ? AC : 1) & ~3; j < (AC ? AC : 1); ++j) s0 += Pr[j] * n[j];
+                        }
+                        x[g.dyn(t) + prow] = (s0 + s1) + (s2 + s3);
+                    }
                 }
-                nb[e] = zb - ue;
-            }
-            double pri = (double)pri_r;
-            if (chk) {
-                double sp = pri, sd = dual;
-                block_sum2_bcast<NT>(sp, sd, red);
-                rp = sqrt(sp / E);
-                rd = sqrt(sd / E);
-                const bool finite = isfinite(rp) && isfinite(rd);
-                if (!finite || (rp <= a.tol_pri && rd <= a.tol_dual) || last) {
-                    done = it - 1;
-                    status = !finite ? kENonFinite
-                                     : ((rp <= a.tol_pri && rd <= a.tol_dual) ||
-                                        (a.tol_pri <= 0.0 && a.tol_dual <= 0.0)) ? 0 : kEBudget;
-                    break;
-                }
-            }
-            __syncthreads();
-            // F2: x-update.  Dynamics rows first (T*A items), then the
-            // elementwise edges (FIX, costs, boxes).
-            const int nrow = g.T * A;
-            const int nitem = nrow + (g.E - nrow);
-            for (int item = threadIdx.x; item < nitem; item += NT) {
-                if (item < nrow) {
+            } else {
+                for (int item = threadIdx.x; item < nrow; item += NT) {
                     const int t = item / A, row = item - t * A;
                     const R *n = nb + g.dyn(t);
-                    const R *Pr = P + row * LP;
+                    const R *Pp = P + row * LP;
                     R acc = R(0);
-                    #pragma unroll
-                    for (int j = 0; j < A; ++j) acc += Pr[j] * n[j];
+                    for (int j = 0; j < A; ++j) acc += Pp[j] * n[j];
                     x[g.dyn(t) + row] = acc;
-                } else {
-                    int e = item - nrow;
-                    if (e < nx) {
-                        x[e] = x0[e];
-                        continue;
-                    }
-                    e += nrow;
-                    const R n = nb[e];
-                    R v;
-                    if (e < g.quadT()) {
-                        const int c = (e - g.quad(0)) % g.S;
-                        const R w = c < nx ? q[c] : r[c - nx];
-                        v = (rho * n) / (w + rho);
-                    } else if (e < g.box(0)) {
-                        v = (rho * n) / (q[e - g.quadT()] + rho);
-                    } else {
-                        v = n;
-                        if (v < a.lo) v = a.lo;
-                        if (v > a.hi) v = a.hi;
-                    }
-                    x[e] = v;
                 }
             }
+            for (int i = threadIdx.x; i < new_; i += NT) {
+                if (i < nx) {
+                    x[i] = x0[i];
+                    continue;
+                }
+                const int e = i + nrow;
+                const R n = nb[e];
+                R v;
+                if (e < g.quadT()) {
+                    v = cw[(e - g.quad(0)) % g.S] * n;
+                } else if (e < g.box(0)) {
+                    v = cw[e - g.quadT()] * n;
+                } else {
+                    v = n;
+                    if (v < a.lo) v = a.lo;
+                    if (v > a.hi) v = a.hi;
+                }
+                x[e] = v;
+            }
             __syncthreads();
-            // Z: rho-weighted mean over each variable's edges
-            const bool chkz = rm == 0 || it == K;
-            R dual_r = R(0);
+            // Z: rho-weighted mean over each variable's edges, then on those
+            // edges u += alpha (x - z) and n = z - u (each edge belongs to one
+            // variable), with the residual partials on check iterations.
+            const bool chk = rm == 0 || it == K;
+            R pri_r = R(0), dual_r = R(0);
             for (int b = threadIdx.x; b < g.V; b += NT) {
                 int ed[3];
                 const int ne = var_edges(g, b, ed);
-                R S = R(0), Rs = R(0);
-                for (int j = 0; j < ne; ++j) {
-                    S += rho * (x[ed[j]] + u[ed[j]]);
+                R xe[3], ue[3];
+                #pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    xe[j] = j < ne ? x[ed[j]] : R(0);
+                    ue[j] = j < ne ? u[ed[j]] : R(0);
+                }
+                R S = rho * (xe[0] + ue[0]) + rho * (xe[1] + ue[1]), Rs = rho + rho;
+                if (ne == 3) {
+                    S += rho * (xe[2] + ue[2]);
                     Rs += rho;
                 }
                 const R zold = z[b];
                 const R znew = S / Rs;
                 z[b] = znew;
-                if (chkz) {
+                #pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (j < ne) {
+                        const R d = xe[j] - znew;
+                        const R un = ue[j] + alpha * d;
+                        u[ed[j]] = un;
+                        nb[ed[j]] = znew - un;
+                        if (chk) pri_r += d * d;
+                    }
+                }
+                if (chk) {
                     const R dz = znew - zold;
                     dual_r += (R)ne * rho * rho * dz * dz;
                 }
             }
-            dual = (double)dual_r;
-            pend = true;
-            rm_prev = rm;
             rm = rm + 1 == ce ? 0 : rm + 1;
+            if (chk) {
+                const CheckOut c = block_check<NT>(pri_r, dual_r, rtp, rtd, a.tol_pri, a.tol_dual, it == K, red,
+                                                         s_flag);
+                if (c.stop) {
+                    done = it;
+                    status = c.status;
+                    rp = c.rp;
+                    rd = c.rd;
+                    break;
+                }
+            }
             __syncthreads();
         }
         // store the state of the instance
@@ -297,10 +475,12 @@ static const void *mpc_kernel(int threads, bool fixed) {
     if (fixed)
         return threads == 64    ? (const void *)k_mpc_batch<R, 64, 12, 4>
                : threads == 128 ? (const void *)k_mpc_batch<R, 128, 12, 4>
-                                : (const void *)k_mpc_batch<R, 256, 12, 4>;
+               : threads == 256 ? (const void *)k_mpc_batch<R, 256, 12, 4>
+                                : (const void *)k_mpc_batch<R, 512, 12, 4>;
     return threads == 64    ? (const void *)k_mpc_batch<R, 64, 0, 0>
            : threads == 128 ? (const void *)k_mpc_batch<R, 128, 0, 0>
-                            : (const void *)k_mpc_batch<R, 256, 0, 0>;
+           : threads == 256 ? (const void *)k_mpc_batch<R, 256, 0, 0>
+                            : (const void *)k_mpc_batch<R, 512, 0, 0>;
 }
 
 template <typename R>
