@@ -86,6 +86,20 @@ __device__ __forceinline__ int var_edges(const Shape &g, int b, int *ed) {
     return 3;
 }
 
+// The same edges as var_edges, computed with selects (no divergence
+// between state and input variables in a warp): x_t (t >= 1) has
+// DYN_{t-1}, DYN_t, QUAD_t; x_0 has FIX, DYN_0, QUAD_0; u_t has DYN_t,
+// QUAD_t, BOX_t; x_T has DYN_{T-1}, QUAD_T.  Ascending in every case.
+__device__ __forceinline__ int var_edges_sel(const Shape &g, int b, int *ed) {
+    const int t = b / g.S, c = b - t * g.S;
+    const bool is_u = c >= g.nx, last = t == g.T;
+    const int prev = t == 0 ? c : g.dyn(t - 1) + g.S + c;
+    ed[0] = is_u ? g.dyn(t) + c : prev;
+    ed[1] = last ? g.quadT() + c : (is_u ? g.quad(t) + c : g.dyn(t) + c);
+    ed[2] = is_u ? g.box(t) + (c - g.nx) : g.quad(t) + c;
+    return last ? 2 : 3;
+}
+
 // (h, l) += (h2, l2) for unevaluated float pairs h + l (TwoSum, then a fast
 // renormalisation): the pair keeps about 44 significant bits, and the sum
 // is commutative, so a butterfly leaves the same value in every lane.
@@ -341,6 +355,12 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
         const int nrow = g.T * A;
         const int new_ = g.E - nrow;   // elementwise edges: FIX (first nx), then costs and boxes
         int rm = 1 % ce;   // it mod check_every, kept by counting (no 64-bit division per iteration)
+        // The elementwise operators (FIX, costs, boxes) need only their own
+        // edge's n, so the Z phase of an unchecked iteration applies them to
+        // the n it has just formed (x of the next iteration, the same
+        // formulas); ew_pending marks an x not advanced that way (the first
+        // iteration, and after a checked one, whose stored x must stay).
+        bool ew_pending = true;
         for (long long it = 1; it <= K; ++it) {
             // X: x-update.  Dynamics rows v = P n, then the elementwise edges.
             if (AC) {
@@ -383,7 +403,7 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
                     x[g.dyn(t) + row] = acc;
                 }
             }
-            for (int i = threadIdx.x; i < new_; i += NT) {
+            for (int i = ew_pending ? (int)threadIdx.x : new_; i < new_; i += NT) {
                 if (i < nx) {
                     x[i] = x0[i];
                     continue;
@@ -407,32 +427,59 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
             // edges u += alpha (x - z) and n = z - u (each edge belongs to one
             // variable), with the residual partials on check iterations.
             const bool chk = rm == 0 || it == K;
+            ew_pending = chk;
             R pri_r = R(0), dual_r = R(0);
             for (int b = threadIdx.x; b < g.V; b += NT) {
                 int ed[3];
-                const int ne = var_edges(g, b, ed);
+                const int ne = var_edges_sel(g, b, ed);
+                const int tb = b / g.S, cb = b - tb * g.S;
+                const bool ub = cb >= nx;             // an input variable u_t
                 R xe[3], ue[3];
                 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     xe[j] = j < ne ? x[ed[j]] : R(0);
                     ue[j] = j < ne ? u[ed[j]] : R(0);
                 }
-                R S = rho * (xe[0] + ue[0]) + rho * (xe[1] + ue[1]), Rs = rho + rho;
-                if (ne == 3) {
-                    S += rho * (xe[2] + ue[2]);
-                    Rs += rho;
+                R znew;
+                if (sizeof(R) == 4) {
+                    // one rho: z = sum (x + u) / deg, by a multiply with 1 / deg
+                    R S = (xe[0] + ue[0]) + (xe[1] + ue[1]);
+                    if (ne == 3) S += xe[2] + ue[2];
+                    znew = S * (ne == 3 ? R(1) / R(3) : R(0.5));
+                } else {
+                    // FP64: the definition's sums and division, in edge order
+                    R S = rho * (xe[0] + ue[0]) + rho * (xe[1] + ue[1]), Rs = rho + rho;
+                    if (ne == 3) {
+                        S += rho * (xe[2] + ue[2]);
+                        Rs += rho;
+                    }
+                    znew = S / Rs;
                 }
                 const R zold = z[b];
-                const R znew = S / Rs;
                 z[b] = znew;
+                R nn[3];
                 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     if (j < ne) {
                         const R d = xe[j] - znew;
                         const R un = ue[j] + alpha * d;
                         u[ed[j]] = un;
-                        nb[ed[j]] = znew - un;
+                        nn[j] = znew - un;
+                        nb[ed[j]] = nn[j];
                         if (chk) pri_r += d * d;
+                    }
+                }
+                if (!chk) {
+                    // next x of this variable's cost edge (QUAD_t, or QUAD_T for
+                    // x_T: the second edge of u_t and x_T, the third of x_t) and
+                    // of u_t's box edge; x_0's FIX edge keeps x_0
+                    const int qj = (ub || ne == 2) ? 1 : 2;
+                    x[ed[qj]] = cw[cb] * nn[qj];
+                    if (ub) {
+                        R v = nn[2];
+                        if (v < a.lo) v = a.lo;
+                        if (v > a.hi) v = a.hi;
+                        x[ed[2]] = v;
                     }
                 }
                 if (chk) {
