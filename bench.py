@@ -375,11 +375,26 @@ def run_extras(log=None):
 def run_profile(args):
     """One warm-up and one solve of --profile-iters iterations (the workload
     of the benchmark, or with --profile-workload svm the SVM of the extras,
-    at a length that suits an ncu capture)."""
+    or with mpc_one the slowest instance of the MPC batch alone), at a
+    length that suits an ncu capture."""
     import torch
     from paper_1603_02526_gb300 import build, inputs, _lib
     from paper_1603_02526_gb300.graph import graph_from_problem
     build.build()
+    if args.profile_workload == "mpc_one":
+        # the slowest instance of the 4096-instance MPC batch (index 778,
+        # T = 12, not converged within its budget) alone, no residual checks
+        from paper_1603_02526_gb300.mpc import batch_from_inputs
+        d = inputs.mpc_batch_inputs(4096, seed=4000)
+        sub = {k: (v[778:779] if isinstance(v, np.ndarray) and v.shape[:1] == (4096,) else v) for k, v in d.items()}
+        b = batch_from_inputs(sub, "f32")
+        for _ in range(2):
+            b.fga_mpc_batch_init()
+            r = b.fga_mpc_batch_solve(args.profile_iters, tol=0.0, check_every=10 ** 9, threads=args.profile_threads,
+                                      use_graph=False)
+        print("profile run: one MPC instance, %d iterations, %d threads, %.3f ms" % (
+            args.profile_iters, args.profile_threads, r["ms"]))
+        return 0
     if args.profile_workload == "svm":
         p = inputs.svm_problem(100000, 64, seed=3000)
     else:
@@ -408,7 +423,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the packing sweep (no SVM / MPC / warm start)")
     ap.add_argument("--zorder", type=int, default=None,
                     help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 disk tiles, 3 hinge bank)")
-    ap.add_argument("--profile-workload", default="packing", choices=["packing", "svm"])
+    ap.add_argument("--profile-workload", default="packing", choices=["packing", "svm", "mpc_one"])
+    ap.add_argument("--profile-threads", type=int, default=256, help="CTA size of the mpc_one profiling run")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")
     args = ap.parse_args()
