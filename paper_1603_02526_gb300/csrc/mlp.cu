@@ -5,9 +5,13 @@
 //
 // GEMM convention: C(m, n) = epilogue( sum_k A(m, k) B(n, k) ), where
 // A(m, k) = A[m*lda + k] (K-major) or A[k*lda + m] (M-major), and likewise B.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "mlp_internal.h"
 #include "tc05.cuh"
@@ -15,19 +19,6 @@
 namespace fga {
 
 namespace {
-
-// Epilogue of one element: v = sum_k A(m, k) B(nn, k).
-template <int EPI>
-__device__ __forceinline__ float epi_value(const GemmEpi &ep, int m, int nn, float v) {
-    if (EPI == EPI_BIAS_RELU || EPI == EPI_BIAS || EPI == EPI_BIAS_DENORM) {
-        v += ep.bias[nn];
-        if (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
-        if (EPI == EPI_BIAS_DENORM) v = v * ep.scale[nn] + ep.shift[nn];
-    } else if (EPI == EPI_RELU_MASK) {
-        v = __bfloat162float(ep.mask[(long long)m * ep.ldm + nn]) > 0.f ? v : 0.f;
-    }
-    return v;
-}
 
 // ---------------------------------------------------------------------------
 // 5th-generation tensor-core path.  One CTA of 128 threads computes a
@@ -114,6 +105,109 @@ __device__ __forceinline__ void tc_stage(unsigned char *S, const __nv_bfloat16 *
     }
 }
 
+// Epilogue of a 128 x 128 tile whose FP32 accumulator sits in tensor memory
+// at tmem, staged through shared memory at S (the operand stages, free once
+// the MMAs are done; 4 x 32 x T_SROW floats).  Pass 1: warp w reads its 32
+// rows (one per lane, 32 columns at a time) and writes them as 16-byte rows
+// segments into its own 32 x T_SROW block (a stride of 132 floats keeps the
+// eight lanes of each store phase on distinct banks).  Pass 2: row by row,
+// lane l takes columns 4l .. 4l + 3 (their bias, scale and shift held in
+// registers), applies the element epilogue and stores whole 512-byte (FP32)
+// or 256-byte (BF16) row segments.  Every thread of the CTA calls it
+// (tcgen05.ld is warp-collective).
+constexpr int T_SROW = TBN + 4;
+static_assert(4 * 32 * T_SROW * 4 <= T_SMEM - T_HDR, "the epilogue's staging fits in the operand area");
+
+template <int EPI>
+__device__ __forceinline__ void tc_epilogue(const GemmEpi &ep, int M, int N, int m0, int n0, uint32_t tmem,
+                                            float *S) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *Sw = S + warp * 32 * T_SROW;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    #pragma unroll 1
+    for (int c = 0; c < TBN / 32; ++c) {
+        if (n0 + c * 32 >= N) break;   // uniform over the CTA
+        float v[32];
+        tc05::ld_32x32b_x32(trow + (uint32_t)(c * 32), v);
+        #pragma unroll
+        for (int q = 0; q < 32; q += 4)
+            *reinterpret_cast<float4 *>(Sw + lane * T_SROW + c * 32 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    }
+    __syncwarp();
+    const int n = n0 + 4 * lane;
+    float bias[4] = {0.f, 0.f, 0.f, 0.f}, scale[4] = {1.f, 1.f, 1.f, 1.f}, shift[4] = {0.f, 0.f, 0.f, 0.f};
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (n + j < N) {
+            if (EPI == EPI_BIAS_RELU || EPI == EPI_BIAS || EPI == EPI_BIAS_DENORM) bias[j] = ep.bias[n + j];
+            if (EPI == EPI_BIAS_DENORM) {
+                scale[j] = ep.scale[n + j];
+                shift[j] = ep.shift[n + j];
+            }
+        }
+    }
+    const bool whole = n + 4 <= N;
+    const bool vf = ep.outf && (ep.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(ep.outf) & 15) == 0;
+    const bool vb = ep.outb && (ep.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(ep.outb) & 7) == 0;
+    const bool vm = EPI == EPI_RELU_MASK && (ep.ldm & 3) == 0 && (reinterpret_cast<uintptr_t>(ep.mask) & 7) == 0;
+    #pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+        const int m = m0 + warp * 32 + r;
+        if (m >= M || n >= N) continue;
+        const float4 a = *reinterpret_cast<const float4 *>(Sw + r * T_SROW + 4 * lane);
+        float o[4] = {a.x, a.y, a.z, a.w};
+        if (EPI == EPI_RELU_MASK) {
+            float mk[4];
+            if (whole && vm) {
+                const uint2 w = *reinterpret_cast<const uint2 *>(ep.mask + (long long)m * ep.ldm + n);
+                const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&w.x);
+                const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&w.y);
+                mk[0] = __low2float(lo);
+                mk[1] = __high2float(lo);
+                mk[2] = __low2float(hi);
+                mk[3] = __high2float(hi);
+            } else {
+                #pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mk[j] = n + j < N ? __bfloat162float(ep.mask[(long long)m * ep.ldm + n + j]) : 0.f;
+            }
+            #pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = mk[j] > 0.f ? o[j] : 0.f;
+        } else if (EPI != EPI_STORE) {
+            #pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float x = o[j] + bias[j];
+                if (EPI == EPI_BIAS_RELU) x = fmaxf(x, 0.f);
+                if (EPI == EPI_BIAS_DENORM) x = x * scale[j] + shift[j];
+                o[j] = x;
+            }
+        }
+        const long long off = (long long)m * ep.ldc + n;
+        if (ep.outf) {
+            if (whole && vf) {
+                *reinterpret_cast<float4 *>(ep.outf + off) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+                #pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (n + j < N) ep.outf[off + j] = o[j];
+            }
+        }
+        if (ep.outb) {
+            if (whole && vb) {
+                const __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
+                uint2 w;
+                w.x = *reinterpret_cast<const uint32_t *>(&p0);
+                w.y = *reinterpret_cast<const uint32_t *>(&p1);
+                *reinterpret_cast<uint2 *>(ep.outb + off) = w;
+            } else {
+                #pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (n + j < N) ep.outb[off + j] = __float2bfloat16_rn(o[j]);
+            }
+        }
+    }
+}
+
 template <bool AK, bool BKM, int EPI>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda,
                                                    const __nv_bfloat16 *B, int ldb, GemmEpi ep) {
@@ -121,7 +215,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
     uint64_t *bar = reinterpret_cast<uint64_t *>(tsm);   // one per stage
     uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + 64);
     unsigned char *tiles = tsm + T_HDR;
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int t = threadIdx.x, warp = t >> 5;
     const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
     if (t == 0) {
         tc05::mbar_init(&bar[0], 1);
@@ -168,45 +262,104 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
     done = __syncthreads_and(done) != 0;
     tc05::fence_after_sync();
     if (ok && done && issued > 0) {
-        const int m = m0 + warp * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        const bool vf = ep.outf && (ep.ldc & 7) == 0 && (reinterpret_cast<uintptr_t>(ep.outf) & 15) == 0;
-        const bool vb = ep.outb && (ep.ldc & 7) == 0 && (reinterpret_cast<uintptr_t>(ep.outb) & 15) == 0;
-        #pragma unroll 1
-        for (int c = 0; c < TBN / 16; ++c) {
-            const int nb = n0 + c * 16;
-            if (nb >= N) break;   // uniform over the CTA
-            float v[16];
-            tc05::ld_32x32b_x16(trow + (uint32_t)(c * 16), v);
-            if (m >= M) continue;
-            const bool full = nb + 16 <= N;
-            #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = (full || nb + q < N) ? epi_value<EPI>(ep, m, nb + q, v[q]) : 0.f;
-            const long long o = (long long)m * ep.ldc + nb;
-            if (full && vf) {
-                #pragma unroll
-                for (int q = 0; q < 16; q += 4)
-                    *reinterpret_cast<float4 *>(ep.outf + o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-            } else if (ep.outf) {
-                for (int q = 0; q < 16 && nb + q < N; ++q) ep.outf[o + q] = v[q];
-            }
-            if (full && vb) {
-                #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t w[4];
-                    #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const __nv_bfloat162 pq = __floats2bfloat162_rn(v[8 * h + 2 * q], v[8 * h + 2 * q + 1]);
-                        w[q] = *reinterpret_cast<const uint32_t *>(&pq);
-                    }
-                    *reinterpret_cast<uint4 *>(ep.outb + o + 8 * h) = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-            } else if (ep.outb) {
-                for (int q = 0; q < 16 && nb + q < N; ++q) ep.outb[o + q] = __float2bfloat16_rn(v[q]);
-            }
-        }
+        tc_epilogue<EPI>(ep, M, N, m0, n0, tmem, reinterpret_cast<float *>(tiles));
     } else if (t == 0 && ep.err) {
         atomicOr(ep.err, 1);
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc05::tmem_dealloc(tmem, TBN);
+}
+
+// ---------------------------------------------------------------------------
+// TMA path for two K-major operands (the forward and data-gradient
+// products).  Warp-specialised: thread 0 (warp 0) is the producer, which
+// fills a ring of T_NS stages with TMA tensor loads (per operand and block
+// of 64 k, eight boxes of 128 rows x 8 k that land as the same core-matrix
+// layout as above) completing on the stage's "full" mbarrier; thread 32
+// (warp 1) issues the MMAs of a stage once it is full and commits them to
+// the stage's "empty" mbarrier, which the producer waits on before it
+// refills the stage; a final commit to "done" releases the epilogue of all
+// four warps.  Every wait is bounded; a wait that gives up sets ep.err,
+// and before it leaves the CTA waits (bounded) for every copy it issued.
+// ---------------------------------------------------------------------------
+constexpr int T_NS = 3;                                   // stages
+constexpr int T_SMEM_TMA = T_HDR + T_NS * 2 * T_TILE;     // 97 KB: two CTAs per SM
+static_assert(4 * 32 * T_SROW * 4 <= T_SMEM_TMA - T_HDR, "the epilogue's staging fits in the stages");
+
+template <int EPI>
+__global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const __grid_constant__ CUtensorMap tmA,
+                                                    const __grid_constant__ CUtensorMap tmB, GemmEpi ep) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(tsm);   // [T_NS]
+    uint64_t *empty = full + T_NS;                        // [T_NS]
+    uint64_t *done = empty + T_NS;                        // [1]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + 128);
+    unsigned char *tiles = tsm + T_HDR;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+    const int nk = (K + TBK - 1) / TBK;
+    if (t == 0) {
+        for (int s = 0; s < T_NS; ++s) {
+            tc05::mbar_init(&full[s], 1);
+            tc05::mbar_init(&empty[s], 1);
+        }
+        tc05::mbar_init(done, 1);
+        tc05::fence_proxy_async_smem();
+    }
+    if (warp == 0) tc05::tmem_alloc(tslot, TBN);
+    tc05::fence_before_sync();
+    __syncthreads();
+    tc05::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+    int issued = 0;   // blocks whose copies thread 0 issued
+    if (t == 0) {
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % T_NS;
+            if (kb >= T_NS && !tc05::mbar_wait(&empty[s], ((kb / T_NS) - 1) & 1, T_TIMEOUT_NS)) {
+                ok = false;
+                break;
+            }
+            unsigned char *sa = tiles + s * 2 * T_TILE, *sb = sa + T_TILE;
+            tc05::mbar_arrive_expect_tx(&full[s], 2 * T_TILE);
+            #pragma unroll
+            for (int c = 0; c < TBK / 8; ++c) {
+                tc05::tma_load_2d(sa + c * T_LBO, &tmA, kb * TBK + 8 * c, m0, &full[s]);
+                tc05::tma_load_2d(sb + c * T_LBO, &tmB, kb * TBK + 8 * c, n0, &full[s]);
+            }
+            issued = kb + 1;
+        }
+    } else if (t == 32) {
+        constexpr uint32_t idesc = tc05::idesc_bf16_f32<TBM, TBN>();
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % T_NS;
+            if (!tc05::mbar_wait(&full[s], (kb / T_NS) & 1, T_TIMEOUT_NS)) {
+                ok = false;
+                break;
+            }
+            tc05::fence_after_sync();
+            const uint32_t a0 = tc05::smem_addr(tiles + s * 2 * T_TILE), b0 = a0 + T_TILE;
+            #pragma unroll
+            for (int j = 0; j < TBK / 16; ++j)
+                tc05::mma_bf16(tmem, tc05::smem_desc(a0 + 2 * j * T_LBO, T_LBO, T_SBO),
+                               tc05::smem_desc(b0 + 2 * j * T_LBO, T_LBO, T_SBO), idesc, kb > 0 || j > 0);
+            tc05::commit(&empty[s]);
+        }
+        tc05::commit(done);   // covers every MMA issued above
+    }
+    __syncwarp();
+    const bool fin = tc05::mbar_wait(done, 0, T_TIMEOUT_NS);
+    const bool good = __syncthreads_and(ok && fin) != 0;
+    tc05::fence_after_sync();
+    if (good && nk > 0) tc_epilogue<EPI>(ep, M, N, m0, n0, tmem, reinterpret_cast<float *>(tiles));
+    else if (t == 0 && ep.err) atomicOr(ep.err, 1);
+    if (t == 0) {
+        // every stage's last issued copy has landed before the CTA leaves
+        for (int s = 0; s < T_NS && s < issued; ++s) {
+            const int uses = (issued - 1 - s) / T_NS + 1;
+            tc05::mbar_wait(&full[s], (uses - 1) & 1, T_TIMEOUT_NS);
+        }
     }
     tc05::fence_before_sync();
     __syncthreads();
@@ -339,6 +492,50 @@ static cudaError_t gemm_tc_t(int M, int N, int K, const __nv_bfloat16 *A, int ld
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+// (no link-time dependency on the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a K-major BF16 operand X(r, k) = X[r*ld + k], rows x K,
+// boxes of 8 k x 128 rows (16 bytes x 128), zero fill outside.
+static cudaError_t kmajor_map(CUtensorMap *m, const __nv_bfloat16 *X, int rows, int K, int ld) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {8, (cuuint32_t)TBM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(X), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int EPI>
+static cudaError_t gemm_tma_t(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
+                              const GemmEpi &ep, cudaStream_t s) {
+    CUtensorMap ta, tb;
+    cudaError_t e = kmajor_map(&ta, A, M, K, lda);
+    if (e == cudaSuccess) e = kmajor_map(&tb, B, N, K, ldb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_TMA);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
+    k_gemm_tma<EPI><<<grid, 128, T_SMEM_TMA, s>>>(M, N, K, ta, tb, ep);
+    return cudaGetLastError();
+}
+
 // Operand rules of the tensor-core path: 16-byte aligned base, K and ld
 // multiples of 8, ld covering the contiguous extent; an M-major operand's
 // row count a multiple of 8 as well.
@@ -363,7 +560,15 @@ cudaError_t mlp_gemm(int layout, int epi, int M, int N, int K, const __nv_bfloat
         default: return gemm_tc_t<AKv, BKv, EPI_STORE>(M, N, K, A, lda, B, ldb, ep, s);                     \
         }                                                                                                   \
     }
-    FGA_GEMM_CASE(3, true, true)
+    if (layout == 3) {   // both K-major: TMA-fed, warp-specialised
+        switch (epi) {
+        case EPI_BIAS_RELU: return gemm_tma_t<EPI_BIAS_RELU>(M, N, K, A, lda, B, ldb, ep, s);
+        case EPI_BIAS: return gemm_tma_t<EPI_BIAS>(M, N, K, A, lda, B, ldb, ep, s);
+        case EPI_BIAS_DENORM: return gemm_tma_t<EPI_BIAS_DENORM>(M, N, K, A, lda, B, ldb, ep, s);
+        case EPI_RELU_MASK: return gemm_tma_t<EPI_RELU_MASK>(M, N, K, A, lda, B, ldb, ep, s);
+        default: return gemm_tma_t<EPI_STORE>(M, N, K, A, lda, B, ldb, ep, s);
+        }
+    }
     FGA_GEMM_CASE(1, true, false)
     FGA_GEMM_CASE(2, false, true)
     FGA_GEMM_CASE(0, false, false)
