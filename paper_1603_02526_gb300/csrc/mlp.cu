@@ -36,10 +36,9 @@ constexpr int T_TILE = TBM * TBK * 2;        // bytes of one operand block (A an
 constexpr int T_LBO = TBM * 16;              // K-direction distance of core matrices
 constexpr int T_SBO = 128;                   // M/N-direction distance of core matrices
 constexpr int T_HDR = 1024;                  // mbarriers and the tensor-memory address
-// Slack after the four blocks, larger than the furthest byte a descriptor of
-// these tiles can address under either reading of its two byte offsets.
-constexpr int T_GUARD = 32768;
-constexpr int T_SMEM = T_HDR + 4 * T_TILE + T_GUARD;
+// two stages of A and B (64 KB), widened to 96 KB for the epilogue's
+// staging block (4 warps x 32 rows x 132 floats), which reuses them
+constexpr int T_SMEM = T_HDR + 6 * T_TILE;
 constexpr unsigned long long T_TIMEOUT_NS = 1000000000ull;
 
 // Copies rows [r0, r0 + 128) x k [k0, k0 + 64) of X into the block at S
