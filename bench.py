@@ -394,8 +394,9 @@ def run_extras(log=None):
 def run_profile(args):
     """One warm-up and one solve of --profile-iters iterations (the workload
     of the benchmark, or with --profile-workload svm the SVM of the extras,
-    or with mpc_one the slowest instance of the MPC batch alone), at a
-    length that suits an ncu capture."""
+    or with mpc_one the slowest instance of the MPC batch alone, or with
+    mlp_forward the warm-start network's inference), at a length that suits
+    an ncu capture."""
     import torch
     from paper_1603_02526_gb300 import build, inputs, _lib
     from paper_1603_02526_gb300.graph import graph_from_problem
@@ -413,6 +414,22 @@ def run_profile(args):
                                       use_graph=False)
         print("profile run: one MPC instance, %d iterations, %d threads, %.3f ms" % (
             args.profile_iters, args.profile_threads, r["ms"]))
+        return 0
+    if args.profile_workload == "mlp_forward":
+        # the warm-start network (12-256-256-960, random initialisation) on
+        # the 16,384-row evaluation batch, --profile-iters forward passes
+        from paper_1603_02526_gb300.mlp import MLP
+        net = MLP(12, 256, 256, 960, max_batch=16384, seed=5002)
+        xin = torch.randn(16384, 12, device="cuda")
+        yout = torch.empty(16384, 960, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.profile_iters):
+            net.fga_mlp_forward(xin, yout)
+        e1.record()
+        torch.cuda.synchronize()
+        print("profile run: MLP forward, 16384 rows, %d passes, %.3f ms each" % (
+            args.profile_iters, e0.elapsed_time(e1) / args.profile_iters))
         return 0
     if args.profile_workload == "svm":
         p = inputs.svm_problem(100000, 64, seed=3000)
@@ -442,7 +459,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the packing sweep (no SVM / MPC / warm start)")
     ap.add_argument("--zorder", type=int, default=None,
                     help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 disk tiles, 3 hinge bank)")
-    ap.add_argument("--profile-workload", default="packing", choices=["packing", "svm", "mpc_one"])
+    ap.add_argument("--profile-workload", default="packing", choices=["packing", "svm", "mpc_one", "mlp_forward"])
     ap.add_argument("--profile-threads", type=int, default=256, help="CTA size of the mpc_one profiling run")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")

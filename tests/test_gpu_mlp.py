@@ -116,3 +116,50 @@ def test_normalization_stats():
     Z = Yd.cpu().numpy()
     np.testing.assert_allclose(Z.mean(0), 0, atol=1e-4)
     np.testing.assert_allclose(Z.std(0), 1, rtol=1e-4)
+
+
+RAGGED = (5, 24, 40, 72)
+
+
+@pytest.mark.parametrize("batch", [8, 200])
+def test_ragged_network_matches_oracle(batch):
+    """Sizes that fill no GEMM tile (128 x 128 outputs, blocks of 64 k):
+    the tensor maps' zero fill past the edges, partial tiles and the scalar
+    tails of the epilogue, in every product of the forward and backward."""
+    import torch
+    from paper_1603_02526_gb300.mlp import MLP
+    rng = np.random.default_rng(batch)
+    m = MLP(*RAGGED, max_batch=256, seed=21)
+    W1, b1, W2, b2, W3, b3 = mo.unpack(m.fga_mlp_get_params().astype(np.float64), RAGGED)
+    p = mo.pack([W1, rng.standard_normal(b1.size) * 0.1, W2, rng.standard_normal(b2.size) * 0.1, W3,
+                 rng.standard_normal(b3.size) * 0.1])
+    m.fga_mlp_set_params(p.astype(np.float32))
+    p = p.astype(np.float32).astype(np.float64)
+    X = rng.standard_normal((batch, RAGGED[0])).astype(np.float32)
+    T = rng.standard_normal((batch, RAGGED[3])).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    loss, g = m.fga_mlp_gradients(Xd, Td)
+    lo, go = mo.loss_and_grads(p, RAGGED, X.astype(np.float64), T.astype(np.float64), bf16=True)
+    assert loss == pytest.approx(lo, rel=1e-4)
+    for a, b in zip(mo.unpack(g.astype(np.float64), RAGGED), mo.unpack(go, RAGGED)):
+        assert _rel(a, b) < 1e-2, _rel(a, b)
+    Y = torch.empty((batch, RAGGED[3]), device="cuda")
+    m.fga_mlp_forward(Xd, Y)
+    yo = mo.forward(p, RAGGED, X.astype(np.float64), bf16=True)["Y"]
+    assert _rel(Y.cpu().numpy().astype(np.float64), yo) < 5e-3
+
+
+def test_forward_evaluation_batch_sampled_rows():
+    """The 16,384-row inference batch (multi-wave GEMM grids): 512 sampled
+    rows against the oracle (rows are independent)."""
+    import torch
+    from paper_1603_02526_gb300.mlp import MLP
+    rng = np.random.default_rng(5)
+    m = MLP(*SHAPE, max_batch=16384, seed=5)
+    p = m.fga_mlp_get_params().astype(np.float64)
+    X = rng.standard_normal((16384, SHAPE[0])).astype(np.float32)
+    Y = torch.empty((16384, SHAPE[3]), device="cuda")
+    m.fga_mlp_forward(torch.tensor(X, device="cuda"), Y)
+    rows = np.sort(rng.choice(16384, 512, replace=False))
+    yo = mo.forward(p, SHAPE, X[rows].astype(np.float64), bf16=True)["Y"]
+    assert _rel(Y.cpu().numpy()[rows].astype(np.float64), yo) < 5e-3
