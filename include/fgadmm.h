@@ -100,11 +100,19 @@ extern "C" {
                                  disk pairs' state in registers, x is
                                  recomputed from u and the previous z, one
                                  grid-wide barrier per iteration; fused
-                                 launches only.  Default: 0 for FGA_F64; for
-                                 FGA_F32, 2 when the graph qualifies, else
-                                 1.  Asking for 2 on a graph that does not
-                                 qualify makes fga_finalize return
-                                 FGA_EINVAL.                                 */
+                                 launches only; 3 = hinge bank: a linear
+                                 soft-margin SVM only (Sec. V-C: hinge
+                                 factors on one shared (w, b), dim(w) <= 64,
+                                 plus L2 factors on w), FP32, one rho,
+                                 alpha = 1, m not kept -- each CTA keeps its
+                                 slice of the data rows in shared memory and
+                                 one value of state per hinge factor in
+                                 registers, one grid-wide barrier per
+                                 iteration; fused launches only.  Default: 0
+                                 for FGA_F64; for FGA_F32, 2 or 3 when the
+                                 graph qualifies, else 1.  Asking for 2 or 3
+                                 on a graph that does not qualify makes
+                                 fga_finalize return FGA_EINVAL.             */
 #define FGA_OPT_STORE_M 1     /* 1 = keep m per edge so FGA_EDGE_M can be read
                                  back (default 1 for FGA_F64, 0 for FGA_F32)  */
 #define FGA_OPT_BLOCK 2       /* threads per CTA of the sweep (0 = library
@@ -173,7 +181,8 @@ typedef struct {
                                    last one (>= 1)                           */
     int32_t fused;              /* 1 = one persistent kernel for the whole
                                    call; 0 = one launch per update phase
-                                   (FGA_EINVAL in the disk-tile order)      */
+                                   (FGA_EINVAL in the disk-tile and hinge
+                                   orders)                                  */
     int64_t barrier_timeout_ns; /* limit on one grid-wide wait inside the
                                    persistent kernel (0 = 2e9 ns)            */
     int32_t fault_skip_block;   /* testing: >= 0 makes that CTA skip its
