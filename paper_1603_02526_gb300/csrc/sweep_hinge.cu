@@ -91,6 +91,9 @@ static __device__ __forceinline__ void hinge_factors(const HingeArgs &a, const P
     for (int k = 0; k < kHingeK; ++k) {
         const int i = gi + k * kHingeGroups;
         const bool valid = i < C.nf;
+        // the slots past the CTA's last row would change nothing (g = 0, no
+        // state): stop once no group of the warp has a row left
+        if (k > 0 && __all_sync(0xffffffffu, !valid)) break;
         const int f = C.f0 + i;
         float x[8];
         float4 mt = make_float4(0.f, 0.f, 1.f, 0.f);
