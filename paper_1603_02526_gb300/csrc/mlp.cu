@@ -11,7 +11,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
+#include <unordered_map>
 
 #include "mlp_internal.h"
 #include "tc05.cuh"
@@ -481,10 +483,24 @@ inline int nblk(long long n, int t) {
 
 }  // namespace
 
+// The dynamic shared-memory limit of a kernel, raised once per device.
+template <typename F>
+static cudaError_t smem_attr_once(F *fn, int bytes, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 template <bool AK, bool BKM, int EPI>
 static cudaError_t gemm_tc_t(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
                              const GemmEpi &ep, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AK, BKM, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM);
+    static std::atomic<unsigned long long> attr_set{0};
+    cudaError_t e = smem_attr_once(k_gemm_tc<AK, BKM, EPI>, T_SMEM, attr_set);
     if (e != cudaSuccess) return e;
     dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
     k_gemm_tc<AK, BKM, EPI><<<grid, 128, T_SMEM, s>>>(M, N, K, A, lda, B, ldb, ep);
@@ -508,8 +524,35 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 }
 
 // Tensor map of a K-major BF16 operand X(r, k) = X[r*ld + k], rows x K,
-// boxes of 8 k x 128 rows (16 bytes x 128), zero fill outside.
+// boxes of 8 k x 128 rows (16 bytes x 128), zero fill outside.  A map is a
+// pure function of (address, rows, K, ld), so maps are kept in a small
+// cache: the network's operands live in buffers it owns, and a training
+// step reuses the same few dozen maps.
+struct MapKey {
+    const void *p;
+    int rows, K, ld;
+    bool operator==(const MapKey &o) const { return p == o.p && rows == o.rows && K == o.K && ld == o.ld; }
+};
+struct MapKeyHash {
+    size_t operator()(const MapKey &k) const {
+        size_t h = std::hash<const void *>()(k.p);
+        h ^= (size_t)k.rows * 0x9E3779B97F4A7C15ull + (size_t)k.K * 0xC2B2AE3D27D4EB4Full + (size_t)k.ld;
+        return h;
+    }
+};
+
 static cudaError_t kmajor_map(CUtensorMap *m, const __nv_bfloat16 *X, int rows, int K, int ld) {
+    static std::mutex mu;
+    static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> cache;
+    const MapKey key{X, rows, K, ld};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *m = it->second;
+            return cudaSuccess;
+        }
+    }
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
     if (!fn) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
@@ -519,16 +562,21 @@ static cudaError_t kmajor_map(CUtensorMap *m, const __nv_bfloat16 *X, int rows, 
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(X), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() > 4096) cache.clear();
+    cache.emplace(key, *m);
+    return cudaSuccess;
 }
 
 template <int EPI>
 static cudaError_t gemm_tma_t(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
                               const GemmEpi &ep, cudaStream_t s) {
+    static std::atomic<unsigned long long> attr_set{0};
     CUtensorMap ta, tb;
     cudaError_t e = kmajor_map(&ta, A, M, K, lda);
     if (e == cudaSuccess) e = kmajor_map(&tb, B, N, K, ldb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM_TMA);
+    if (e == cudaSuccess) e = smem_attr_once(k_gemm_tma<EPI>, T_SMEM_TMA, attr_set);
     if (e != cudaSuccess) return e;
     dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
     k_gemm_tma<EPI><<<grid, 128, T_SMEM_TMA, s>>>(M, N, K, ta, tb, ep);
