@@ -1,5 +1,6 @@
 // fga_mlp.cpp -- host side of the warm-start MLP (C-ABI): parameters,
 // buffers, forward, backward, Adam.  All arithmetic runs in mlp.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -78,6 +79,8 @@ struct fga_mlp {
     Layer L[3];
     DBuf xb, a1, a2, y, dyf, dyb, d2, d1, loss_part, mean, stdv;
     DBuf err;                 // int: a tensor-core wait of a GEMM timed out
+    DBuf ws;                  // split-K partials of the products of small batches
+    long long ws_floats = 0;
     bool normalized = false;
     long long step = 0;
     int nparts = 256;
@@ -139,6 +142,12 @@ extern "C" int fga_mlp_create(fga_mlp **outp, int32_t in, int32_t h1, int32_t h2
     MCUDA(m->mean.alloc((size_t)out * 4));
     MCUDA(m->stdv.alloc((size_t)out * 4));
     MCUDA(m->err.alloc(sizeof(int)));
+    {
+        const long long mn = std::max<long long>(std::max<long long>((long long)out * h2, (long long)h2 * h1),
+                                                 (long long)h1 * m->in_pad);
+        m->ws_floats = 16 * mn;
+        MCUDA(m->ws.alloc((size_t)m->ws_floats * sizeof(float)));
+    }
     // He initialisation (seeded), zero biases, zero padding columns
     Rng rng{seed};
     int dims[3][2] = {{h1, in}, {h2, h1}, {out, h2}};
@@ -231,6 +240,8 @@ static GemmEpi epi0(fga_mlp *m) {
     GemmEpi e;
     std::memset(&e, 0, sizeof e);
     e.err = m->err.as<int>();
+    e.ws = m->ws.as<float>();        // split-K partials (products of small batches)
+    e.ws_floats = m->ws_floats;
     return e;
 }
 

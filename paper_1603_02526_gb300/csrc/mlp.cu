@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstring>
 #include <atomic>
 #include <mutex>
 #include <unordered_map>
@@ -228,7 +230,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
     tc05::fence_after_sync();
     const uint32_t tmem = *tslot;
     constexpr uint32_t idesc = tc05::idesc_bf16_f32<TBM, TBN>();
-    const int nk = (K + TBK - 1) / TBK;
+    // split K: slice blockIdx.z takes the blocks [kbeg, kbeg + nk)
+    const int nk_all = (K + TBK - 1) / TBK;
+    const int per = (nk_all + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int kbeg = (int)blockIdx.z * per;
+    const int nk = max(0, min(nk_all, kbeg + per) - kbeg);
     bool ok = true;
     int issued = 0;   // K blocks committed
     for (int kb = 0; kb < nk; ++kb) {
@@ -242,8 +248,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
                 break;
             }
         }
-        tc_stage<AK>(sa, A, lda, M, K, m0, kb * TBK);
-        tc_stage<BKM>(sb, B, ldb, N, K, n0, kb * TBK);
+        tc_stage<AK>(sa, A, lda, M, K, m0, (kbeg + kb) * TBK);
+        tc_stage<BKM>(sb, B, ldb, N, K, n0, (kbeg + kb) * TBK);
         tc05::fence_proxy_async_smem();
         __syncthreads();
         if (t == 0) {
@@ -263,7 +269,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
     done = __syncthreads_and(done) != 0;
     tc05::fence_after_sync();
     if (ok && done && issued > 0) {
-        tc_epilogue<EPI>(ep, M, N, m0, n0, tmem, reinterpret_cast<float *>(tiles));
+        GemmEpi e = ep;
+        if (gridDim.z > 1) e.outf = ep.outf + (long long)blockIdx.z * M * ep.ldc;   // this slice's partial
+        tc_epilogue<EPI>(e, M, N, m0, n0, tmem, reinterpret_cast<float *>(tiles));
     } else if (t == 0 && ep.err) {
         atomicOr(ep.err, 1);
     }
@@ -299,7 +307,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const 
     unsigned char *tiles = tsm + T_HDR;
     const int t = threadIdx.x, warp = t >> 5;
     const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
-    const int nk = (K + TBK - 1) / TBK;
+    // split K: slice blockIdx.z takes the blocks [kbeg, kbeg + nk)
+    const int nk_all = (K + TBK - 1) / TBK;
+    const int per = (nk_all + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int kbeg = (int)blockIdx.z * per;
+    const int nk = max(0, min(nk_all, kbeg + per) - kbeg);
     if (t == 0) {
         for (int s = 0; s < T_NS; ++s) {
             tc05::mbar_init(&full[s], 1);
@@ -326,8 +338,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const 
             tc05::mbar_arrive_expect_tx(&full[s], 2 * T_TILE);
             #pragma unroll
             for (int c = 0; c < TBK / 8; ++c) {
-                tc05::tma_load_2d(sa + c * T_LBO, &tmA, kb * TBK + 8 * c, m0, &full[s]);
-                tc05::tma_load_2d(sb + c * T_LBO, &tmB, kb * TBK + 8 * c, n0, &full[s]);
+                tc05::tma_load_2d(sa + c * T_LBO, &tmA, (kbeg + kb) * TBK + 8 * c, m0, &full[s]);
+                tc05::tma_load_2d(sb + c * T_LBO, &tmB, (kbeg + kb) * TBK + 8 * c, n0, &full[s]);
             }
             issued = kb + 1;
         }
@@ -353,7 +365,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const 
     const bool fin = tc05::mbar_wait(done, 0, T_TIMEOUT_NS);
     const bool good = __syncthreads_and(ok && fin) != 0;
     tc05::fence_after_sync();
-    if (good && nk > 0) tc_epilogue<EPI>(ep, M, N, m0, n0, tmem, reinterpret_cast<float *>(tiles));
+    if (good && nk > 0) {
+        GemmEpi e = ep;
+        if (gridDim.z > 1) e.outf = ep.outf + (long long)blockIdx.z * M * ep.ldc;   // this slice's partial
+        tc_epilogue<EPI>(e, M, N, m0, n0, tmem, reinterpret_cast<float *>(tiles));
+    }
     else if (t == 0 && ep.err) atomicOr(ep.err, 1);
     if (t == 0) {
         // every stage's last issued copy has landed before the CTA leaves
@@ -365,6 +381,29 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const 
     tc05::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc05::tmem_dealloc(tmem, TBN);
+}
+
+// The split-K slices' sums, added in slice order, through the element
+// epilogue EPI: v = sum_z ws[z][m][n], then bias / ReLU / mask /
+// de-standardise as in tc_epilogue, stored as FP32 and/or BF16.
+template <int EPI>
+__global__ void k_split_sum(const float *ws, int S, int M, int N, GemmEpi ep) {
+    const long long n_el = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_el; i += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < S; ++z) v += ws[z * n_el + i];
+        const int m = (int)(i / N), n = (int)(i % N);
+        if (EPI == EPI_BIAS_RELU || EPI == EPI_BIAS || EPI == EPI_BIAS_DENORM) {
+            v += ep.bias[n];
+            if (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
+            if (EPI == EPI_BIAS_DENORM) v = v * ep.scale[n] + ep.shift[n];
+        } else if (EPI == EPI_RELU_MASK) {
+            v = __bfloat162float(ep.mask[(long long)m * ep.ldm + n]) > 0.f ? v : 0.f;
+        }
+        const long long o = (long long)m * ep.ldc + n;
+        if (ep.outf) ep.outf[o] = v;
+        if (ep.outb) ep.outb[o] = __float2bfloat16_rn(v);
+    }
 }
 
 __global__ void k_to_bf16_pad(const float *X, int rows, int cols, int ldo, __nv_bfloat16 *out) {
@@ -498,11 +537,11 @@ static cudaError_t smem_attr_once(F *fn, int bytes, std::atomic<unsigned long lo
 
 template <bool AK, bool BKM, int EPI>
 static cudaError_t gemm_tc_t(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
-                             const GemmEpi &ep, cudaStream_t s) {
+                             const GemmEpi &ep, cudaStream_t s, int S) {
     static std::atomic<unsigned long long> attr_set{0};
     cudaError_t e = smem_attr_once(k_gemm_tc<AK, BKM, EPI>, T_SMEM, attr_set);
     if (e != cudaSuccess) return e;
-    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
+    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, S);
     k_gemm_tc<AK, BKM, EPI><<<grid, 128, T_SMEM, s>>>(M, N, K, A, lda, B, ldb, ep);
     return cudaGetLastError();
 }
@@ -571,14 +610,14 @@ static cudaError_t kmajor_map(CUtensorMap *m, const __nv_bfloat16 *X, int rows, 
 
 template <int EPI>
 static cudaError_t gemm_tma_t(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
-                              const GemmEpi &ep, cudaStream_t s) {
+                              const GemmEpi &ep, cudaStream_t s, int S) {
     static std::atomic<unsigned long long> attr_set{0};
     CUtensorMap ta, tb;
     cudaError_t e = kmajor_map(&ta, A, M, K, lda);
     if (e == cudaSuccess) e = kmajor_map(&tb, B, N, K, ldb);
     if (e == cudaSuccess) e = smem_attr_once(k_gemm_tma<EPI>, T_SMEM_TMA, attr_set);
     if (e != cudaSuccess) return e;
-    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
+    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, S);
     k_gemm_tma<EPI><<<grid, 128, T_SMEM_TMA, s>>>(M, N, K, ta, tb, ep);
     return cudaGetLastError();
 }
@@ -591,36 +630,64 @@ static bool operand_ok(const __nv_bfloat16 *X, int ld, int rows, int K, bool kma
     return kmaj ? ld >= K : (rows % 8 == 0 && ld >= rows);
 }
 
+// Split-K factor: about one wave of CTAs when the tile grid is small (the
+// products of a training batch), K long enough (at least 8 blocks) for the
+// shorter slices to pay for the slice sum, and a workspace for the slices'
+// partials is given; every slice non-empty; 1 otherwise.
+static int split_factor(int M, int N, int K, const GemmEpi &ep) {
+    const int tiles = ((N + TBN - 1) / TBN) * ((M + TBM - 1) / TBM), nk = (K + TBK - 1) / TBK;
+    if (!ep.ws || nk < 8) return 1;
+    int S = std::min(std::min(nk, 16), std::max(1, 148 / tiles));
+    while (S > 1 && (long long)S * M * N > ep.ws_floats) --S;
+    if (S > 1) {
+        const int per = (nk + S - 1) / S;
+        S = (nk + per - 1) / per;
+    }
+    return S;
+}
+
+template <int EPI>
+static cudaError_t gemm_launch(int layout, int M, int N, int K, const __nv_bfloat16 *A, int lda,
+                               const __nv_bfloat16 *B, int ldb, const GemmEpi &ep, cudaStream_t s, int S) {
+    switch (layout) {   // bit 0: A is K-major, bit 1: B is K-major
+    case 3: return gemm_tma_t<EPI>(M, N, K, A, lda, B, ldb, ep, s, S);   // TMA-fed, warp-specialised
+    case 1: return gemm_tc_t<true, false, EPI>(M, N, K, A, lda, B, ldb, ep, s, S);
+    case 2: return gemm_tc_t<false, true, EPI>(M, N, K, A, lda, B, ldb, ep, s, S);
+    case 0: return gemm_tc_t<false, false, EPI>(M, N, K, A, lda, B, ldb, ep, s, S);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int EPI>
+static cudaError_t gemm_epi(int layout, int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
+                            int ldb, const GemmEpi &ep, cudaStream_t s) {
+    const int S = split_factor(M, N, K, ep);
+    if (S <= 1) return gemm_launch<EPI>(layout, M, N, K, A, lda, B, ldb, ep, s, 1);
+    // slices write raw sums; the slice sum applies the epilogue
+    GemmEpi part;
+    std::memset(&part, 0, sizeof part);
+    part.outf = ep.ws;
+    part.ldc = N;
+    part.err = ep.err;
+    cudaError_t e = gemm_launch<EPI_STORE>(layout, M, N, K, A, lda, B, ldb, part, s, S);
+    if (e != cudaSuccess) return e;
+    const long long n_el = (long long)M * N;
+    k_split_sum<EPI><<<(int)std::min<long long>((n_el + 255) / 256, 1184), 256, 0, s>>>(ep.ws, S, M, N, ep);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_gemm(int layout, int epi, int M, int N, int K, const __nv_bfloat16 *A, int lda,
                      const __nv_bfloat16 *B, int ldb, const GemmEpi &ep, cudaStream_t s) {
-    // layout: bit 0 = A is K-major, bit 1 = B is K-major
-    if (M < 1 || N < 1 || K < 8 || K % 8 || ep.ldc < N || !operand_ok(A, lda, M, K, layout & 1) ||
-        !operand_ok(B, ldb, N, K, (layout >> 1) & 1))
+    if (layout < 0 || layout > 3 || M < 1 || N < 1 || K < 8 || K % 8 || ep.ldc < N ||
+        !operand_ok(A, lda, M, K, layout & 1) || !operand_ok(B, ldb, N, K, (layout >> 1) & 1))
         return cudaErrorInvalidValue;
-#define FGA_GEMM_CASE(L, AKv, BKv)                                                                          \
-    if (layout == L) {                                                                                      \
-        switch (epi) {                                                                                      \
-        case EPI_BIAS_RELU: return gemm_tc_t<AKv, BKv, EPI_BIAS_RELU>(M, N, K, A, lda, B, ldb, ep, s);      \
-        case EPI_BIAS: return gemm_tc_t<AKv, BKv, EPI_BIAS>(M, N, K, A, lda, B, ldb, ep, s);                \
-        case EPI_BIAS_DENORM: return gemm_tc_t<AKv, BKv, EPI_BIAS_DENORM>(M, N, K, A, lda, B, ldb, ep, s);  \
-        case EPI_RELU_MASK: return gemm_tc_t<AKv, BKv, EPI_RELU_MASK>(M, N, K, A, lda, B, ldb, ep, s);      \
-        default: return gemm_tc_t<AKv, BKv, EPI_STORE>(M, N, K, A, lda, B, ldb, ep, s);                     \
-        }                                                                                                   \
+    switch (epi) {
+    case EPI_BIAS_RELU: return gemm_epi<EPI_BIAS_RELU>(layout, M, N, K, A, lda, B, ldb, ep, s);
+    case EPI_BIAS: return gemm_epi<EPI_BIAS>(layout, M, N, K, A, lda, B, ldb, ep, s);
+    case EPI_BIAS_DENORM: return gemm_epi<EPI_BIAS_DENORM>(layout, M, N, K, A, lda, B, ldb, ep, s);
+    case EPI_RELU_MASK: return gemm_epi<EPI_RELU_MASK>(layout, M, N, K, A, lda, B, ldb, ep, s);
+    default: return gemm_epi<EPI_STORE>(layout, M, N, K, A, lda, B, ldb, ep, s);
     }
-    if (layout == 3) {   // both K-major: TMA-fed, warp-specialised
-        switch (epi) {
-        case EPI_BIAS_RELU: return gemm_tma_t<EPI_BIAS_RELU>(M, N, K, A, lda, B, ldb, ep, s);
-        case EPI_BIAS: return gemm_tma_t<EPI_BIAS>(M, N, K, A, lda, B, ldb, ep, s);
-        case EPI_BIAS_DENORM: return gemm_tma_t<EPI_BIAS_DENORM>(M, N, K, A, lda, B, ldb, ep, s);
-        case EPI_RELU_MASK: return gemm_tma_t<EPI_RELU_MASK>(M, N, K, A, lda, B, ldb, ep, s);
-        default: return gemm_tma_t<EPI_STORE>(M, N, K, A, lda, B, ldb, ep, s);
-        }
-    }
-    FGA_GEMM_CASE(1, true, false)
-    FGA_GEMM_CASE(2, false, true)
-    FGA_GEMM_CASE(0, false, false)
-#undef FGA_GEMM_CASE
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t mlp_to_bf16_pad(const float *X, int rows, int cols, int ldo, __nv_bfloat16 *out, cudaStream_t s) {

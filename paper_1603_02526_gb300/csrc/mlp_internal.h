@@ -24,6 +24,8 @@ struct GemmEpi {
     __nv_bfloat16 *outb;    // BF16 output (may be null)
     int ldc;
     int *err;               // device word: set to 1 when a wait of the tensor-core path timed out (may be null)
+    float *ws;              // split-K workspace for products with few output tiles (may be null)
+    long long ws_floats;    // its capacity
 };
 
 cudaError_t mlp_gemm(int layout, int epi, int M, int N, int K, const __nv_bfloat16 *A, int lda,
