@@ -99,6 +99,17 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=3.0):
+        """Blocks until nvidia-smi has printed its first sample (it takes a
+        moment to start), so that the timed region is sampled from its start."""
+        t = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t < timeout:
+            time.sleep(0.01)
+
+    def mark(self):
+        """The timed region starts: later stop() uses only the samples after this."""
+        self.n0 = len(self.lines)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -109,7 +120,9 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        n0 = getattr(self, "n0", 0)
+        lines = self.lines[n0:] if len(self.lines) > n0 else self.lines[-1:]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -230,9 +243,11 @@ def run_ours(args):
         r = one_step()
     assert r["iters"] == ITERS, r
     sampler = ClockSampler(local)
+    sampler.start()
+    sampler.wait_first()
     _barrier(ws)
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.mark()
     t0 = time.perf_counter()
     dev_ms = []
     for _ in range(args.steps):
@@ -451,7 +466,7 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=200)
