@@ -284,8 +284,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const _
 // TMA path for two K-major operands (the forward and data-gradient
 // products).  Warp-specialised: thread 0 (warp 0) is the producer, which
 // fills a ring of T_NS stages with TMA tensor loads (per operand and block
-// of 64 k, eight boxes of 128 rows x 8 k that land as the same core-matrix
-// layout as above) completing on the stage's "full" mbarrier; thread 32
+// of 64 k, one box of 128 rows x 128 bytes in the 128-byte swizzled layout,
+// every stage on a 1024-byte boundary) completing on the stage's "full"
+// mbarrier; thread 32
 // (warp 1) issues the MMAs of a stage once it is full and commits them to
 // the stage's "empty" mbarrier, which the producer waits on before it
 // refills the stage; a final commit to "done" releases the epilogue of all
@@ -311,7 +312,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const 
     const int nk_all = (K + TBK - 1) / TBK;
     const int per = (nk_all + (int)gridDim.z - 1) / (int)gridDim.z;
     const int kbeg = (int)blockIdx.z * per;
-    const int nk = max(0, min(nk_all, kbeg + per) - kbeg);
+    // the swizzled stages must start on 1024-byte boundaries: otherwise no
+    // copy and no MMA is issued and the error word is set
+    const bool aligned = (tc05::smem_addr(tiles) & 1023u) == 0;
+    const int nk = aligned ? max(0, min(nk_all, kbeg + per) - kbeg) : 0;
+    if (t == 0 && !aligned && ep.err) atomicOr(ep.err, 1);
     if (t == 0) {
         for (int s = 0; s < T_NS; ++s) {
             tc05::mbar_init(&full[s], 1);
@@ -336,11 +341,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const 
             }
             unsigned char *sa = tiles + s * 2 * T_TILE, *sb = sa + T_TILE;
             tc05::mbar_arrive_expect_tx(&full[s], 2 * T_TILE);
-            #pragma unroll
-            for (int c = 0; c < TBK / 8; ++c) {
-                tc05::tma_load_2d(sa + c * T_LBO, &tmA, (kbeg + kb) * TBK + 8 * c, m0, &full[s]);
-                tc05::tma_load_2d(sb + c * T_LBO, &tmB, (kbeg + kb) * TBK + 8 * c, n0, &full[s]);
-            }
+            tc05::tma_load_2d(sa, &tmA, (kbeg + kb) * TBK, m0, &full[s]);
+            tc05::tma_load_2d(sb, &tmB, (kbeg + kb) * TBK, n0, &full[s]);
             issued = kb + 1;
         }
     } else if (t == 32) {
@@ -354,9 +356,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tma(int M, int N, int K, const 
             tc05::fence_after_sync();
             const uint32_t a0 = tc05::smem_addr(tiles + s * 2 * T_TILE), b0 = a0 + T_TILE;
             #pragma unroll
-            for (int j = 0; j < TBK / 16; ++j)
-                tc05::mma_bf16(tmem, tc05::smem_desc(a0 + 2 * j * T_LBO, T_LBO, T_SBO),
-                               tc05::smem_desc(b0 + 2 * j * T_LBO, T_LBO, T_SBO), idesc, kb > 0 || j > 0);
+            for (int j = 0; j < TBK / 16; ++j)   // K step of 16 bf16 = 32 bytes inside the swizzle atom
+                tc05::mma_bf16(tmem, tc05::smem_desc_sw128(a0 + 32 * j), tc05::smem_desc_sw128(b0 + 32 * j), idesc,
+                               kb > 0 || j > 0);
             tc05::commit(&empty[s]);
         }
         tc05::commit(done);   // covers every MMA issued above
@@ -563,7 +565,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 }
 
 // Tensor map of a K-major BF16 operand X(r, k) = X[r*ld + k], rows x K,
-// boxes of 8 k x 128 rows (16 bytes x 128), zero fill outside.  A map is a
+// boxes of 64 k x 128 rows (128 bytes x 128) written in the 128-byte
+// swizzled layout, zero fill outside.  A map is a
 // pure function of (address, rows, K, ld), so maps are kept in a small
 // cache: the network's operands live in buffers it owns, and a training
 // step reuses the same few dozen maps.
@@ -596,10 +599,10 @@ static cudaError_t kmajor_map(CUtensorMap *m, const __nv_bfloat16 *X, int rows, 
     if (!fn) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
-    const cuuint32_t box[2] = {8, (cuuint32_t)TBM};
+    const cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)TBM};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(X), dims, strides, box,
-                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     std::lock_guard<std::mutex> lk(mu);

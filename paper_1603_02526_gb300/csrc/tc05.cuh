@@ -34,6 +34,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
+// Descriptor of a K-major operand in the 128-byte swizzled layout that a
+// TMA load with CU_TENSOR_MAP_SWIZZLE_128B writes: rows of 128 bytes (64
+// bf16), the 16-byte chunks of row r stored at chunk ^ (r % 8), groups of 8
+// rows 1024 bytes apart (the stride offset); the leading offset is unused
+// (one swizzle atom spans the K of an instruction) and set to 16 bytes;
+// layout type 2 at bits 61..63.  The atom must start on a 1024-byte
+// boundary; a K step of 16 elements advances addr by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both
 // operands K-major, dense, no negation: D format at bits 4..5, A/B formats
 // at 7..9 / 10..12, N / 8 at 17..22, M / 16 at 24..28.
