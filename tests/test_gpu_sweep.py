@@ -191,12 +191,15 @@ def test_f32_is_deterministic():
     assert np.array_equal(a.fga_read_edge_state(_lib.FGA_EDGE_U), b.fga_read_edge_state(_lib.FGA_EDGE_U))
 
 
-def test_barrier_time_limit_returns_timeout_and_recovers():
-    """Fault injection: one CTA skips its first barrier arrival; the bounded
-    wait runs out (50 ms) and fga_iterate returns FGA_ETIMEOUT.  The context
+@pytest.mark.parametrize("kind,zorder", [("packing", 1), ("packing", 2), ("svm", 3)])
+def test_barrier_time_limit_returns_timeout_and_recovers(kind, zorder):
+    """Fault injection, in each fused kernel (chunked order, disk tiles,
+    hinge bank): one CTA skips its first barrier arrival; the bounded wait
+    runs out (50 ms) and fga_iterate returns FGA_ETIMEOUT.  The context
     stays usable: after fga_init the same graph iterates normally."""
-    p = inputs.packing_problem(200)
-    g = graph_from_problem(p, "f32")
+    p = inputs.packing_problem(200) if kind == "packing" else inputs.svm_problem(3000, 32, seed=3600)
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_ZORDER: zorder})
+    assert g.fga_launch_info()["zorder"] == zorder
     r = g.fga_iterate(10, barrier_timeout_ns=50_000_000, fault_skip_block=0, raise_on_error=False)
     assert r["rc"] == _lib.FGA_ETIMEOUT and r["status"] == _lib.FGA_ETIMEOUT
     with pytest.raises(_lib.FgaError):
