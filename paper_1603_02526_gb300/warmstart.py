@@ -76,42 +76,67 @@ def evaluate(net, n_eval=16384, x0_seed=5003, system_seed=5000, T=30, tol=1e-4, 
     inference, warm-start map, solve with an iteration budget (default: the
     99th percentile of cold iterations on a calibration set), then every
     instance that missed the budget re-solved from cold; all of it timed.
-    Both timed regions end with the per-instance counters on the host; the
-    solutions (z, u) are read afterwards for the comparison."""
+    Both timed arms run in the configuration the autotuner picks on the
+    calibration set (CTA size, check interval), each after one untimed
+    warm-up solve (CUDA-graph capture), and end with the per-instance
+    counters on the host; iteration statistics are given both at that check
+    interval (the timed runs) and exactly (untimed runs checking every
+    iteration).  The solutions (z, u) are read afterwards."""
     import torch
+    dc = inputs.mpc_warmstart_inputs(calib, system_seed=system_seed, x0_seed=x0_seed + 100, T=T)
+    bc = _batch(dc)
     if budget is None:
-        dc = inputs.mpc_warmstart_inputs(calib, system_seed=system_seed, x0_seed=x0_seed + 100, T=T)
-        bc = _batch(dc)
-        bc.fga_mpc_batch_solve(max_iters, tol=tol, check_every=1)
-        budget = int(np.percentile(bc.fga_mpc_batch_read()["iters"], 99))
+        bc.fga_mpc_batch_solve(max_iters, tol=tol, check_every=1, use_graph=False)
+        budget = int(np.percentile(bc.fga_mpc_batch_read(state=False)["iters"], 99))
+        bc.fga_mpc_batch_init()
+    th, ce = bc.fga_mpc_batch_autotune(max_iters, tol)
     d = inputs.mpc_warmstart_inputs(n_eval, system_seed=system_seed, x0_seed=x0_seed, T=T)
     ld = 2 * (d["nx"] + d["nu"]) * T
-    # cold
+    X = torch.tensor(d["x0"], dtype=torch.float32, device="cuda")
+    pred = torch.empty((n_eval, ld), dtype=torch.float32, device="cuda")
+
+    def fallback(status, check_every, use_graph):
+        miss = np.nonzero(status != 0)[0]
+        it = np.zeros(n_eval, dtype=np.int64)
+        if miss.size:
+            dm = dict(d, x0=d["x0"][miss], T=d["T"][miss])
+            bm = _batch(dm)
+            bm.fga_mpc_batch_solve(max_iters, tol=tol, check_every=check_every, threads=th, use_graph=use_graph)
+            it[miss] = bm.fga_mpc_batch_read(state=False)["iters"]
+        return miss, it
+
+    # exact iteration counts (untimed; residuals checked every iteration)
+    be = _batch(d)
+    be.fga_mpc_batch_solve(max_iters, tol=tol, check_every=1, threads=th, use_graph=False)
+    it_cold_exact = be.fga_mpc_batch_read(state=False)["iters"]
+    be.fga_mpc_batch_init()
+    net.fga_mlp_forward(X, pred)
+    be.fga_mpc_batch_warm_start(pred, ld)
+    be.fga_mpc_batch_solve(budget, tol=tol, check_every=1, threads=th, use_graph=False)
+    we = be.fga_mpc_batch_read(state=False)
+    it_warm_exact = we["iters"] + fallback(we["status"], 1, False)[1]
+    del be
+    # cold, timed
     bcold = _batch(d)
+    bcold.fga_mpc_batch_solve(max_iters, tol=tol, check_every=ce, threads=th)   # warm-up: graph capture
+    bcold.fga_mpc_batch_init()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rc = bcold.fga_mpc_batch_solve(max_iters, tol=tol, check_every=1)
+    rc = bcold.fga_mpc_batch_solve(max_iters, tol=tol, check_every=ce, threads=th)
     cold = bcold.fga_mpc_batch_read(state=False)
     t_cold = time.perf_counter() - t0
     cold["z"] = bcold.fga_mpc_batch_read()["z"]
-    # warm
-    X = torch.tensor(d["x0"], dtype=torch.float32, device="cuda")
-    pred = torch.empty((n_eval, ld), dtype=torch.float32, device="cuda")
+    # warm, timed
     bwarm = _batch(d)
+    bwarm.fga_mpc_batch_solve(budget, tol=tol, check_every=ce, threads=th)      # warm-up: graph capture
+    bwarm.fga_mpc_batch_init()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     net.fga_mlp_forward(X, pred)
     bwarm.fga_mpc_batch_warm_start(pred, ld)
-    rw = bwarm.fga_mpc_batch_solve(budget, tol=tol, check_every=1)
+    rw = bwarm.fga_mpc_batch_solve(budget, tol=tol, check_every=ce, threads=th)
     warm = bwarm.fga_mpc_batch_read(state=False)
-    miss = np.nonzero(warm["status"] != 0)[0]
-    fb_iters = np.zeros(n_eval, dtype=np.int64)
-    if miss.size:
-        dm = dict(d, x0=d["x0"][miss], T=d["T"][miss])
-        bm = _batch(dm)
-        bm.fga_mpc_batch_solve(max_iters, tol=tol, check_every=1)
-        fb = bm.fga_mpc_batch_read(state=False)
-        fb_iters[miss] = fb["iters"]
+    miss, fb_iters = fallback(warm["status"], ce, False)
     torch.cuda.synchronize()
     t_warm = time.perf_counter() - t0
     warm["z"] = bwarm.fga_mpc_batch_read()["z"]
@@ -119,11 +144,15 @@ def evaluate(net, n_eval=16384, x0_seed=5003, system_seed=5000, T=30, tol=1e-4, 
     it_warm = warm["iters"] + fb_iters
     # the warm solutions are the cold ones (same optimum, same tolerance)
     dz = np.abs(warm["z"] - cold["z"]).max() if miss.size == 0 else None
-    return dict(n=n_eval, budget=budget, misses=int(miss.size),
-                cold=dict(solves_per_s=n_eval / t_cold, s=t_cold, device_ms=rc["ms"], iters_mean=float(it_cold.mean()),
-                          iters_p50=float(np.percentile(it_cold, 50)), iters_p99=float(np.percentile(it_cold, 99)),
-                          converged=int((cold["status"] == 0).sum())),
+
+    def stats(it):
+        return dict(iters_mean=float(it.mean()), iters_p50=float(np.percentile(it, 50)),
+                    iters_p99=float(np.percentile(it, 99)))
+
+    return dict(n=n_eval, budget=budget, misses=int(miss.size), threads=th, check_every=ce,
+                cold=dict(solves_per_s=n_eval / t_cold, s=t_cold, device_ms=rc["ms"],
+                          converged=int((cold["status"] == 0).sum()), at_check_interval=stats(it_cold),
+                          **stats(it_cold_exact)),
                 warm=dict(solves_per_s=n_eval / t_warm, s=t_warm, device_ms_solve=rw["ms"],
-                          iters_mean=float(it_warm.mean()), iters_p50=float(np.percentile(it_warm, 50)),
-                          iters_p99=float(np.percentile(it_warm, 99))),
+                          at_check_interval=stats(it_warm), **stats(it_warm_exact)),
                 max_abs_dz_warm_vs_cold=None if dz is None else float(dz))
