@@ -851,11 +851,26 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     if (a.zorder == 0) {
-        // canonical: one thread per variable, edges one by one in creation order
-        for (long long b = gtid; b < a.nz; b += gstride) {
+        // canonical: one warp per variable; the lanes load 32 consecutive
+        // values of the variable's row at a time (the next 32 requested
+        // before these are added) and every lane adds them one by one in
+        // creation order from shuffles, so each lane holds exactly the
+        // serial sum; lane 0 stores z.  The chain of additions, not a memory
+        // round trip per value, sets the time.
+        const int lane = threadIdx.x & 31;
+        const long long wid = gtid >> 5, nw = gstride >> 5;
+        for (long long b = wid; b < a.nz; b += nw) {
+            const int k0 = a.row[b], k1 = a.row[b + 1];
             R S = R(0);
-            for (int k = a.row[b]; k < a.row[b + 1]; ++k) S += ldg_l2(a.pvm + k);
-            z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
+            R cur = k0 + lane < k1 ? ldg_l2(a.pvm + k0 + lane) : R(0);
+            for (int k = k0; k < k1; k += 32) {
+                const R nxt = k + 32 + lane < k1 ? ldg_l2(a.pvm + k + 32 + lane) : R(0);
+                const int cnt = k1 - k < 32 ? k1 - k : 32;
+                #pragma unroll 8
+                for (int t = 0; t < cnt; ++t) S += __shfl_sync(0xffffffffu, cur, t);
+                cur = nxt;
+            }
+            if (lane == 0) z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
         }
         return;
     }
