@@ -1045,7 +1045,7 @@ extern "C" int fga_finalize(fga_graph *g) {
     int dev_sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
     g->blk = g->block ? g->block : 256;
-    g->smem = g->zorder == 1 ? chunk_smem((int)g->rsize()).total : 0;
+    g->smem = g->zorder == 1 ? chunk_smem((int)g->rsize()).total : canonical_z_smem((int)g->rsize());
     g->kind = 1;   // the kernel without hinge / dynamics paths when the graph has neither
     for (const Bucket &bk : g->buckets)
         if (bk.type == FGA_SVM_HINGE || bk.type == FGA_MPC_DYN) g->kind = 0;

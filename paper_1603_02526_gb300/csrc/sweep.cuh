@@ -59,6 +59,21 @@ static __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p,
     return old;
 }
 
+// ---- cp.async (global -> shared, one element, zero when !valid) -------------
+template <typename R>
+static __device__ __forceinline__ void cp_async_zfill(R *dst, const R *src, bool valid) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    if (sizeof(R) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+static __device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---- mbarrier + bulk asynchronous copy (global -> shared) --------------------
 static __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -851,26 +866,51 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     if (a.zorder == 0) {
-        // canonical: one warp per variable; the lanes load 32 consecutive
-        // values of the variable's row at a time (the next 32 requested
-        // before these are added) and every lane adds them one by one in
-        // creation order from shuffles, so each lane holds exactly the
-        // serial sum; lane 0 stores z.  The chain of additions, not a memory
-        // round trip per value, sets the time.
-        const int lane = threadIdx.x & 31;
-        const long long wid = gtid >> 5, nw = gstride >> 5;
-        for (long long b = wid; b < a.nz; b += nw) {
-            const int k0 = a.row[b], k1 = a.row[b + 1];
-            R S = R(0);
-            R cur = k0 + lane < k1 ? ldg_l2(a.pvm + k0 + lane) : R(0);
-            for (int k = k0; k < k1; k += 32) {
-                const R nxt = k + 32 + lane < k1 ? ldg_l2(a.pvm + k + 32 + lane) : R(0);
-                const int cnt = k1 - k < 32 ? k1 - k : 32;
-                #pragma unroll 8
-                for (int t = 0; t < cnt; ++t) S += __shfl_sync(0xffffffffu, cur, t);
-                cur = nxt;
+        // canonical: warp 0 of a CTA takes 32 consecutive variables, one per
+        // lane; the warp copies 32 values of each of the 32 rows at a time
+        // into shared memory (cp.async, zero past a row's end; two buffers,
+        // the next block in flight while this one is added) and each lane
+        // adds its own row's values one by one in creation order.  One lane
+        // per variable keeps every FP64 addition of a warp useful.
+        if ((threadIdx.x >> 5) == 0) {
+            extern __shared__ __align__(16) unsigned char zs_raw[];
+            R *zbuf = reinterpret_cast<R *>(zs_raw);   // [2][32 rows][kZRow]
+            const int lane = threadIdx.x & 31;
+            for (long long base = (long long)blockIdx.x * 32; base < a.nz; base += (long long)gridDim.x * 32) {
+                const long long b = base + lane;
+                const bool valid = b < a.nz;
+                const int k0 = valid ? a.row[b] : 0, len = valid ? a.row[b + 1] - k0 : 0;
+                int maxlen = len;
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+                const int nch = (maxlen + 31) / 32;
+                R S = R(0);
+                auto issue = [&](int c) {
+                    R *buf = zbuf + (c & 1) * 32 * kZRow;
+                    #pragma unroll 4
+                    for (int j = 0; j < 32; ++j) {
+                        const int kj0 = __shfl_sync(0xffffffffu, k0, j), lj = __shfl_sync(0xffffffffu, len, j);
+                        const int t = c * 32 + lane;
+                        cp_async_zfill<R>(buf + j * kZRow + lane, a.pvm + (t < lj ? kj0 + t : 0), t < lj);
+                    }
+                    cp_async_commit();
+                };
+                if (nch > 0) issue(0);
+                for (int c = 0; c < nch; ++c) {
+                    if (c + 1 < nch) {
+                        issue(c + 1);
+                        cp_async_wait_group<1>();
+                    } else {
+                        cp_async_wait_group<0>();
+                    }
+                    __syncwarp();
+                    const R *row = zbuf + (c & 1) * 32 * kZRow + lane * kZRow;
+                    const int n = min(32, len - c * 32);
+                    for (int t = 0; t < n; ++t) S += row[t];
+                    __syncwarp();
+                }
+                if (valid) z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
             }
-            if (lane == 0) z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
         }
         return;
     }

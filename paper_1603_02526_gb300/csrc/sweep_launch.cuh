@@ -68,7 +68,7 @@ cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int g
 template <typename R>
 cudaError_t sweep_phase_z(const SweepArgs<R> &a, int zp, long long it, int chk, int grid, int block,
                           cudaStream_t s) {
-    k_phase_z<R><<<grid, block, 0, s>>>(a, zp, it, chk);
+    k_phase_z<R><<<grid, block, a.zorder == 0 ? canonical_z_smem((int)sizeof(R)) : 0, s>>>(a, zp, it, chk);
     return cudaGetLastError();
 }
 
