@@ -27,7 +27,7 @@
  * the order variables were introduced.  Vector variables are expanded into
  * scalar edges, one per component.
  *
- * Readings where the paper is silent or garbled (all listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - Sums in the z-update run over a variable's edges in ascending
  *     creation order, sequentially (a canonical order so that a GPU path can
  *     reproduce the sums bit for bit).  Build with -ffp-contract=off.
