@@ -281,7 +281,11 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": BYTES_PER_EDGE_ITER * E * ITERS,
-            "kernel": "k_tile_sweep" if launch["zorder"] == 2 else "k_sweep_persistent<float>"}
+            "kernel": "k_tile_sweep" if launch["zorder"] == 2 else "k_sweep_persistent<float>",
+            "note": "achieved = algorithmic bytes (20 B per scalar edge per iteration: read u, read x, write u, "
+                    "write x, read m) / device time; the disk-tile kernel keeps each pair's state in registers, "
+                    "so its DRAM traffic per launch (traffic, ncu) is a small fraction of them and frac can "
+                    "exceed 1; the kernel is bound by latency and its grid barrier"}
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
