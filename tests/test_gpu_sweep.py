@@ -230,3 +230,30 @@ def test_device_pointer_io():
     zd = torch.empty(g.num_scalar_vars, dtype=torch.float64, device="cuda")
     g.fga_read_z(zd)
     assert np.array_equal(zd.cpu().numpy(), g.fga_read_z())
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_canonical_z_rows_of_every_length(fused):
+    """FP64 canonical z order over variables whose degrees straddle the
+    32-value blocks in which the z sums are staged (0, 1, 31, 32, 33, 63, 64,
+    65, 97, 200) and more than 32 variables (groups of 32 with an uneven
+    tail); quadratic costs, boxes and fixed values interleaved in creation
+    order.  Every message against the oracle to 1e-10 after 40 iterations."""
+    degrees = [0, 1, 31, 32, 33, 63, 64, 65, 97, 200] * 4 + [2, 3]
+    rng = np.random.default_rng(11)
+    p = inputs.Problem("degrees")
+    v0 = p.add_vars(len(degrees), 1)
+    for rep in range(max(degrees)):
+        live = [i for i, d in enumerate(degrees) if rep < d]
+        kind = rep % 3
+        ids = [[v0 + i] for i in live]
+        if kind == 0:
+            p.add_factors(7, ids, [[0.5 + rng.random()] for _ in live])          # quadratic cost
+        elif kind == 1:
+            p.add_factors(8, ids, [[-0.5, 0.5 + rng.random()] for _ in live])    # box
+        else:
+            p.add_factors(9, ids, [[rng.standard_normal()] for _ in live])       # fixed value
+    p.z0 = rng.standard_normal(p.num_scalar_vars)
+    g, o, rg, ro = _both(p, 40, fused=fused)
+    assert_messages_match(g, o, 1e-10)
+    assert np.array_equal(g.fga_read_z(), o.z())
