@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include "hinge_internal.h"
+#include "residual.cuh"
 #include "persist.cuh"
 
 namespace fga {
@@ -238,6 +239,13 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
     float *l2d = reinterpret_cast<float *>(hsm + L.l2d);
     float *l2s = reinterpret_cast<float *>(hsm + L.l2s);
     __shared__ double s_res[2];
+    __shared__ int s_dec[2];
+    __shared__ ResidualTest s_rt[2];   // primal, dual; read by thread 0 at checks
+    if (threadIdx.x == 0) {
+        const double E = a.E > 0 ? (double)a.E : 1.0;
+        s_rt[0].init(E, a.tol_pri);
+        s_rt[1].init(E, a.tol_dual);
+    }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gi = warp * 4 + (lane >> 3), m = lane & 7;
@@ -361,34 +369,35 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
             }
         }
         if (chk) {
-            const double sp = block_sum(pri);
-            const double sd = block_sum(dual);
-            if (threadIdx.x == 0) {
-                double *r = a.res + (size_t)(it & 1) * 2 * a.G;
-                r[blockIdx.x] = sp;
-                r[a.G + blockIdx.x] = sd;
-            }
+            // the CTA's two sums as float pairs, one float4 per CTA and pass parity
+            const float4 bs = block_sum2_ff(pri, dual);
+            if (threadIdx.x == 0) reinterpret_cast<float4 *>(a.res)[(size_t)(it & 1) * a.G + blockIdx.x] = bs;
         }
         if (!tile_barrier(a.sync, G * (unsigned long long)it, a.timeout_ns, skip)) return;
         skip = false;
         if (chk) {
             if (threadIdx.x < 32) {
-                const double *r = a.res + (size_t)(it & 1) * 2 * a.G;
-                const double sp = warp_sum_partials(r, a.G);
-                const double sd = warp_sum_partials(r + a.G, a.G);
+                const float4 *r4 = reinterpret_cast<const float4 *>(a.res) + (size_t)(it & 1) * a.G;
+                const float2 tp = warp_sum_partial_ff(r4, a.G, 0);
+                const float2 td = warp_sum_partial_ff(r4, a.G, 1);
                 if (threadIdx.x == 0) {
-                    const double E = a.E > 0 ? (double)a.E : 1.0;
-                    s_res[0] = sqrt(sp / E);
-                    s_res[1] = sqrt(sd / E);
+                    const bool finite = isfinite(tp.x) && isfinite(td.x) && *(volatile int *)&a.sync->overflow == 0;
+                    const bool conv = finite && s_rt[0].pass(tp.x, tp.y) && s_rt[1].pass(td.x, td.y);
+                    s_dec[0] = finite;
+                    s_dec[1] = conv;
+                    if (!finite || conv || fin) {   // the reported values, in FP64
+                        s_res[0] = sqrt(((double)tp.x + (double)tp.y) / s_rt[0].E);
+                        s_res[1] = sqrt(((double)td.x + (double)td.y) / s_rt[1].E);
+                    }
                 }
             }
             __syncthreads();
             CheckOut c;
             c.rp = s_res[0];
             c.rd = s_res[1];
-            const bool finite = isfinite(c.rp) && isfinite(c.rd) && *(volatile int *)&a.sync->overflow == 0;
+            const bool finite = s_dec[0] != 0;
             c.status = finite ? 0 : kENonFinite;
-            c.stop = !finite || (c.rp <= a.tol_pri && c.rd <= a.tol_dual);
+            c.stop = !finite || s_dec[1] != 0;
             if (c.stop || fin) {
                 hinge_state(a, C, it, pm.reload, Xs, zt, zpt, ypt);
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
