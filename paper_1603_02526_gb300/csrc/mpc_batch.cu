@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "mpc_internal.h"
+#include "residual.cuh"
 
 namespace fga {
 
@@ -100,57 +101,10 @@ __device__ __forceinline__ int var_edges_sel(const Shape &g, int b, int *ed) {
     return last ? 2 : 3;
 }
 
-// (h, l) += (h2, l2) for unevaluated float pairs h + l (TwoSum, then a fast
-// renormalisation): the pair keeps about 44 significant bits, and the sum
-// is commutative, so a butterfly leaves the same value in every lane.
-__device__ __forceinline__ void ff_add(float &h, float &l, float h2, float l2) {
-    const float s = h + h2;
-    const float bb = s - h;
-    float e = (h - (s - bb)) + (h2 - bb);
-    e += l + l2;
-    h = s + e;
-    l = e - (h - s);
-}
-
 struct CheckOut {
     bool stop;
     int status;
     double rp, rd;
-};
-
-// sqrt(t / E) <= tol (the RMS residual test), decided without the FP64
-// divide and square root (long dependent sequences on this part's narrow
-// FP64 pipe) unless t lies close to tol^2 E, where the exact form decides:
-// within a relative 2^-40 for an FP64 t, within 2^-20 for a float pair
-// h + l (carried to about 2^-44), whose fast test compares h alone.
-struct ResidualTest {
-    double E, tol, lo, hi;
-    float lo32, hi32;
-    __device__ void init(double E_, double tol_) {
-        E = E_;
-        tol = tol_;
-        if (!(tol_ > 0.0)) {
-            lo = hi = 0.0;                        // only t = 0 can pass
-            lo32 = hi32 = 0.f;
-        } else {
-            const double t2 = tol_ * tol_ * E_;
-            const bool normal = t2 > 1e-30 && t2 < 1e30;
-            lo = normal ? t2 * (1.0 - 0x1p-40) : -INFINITY;   // else always the exact form
-            hi = normal ? t2 * (1.0 + 0x1p-40) : INFINITY;
-            lo32 = normal ? (float)(t2 * (1.0 - 0x1p-20)) : -INFINITY;
-            hi32 = normal ? (float)(t2 * (1.0 + 0x1p-20)) : INFINITY;
-        }
-    }
-    __device__ bool pass(double t) const {
-        if (t < lo) return true;
-        if (t > hi) return false;
-        return sqrt(t / E) <= tol;
-    }
-    __device__ bool pass(float h, float l) const {
-        if (h < lo32) return true;
-        if (h > hi32) return false;
-        return sqrt(((double)h + (double)l) / E) <= tol;
-    }
 };
 
 // Four consecutive values from a 16-byte aligned shared-memory address.
@@ -174,7 +128,7 @@ __device__ __forceinline__ void ld4(const double *p, double *v) {
 // warps in order by thread 0, which alone decides); every thread returns
 // the same decision.  FP64 state sums in FP64.  FP32 state sums in float
 // pairs (TwoSum), which carry the sum to about 2^-44 relative: an FP64-class
-// sum without the FP64 pipe, whose dependent adds cost about 150 cycles
+// sum without the FP64 pipe, whose dependent adds cost about 64 cycles
 // each here; the reported norms are formed in FP64 from the pair.  red
 // holds at least 34 doubles (up to 16 warps) and flag 2 ints.
 template <int NT>
