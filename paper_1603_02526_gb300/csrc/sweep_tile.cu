@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include "persist.cuh"
+#include "residual.cuh"
 #include "sweep.cuh"
 #include "tile_internal.h"
 
@@ -554,6 +555,13 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     float *yt = reinterpret_cast<float *>(y4);
     float *ypt = reinterpret_cast<float *>(yp4);
     __shared__ double s_res[2];
+    __shared__ int s_dec[2];
+    __shared__ ResidualTest s_rt[2];   // primal, dual; read by thread 0 at checks
+    if (threadIdx.x == 0) {
+        const double E = a.E > 0 ? (double)a.E : 1.0;
+        s_rt[0].init(E, a.tol_pri);
+        s_rt[1].init(E, a.tol_dual);
+    }
 
     const TileCta C = a.cta[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -678,8 +686,10 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
             if (ovf) atomicOr(&a.sync->overflow, 1);
         }
         if (chk) {
-            const double sp = block_sum(pri);
-            const double sd = block_sum(dual);
+            // the CTA's sums through float pairs (csrc/residual.cuh), stored as doubles
+            const float4 bs = block_sum2_ff(pri, dual);
+            const double sp = (double)bs.x + (double)bs.y;
+            const double sd = (double)bs.z + (double)bs.w;
             if (threadIdx.x == 0) {
                 double *r = a.res + (size_t)(it & 1) * 2 * a.G;
                 r[blockIdx.x] = sp;
@@ -694,18 +704,23 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
                 const double sp = warp_sum_partials(r, a.G);
                 const double sd = warp_sum_partials(r + a.G, a.G);
                 if (threadIdx.x == 0) {
-                    const double E = a.E > 0 ? (double)a.E : 1.0;
-                    s_res[0] = sqrt(sp / E);
-                    s_res[1] = sqrt(sd / E);
+                    const bool finite = isfinite(sp) && isfinite(sd) && *(volatile int *)&a.sync->overflow == 0;
+                    const bool conv = finite && s_rt[0].pass(sp) && s_rt[1].pass(sd);
+                    s_dec[0] = finite;
+                    s_dec[1] = conv;
+                    if (!finite || conv || fin) {   // the reported values
+                        s_res[0] = sqrt(sp / s_rt[0].E);
+                        s_res[1] = sqrt(sd / s_rt[1].E);
+                    }
                 }
             }
             __syncthreads();
             CheckOut c;
             c.rp = s_res[0];
             c.rd = s_res[1];
-            const bool finite = isfinite(c.rp) && isfinite(c.rd) && *(volatile int *)&a.sync->overflow == 0;
+            const bool finite = s_dec[0] != 0;
             c.status = finite ? 0 : kENonFinite;
-            c.stop = !finite || (c.rp <= a.tol_pri && c.rd <= a.tol_dual);
+            c.stop = !finite || s_dec[1] != 0;
             if (c.stop || fin) {
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
                     Ctl *ctl = a.ctl;
