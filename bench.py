@@ -318,7 +318,8 @@ def run_extras(log=None):
     packing solve in FP64, the SVM (100k x 64), the batched ragged MPC
     (4096 instances, autotuned,
     CUDA graph) and the learned warm start (train on 200k solver solutions,
-    evaluate on 16,384 fresh instances, cold vs warm)."""
+    evaluate on 16,384 fresh instances, cold vs warm), and one long-horizon
+    MPC (horizons 200 to 10^5) as a single graph."""
     import torch
     from paper_1603_02526_gb300 import inputs, _lib, warmstart
     from paper_1603_02526_gb300.graph import graph_from_problem
@@ -388,6 +389,35 @@ def run_extras(log=None):
                         "frac_of_fp32_fma_peak": fmas / (min(times) * 1e-3) / fma_peak,
                         "fma_peak_basis": "%d SMs x 128 lanes x 2070 MHz" % sms}
     del b
+    # one long-horizon MPC (the inverted pendulum, A 4 x 4, B 4 x 1) as a
+    # single graph: the time of 100 iterations against the horizon K, and
+    # the K = 10^5 solve to RMS residual 1e-5 (1e-4 is met after about 10
+    # iterations: the RMS runs over 1.4M edges, most of them near zero)
+    hz = {"workload": "inverted-pendulum MPC, one instance as one factor graph (FIX, DYN, stage and terminal "
+                      "QUAD; 14 scalar edges per step), rho 1, z0 = 0; FP32 fast z order and FP64 canonical "
+                      "order; per K: device time of 100 fused iterations",
+          "kernel": "k_sweep_persistent<float> / <double>", "per_K": {}}
+    for K in (200, 1000, 10000, 50000, 100000):
+        p = inputs.mpc_horizon_problem(K)
+        row = {"scalar_edges": p.num_edges}
+        for prec in ("f32", "f64"):
+            g = graph_from_problem(p, prec)
+            g.fga_iterate(20, check_every=20)
+            g.fga_init(p.z0)
+            r = g.fga_iterate(100, check_every=100)
+            bpe = 20 if prec == "f32" else 40
+            row[prec] = {"ms_100_iters": r["ms"], "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3),
+                         "frac_of_hbm": bpe * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak}
+            if K == 100000 and prec == "f32":
+                g.fga_init(p.z0)
+                r = g.fga_iterate(50000, 1e-5, 1e-5, check_every=10)
+                hz["solve_K100000_f32"] = {"tol": 1e-5, "check_every": 10, "iters": r["iters"],
+                                           "status": r["status"], "ms": r["ms"], "r_pri": r["r_pri"],
+                                           "r_dual": r["r_dual"]}
+            del g
+        hz["per_K"][str(K)] = row
+    hz["peak_kind"] = peak_kind
+    out["mpc_horizon"] = hz
     # learned warm start
     t0 = time.perf_counter()
     X, Y, gen = warmstart.generate(200000, x0_seed=5001)

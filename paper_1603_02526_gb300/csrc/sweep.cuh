@@ -711,6 +711,7 @@ __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const B
     case 6:
         if constexpr (KIND == 0) {
             if (B.arity == 28) item_mpc_dyn<R, MODE, FAST, 28>(a, B, io, li, pri);
+            else if (B.arity == 9) item_mpc_dyn<R, MODE, FAST, 9>(a, B, io, li, pri);   // 4 states, 1 input
             else item_mpc_dyn<R, MODE, FAST, 0>(a, B, io, li, pri);
         }
         break;

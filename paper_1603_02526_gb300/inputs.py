@@ -13,7 +13,9 @@ Workloads (paper Sec. V):
   * linear soft-margin SVM (Sec. V-C): one hinge factor per point on a
     shared (w, b) plus an L2 factor on w.
   * linear MPC (Sec. V-B, Appendix B): states x_0..x_T, inputs u_0..u_{T-1};
-    a fixed-x_0 factor, dynamics, diagonal quadratic costs and input boxes.
+    a fixed-x_0 factor, dynamics, diagonal quadratic costs and input boxes;
+    batches of small instances, or one inverted-pendulum instance with a
+    horizon of up to 10^5 steps.
 """
 from dataclasses import dataclass, field
 from typing import List, Optional, Tuple
@@ -263,6 +265,75 @@ def mpc_problem(A, B, q, r, x0, T, umax=1.0, rho=1.0, alpha=1.0):
     p.z0 = np.zeros(p.num_scalar_vars)
     p.meta = dict(nx=nx, nu=nu, T=T, xs=xs, us=us)
     return p
+
+
+def pendulum_system(dt=0.04, M=1.0, m=0.1, l=0.5, g=9.81):
+    """The cart-and-pole inverted pendulum of Sec. V-B, linearised about the
+    upright equilibrium and sampled every dt seconds with a zero-order hold.
+    State (cart position, cart velocity, pole angle, angular velocity), input
+    the force on the cart; cart mass M, a point mass m at distance l on a
+    massless pole, no friction:
+        p'' = (F - m g th) / M,    th'' = ((M + m) g th - F) / (M l).
+    Returns (A_d, B_d) with x_{t+1} = A_d x_t + B_d u_t, i.e. the paper's
+    q(t+1) - q(t) = A q(t) + B u(t) with A = A_d - I, B = B_d."""
+    from scipy.linalg import expm
+    Ac = np.zeros((4, 4))
+    Ac[0, 1] = 1.0
+    Ac[1, 2] = -m * g / M
+    Ac[2, 3] = 1.0
+    Ac[3, 2] = (M + m) * g / (M * l)
+    Bc = np.array([[0.0], [1.0 / M], [0.0], [-1.0 / (M * l)]])
+    aug = np.zeros((5, 5))
+    aug[:4, :4] = Ac
+    aug[:4, 4:] = Bc
+    E = expm(aug * dt)
+    return E[:4, :4].copy(), E[:4, 4:].copy()
+
+
+def mpc_horizon_problem(K, seed=6000, q=(1.0, 0.1, 10.0, 0.1), r=(0.1,), umax=None, rho=1.0, alpha=1.0,
+                        system=None):
+    """One long-horizon MPC of the inverted pendulum (Sec. V-B: A 4 x 4,
+    B 4 x 1, sampled at 40 ms, equal diagonal Q_t and R_t, horizon K from 200
+    to 10^5) as a single factor graph.  Variables in creation order: the
+    states x_0..x_K (one block of dimension 4), then the inputs
+    u_0..u_{K-1} (one block of dimension 1).  Factors: FIX(x_0), DYN(x_t,
+    u_t, x_{t+1}) t = 0..K-1, stage QUAD(x_t, u_t) with diag(q, r), terminal
+    QUAD(x_K) with diag(q) (Q_f = Q), and BOX(u_t) only when umax is given.
+    x_0 ~ N(0, diag(0.1, 0.1, 0.05, 0.1)^2) from the seed; z0 = 0."""
+    A, B = pendulum_system() if system is None else system
+    nx, nu = B.shape
+    q = np.asarray(q, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    x0 = rng.standard_normal(nx) * np.array([0.1, 0.1, 0.05, 0.1])[:nx]
+    p = Problem("mpc_horizon_K%d" % K, rho=rho, alpha=alpha)
+    x_first = p.add_vars(K + 1, nx)
+    u_first = p.add_vars(K, nu)
+    xs = x_first + np.arange(K + 1, dtype=np.int64)
+    us = u_first + np.arange(K, dtype=np.int64)
+    p.add_factors(FIX, xs[:1, None], x0[None, :])
+    p.add_factors(MPC_DYN, np.stack([xs[:-1], us, xs[1:]], axis=1),
+                  np.concatenate([A.reshape(-1), B.reshape(-1)]))
+    p.add_factors(MPC_QUAD, np.stack([xs[:-1], us], axis=1), np.concatenate([q, r]))
+    p.add_factors(MPC_QUAD, xs[-1:, None], q)
+    if umax is not None:
+        p.add_factors(MPC_BOX, us[:, None], np.array([-umax, umax]))
+    p.z0 = np.zeros(p.num_scalar_vars)
+    p.meta = dict(nx=nx, nu=nu, K=K, A=A, B=B, q=q, r=r, x0=x0, umax=umax)
+    return p
+
+
+def mpc_horizon_split(z, K, nx=4, nu=1):
+    """(states (K+1, nx), inputs (K, nu)) of a mpc_horizon_problem solution
+    in variable order."""
+    z = np.asarray(z)
+    return z[:(K + 1) * nx].reshape(K + 1, nx), z[(K + 1) * nx:].reshape(K, nu)
+
+
+def mpc_horizon_edges(K, nx=4, nu=1, box=False):
+    """Scalar edges of mpc_horizon_problem: FIX + K DYN + K stage + terminal
+    (+ K BOX)."""
+    return nx + (2 * nx + nu) * K + (nx + nu) * K + nx + (nu * K if box else 0)
 
 
 def mpc_edges(T, nx=12, nu=4):

@@ -294,6 +294,48 @@ def test_mpc_active_box_matches_qp():
     assert cost(us.ravel()) <= sol.fun + 1e-9
 
 
+def test_pendulum_sampling_closed_form():
+    """The sampled inverted pendulum of the long-horizon MPC (Sec. V-B: A
+    4 x 4, B 4 x 1, 40 ms) against the zero-order-hold solution written out
+    by hand: the angle obeys th'' = w^2 th - F/(M l), w^2 = (M + m) g / (M l)
+    (hyperbolic sines and cosines), and the cart integrates F/M - (m g/M) th
+    twice."""
+    h, M, m, l, g = 0.04, 1.0, 0.1, 0.5, 9.81
+    A, B = inputs.pendulum_system(h, M, m, l, g)
+    w = np.sqrt((M + m) * g / (M * l))
+    ch, sh = np.cosh(w * h), np.sinh(w * h)
+    c = m * g / M
+    A_ref = np.array([
+        [1.0, h, -c * (ch - 1) / w**2, -c * (sh / w - h) / w**2],
+        [0.0, 1.0, -c * sh / w, -c * (ch - 1) / w**2],
+        [0.0, 0.0, ch, sh / w],
+        [0.0, 0.0, w * sh, ch]])
+    k = 1.0 / (M * l)
+    B_ref = np.array([h * h / (2 * M) + c * k * ((ch - 1) / w**2 - h * h / 2) / w**2,
+                      h / M + c * k * (sh / w - h) / w**2,
+                      -k * (ch - 1) / w**2,
+                      -k * sh / w])
+    np.testing.assert_allclose(A, A_ref, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(B.ravel(), B_ref, rtol=1e-12, atol=1e-15)
+    assert np.max(np.abs(np.linalg.eigvals(A))) > 1.2     # open-loop unstable
+
+
+def test_mpc_horizon_pendulum_is_lqr():
+    """The long-horizon pendulum graph (two variable blocks, no box),
+    converged by the oracle, is the finite-horizon LQR trajectory."""
+    K = 60
+    p = inputs.mpc_horizon_problem(K)
+    assert p.num_edges == inputs.mpc_horizon_edges(K)
+    g = from_problem(p)
+    res = g.iterate(200000, 1e-10, 1e-10)
+    assert res["status"] == 0
+    xs, us = inputs.mpc_horizon_split(g.z(), K)
+    m = p.meta
+    xl, ul = _lqr(m["A"], m["B"], m["q"], m["r"], m["x0"], K)
+    np.testing.assert_allclose(xs, xl, atol=1e-6)
+    np.testing.assert_allclose(us, ul, atol=1e-6)
+
+
 # ---------------------------------------------------------------------------
 # SVM
 # ---------------------------------------------------------------------------
