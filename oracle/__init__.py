@@ -6,5 +6,5 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 from .oracle import (  # noqa: F401
     OracleGraph, build_oracle, from_problem, oracle_prox, T_PACK_PAIR, T_PACK_WALL,
     T_PACK_RADIUS_LIN, T_PACK_RADIUS_QUAD, T_SVM_HINGE, T_SVM_L2, T_MPC_DYN,
-    T_MPC_QUAD, T_MPC_BOX, T_FIX,
+    T_MPC_QUAD, T_MPC_BOX, T_FIX, T_SVM_MARGIN, T_SVM_SLACK, T_EQUAL,
 )

@@ -57,7 +57,10 @@ enum {
     OT_MPC_QUAD = 7,         /* f = 1/2 sum q_k v_k^2, Appendix B             */
     OT_MPC_BOX = 8,          /* indicator of lo <= v <= hi                    */
     OT_FIX = 9,              /* indicator of v = value                        */
-    OT_NTYPES = 10
+    OT_SVM_MARGIN = 10,      /* indicator of y (w.x + b) >= 1 - xi, App. C    */
+    OT_SVM_SLACK = 11,       /* f = lambda sum xi on xi >= 0, Appendix C      */
+    OT_EQUAL = 12,           /* indicator of v1 = v2, Appendix C              */
+    OT_NTYPES = 13
 };
 
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ESTATE = -4, OR_ENONFINITE = -6 };
@@ -178,6 +181,15 @@ static int expected_params(int32_t type, int32_t nv, const int32_t *dims, int32_
         return 2;
     case OT_FIX:
         return arity;
+    case OT_SVM_MARGIN:
+        if (nv != 3 || dims[1] != 1 || dims[2] != 1) return -1;
+        return dims[0] + 1;
+    case OT_SVM_SLACK:
+        if (nv != 1) return -1;
+        return 1;
+    case OT_EQUAL:
+        if (nv != 2 || dims[0] != dims[1]) return -1;
+        return 0;
     default:
         return -1;
     }
@@ -415,6 +427,55 @@ static void prox_svm_l2(int32_t arity, const double *n, const double *rho, const
     for (int32_t j = 0; j < arity; ++j) x[j] = (rho[j] * n[j]) / (rho[j] + p[0]);
 }
 
+/* Appendix C, one-point minimal margin: the indicator of
+ * y (w.x + b) >= 1 - xi on v = (w in R^d, b, xi); params x[d], y.  Its prox
+ * is the rho-weighted projection onto the half-space a.v >= 1 with
+ * a = (y x, y, 1):
+ *     v = n + lambda W a,   lambda = (1 - a.n)^+ / (a^T W a),   W = diag(1/rho).
+ * (The printed closed form inverts the sign of the violation, writes
+ * n1.w + n2 b for n1.x + n2, drops y from the b update and moves w, b, xi
+ * against a; this is the projection the stated problem defines.) */
+static void prox_svm_margin(int32_t d, const double *n, const double *rho, const double *p, double *x)
+{
+    const double y = p[d];
+    double an = 0.0, awa = 0.0;
+    for (int32_t j = 0; j < d; ++j) {
+        const double aj = y * p[j];
+        an += aj * n[j];
+        awa += (aj * aj) / rho[j];
+    }
+    an += y * n[d];
+    awa += (y * y) / rho[d];
+    an += n[d + 1];
+    awa += 1.0 / rho[d + 1];
+    const double viol = 1.0 - an;
+    const double lam = viol > 0.0 ? viol / awa : 0.0;
+    for (int32_t j = 0; j < d; ++j) x[j] = n[j] + (lam * (y * p[j])) / rho[j];
+    x[d] = n[d] + (lam * y) / rho[d];
+    x[d + 1] = n[d + 1] + lam / rho[d + 1];
+}
+
+/* Appendix C, minimal error: argmin lambda xi + rho/2 (xi - n)^2 over
+ * xi >= 0, per component: xi = (n - lambda/rho)^+. */
+static void prox_svm_slack(int32_t arity, const double *n, const double *rho, const double *p, double *x)
+{
+    for (int32_t j = 0; j < arity; ++j) {
+        const double v = n[j] - p[0] / rho[j];
+        x[j] = v > 0.0 ? v : 0.0;
+    }
+}
+
+/* Appendix C, equality of two copies v1, v2 in R^d: both become the
+ * rho-weighted mean, per component. */
+static void prox_equal(int32_t d, const double *n, const double *rho, double *x)
+{
+    for (int32_t j = 0; j < d; ++j) {
+        const double v = (rho[j] * n[j] + rho[d + j] * n[d + j]) / (rho[j] + rho[d + j]);
+        x[j] = v;
+        x[d + j] = v;
+    }
+}
+
 /* Dense Cholesky solve of an SPD k x k system (in place), used by the
  * dynamics projection below. */
 static int chol_solve(int k, double *K, double *b)
@@ -529,6 +590,9 @@ int og_prox(int32_t type, int32_t nv, const int32_t *dims, const double *params,
     case OT_MPC_QUAD: prox_mpc_quad(arity, n, rho, params, x); return OR_OK;
     case OT_MPC_BOX: prox_mpc_box(arity, n, params, x); return OR_OK;
     case OT_FIX: prox_fix(arity, params, x); return OR_OK;
+    case OT_SVM_MARGIN: prox_svm_margin(dims[0], n, rho, params, x); return OR_OK;
+    case OT_SVM_SLACK: prox_svm_slack(arity, n, rho, params, x); return OR_OK;
+    case OT_EQUAL: prox_equal(dims[0], n, rho, x); return OR_OK;
     default: return OR_EINVAL;
     }
 }

@@ -33,6 +33,9 @@ T_MPC_DYN = 6
 T_MPC_QUAD = 7
 T_MPC_BOX = 8
 T_FIX = 9
+T_SVM_MARGIN = 10
+T_SVM_SLACK = 11
+T_EQUAL = 12
 
 EDGE_X, EDGE_M, EDGE_U, EDGE_N = 0, 1, 2, 3
 

@@ -11,7 +11,8 @@ Workloads (paper Sec. V):
     radius-reward factor per disk; 2N variable nodes (c_i in R^2, r_i);
     2N^2 - N + 2NS edges; N(N-1)/2 + N + NS factors.
   * linear soft-margin SVM (Sec. V-C): one hinge factor per point on a
-    shared (w, b) plus an L2 factor on w.
+    shared (w, b) plus an L2 factor on w; or the paper's own form, a copy
+    of w per point with margin, slack, split-norm and equality factors.
   * linear MPC (Sec. V-B, Appendix B): states x_0..x_T, inputs u_0..u_{T-1};
     a fixed-x_0 factor, dynamics, diagonal quadratic costs and input boxes;
     batches of small instances, or one inverted-pendulum instance with a
@@ -33,6 +34,9 @@ MPC_DYN = 6
 MPC_QUAD = 7
 MPC_BOX = 8
 FIX = 9
+SVM_MARGIN = 10
+SVM_SLACK = 11
+EQUAL = 12
 
 
 @dataclass
@@ -194,6 +198,41 @@ def svm_problem(npts, d, seed=3000, lam=1e-3, c=1.0, rho=1.0, alpha=1.0, X=None,
     p.z0 = np.zeros(d + 1)
     p.meta = dict(X=X, y=y, lam=lam, c=c)
     return p
+
+
+def svm_paper_problem(npts, d, seed=3000, C=1000.0, rho=1.0, alpha=1.0, X=None, y=None):
+    """The soft-margin SVM in the paper's own factor-graph form (Sec. V-C,
+    Appendix C): min 1/2 |w|^2 + C sum xi_i subject to y_i (w.x_i + b) >=
+    1 - xi_i, xi_i >= 0, with one copy w_i of w per point and the norm term
+    split into N equal parts.  Variables in creation order: the copies
+    w_1..w_N (one block of dimension d), b, the slacks xi_1..xi_N.  Factors:
+    one margin factor per point on (w_i, b, xi_i); one minimal-error factor
+    per slack (weight C); one norm factor (1/(2N)) |w_i|^2 per copy; the
+    equality factors w_i = w_{i+1}, i = 1..N-1, a chain.  The same minimiser
+    (w, b) as svm_problem with c = C, lam = 1, or c = 1, lam = 1/C."""
+    if X is None:
+        X, y = svm_data(npts, d, seed)
+    p = Problem("svm_paper_%dx%d" % (npts, d), rho=rho, alpha=alpha)
+    w0 = p.add_vars(npts, d)
+    b = p.add_vars(1, 1)
+    xi0 = p.add_vars(npts, 1)
+    ws = w0 + np.arange(npts, dtype=np.int64)
+    xis = xi0 + np.arange(npts, dtype=np.int64)
+    p.add_factors(SVM_MARGIN, np.stack([ws, np.full(npts, b, dtype=np.int64), xis], axis=1),
+                  np.concatenate([X, y[:, None]], axis=1))
+    p.add_factors(SVM_SLACK, xis[:, None], np.array([C]))
+    p.add_factors(SVM_L2, ws[:, None], np.array([1.0 / npts]))
+    if npts > 1:
+        p.add_factors(EQUAL, np.stack([ws[:-1], ws[1:]], axis=1))
+    p.z0 = np.zeros(p.num_scalar_vars)
+    p.meta = dict(X=X, y=y, C=C, w0=w0, b=b, xi0=xi0)
+    return p
+
+
+def svm_paper_edges(npts, d):
+    """Scalar edges of svm_paper_problem: margins N(d + 2), slacks N, norms
+    N d, equalities 2 d (N - 1)."""
+    return npts * (d + 2) + npts + npts * d + 2 * d * max(npts - 1, 0)
 
 
 # ---------------------------------------------------------------------------

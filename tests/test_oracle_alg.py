@@ -351,6 +351,33 @@ def test_svm_two_points_closed_form():
     np.testing.assert_allclose(g.z(), [1 / a, 0.0, 0.0], atol=1e-8)
 
 
+def test_svm_paper_form_matches_qp():
+    """The paper's SVM form (a copy of w per point chained by equality
+    factors, margin, slack and split-norm factors), converged by the oracle:
+    the soft-margin QP's solution min 1/2 |w|^2 + C sum xi (SLSQP on the
+    epigraph form), every copy of w equal, and the slacks the hinge losses."""
+    X, y = inputs.svm_data(12, 2, seed=11)
+    C = 2.0
+    p = inputs.svm_paper_problem(12, 2, C=C, X=X, y=y)
+    assert p.num_edges == inputs.svm_paper_edges(12, 2)
+    g = from_problem(p)
+    res = g.iterate(2000000, 1e-11, 1e-11, check_every=10)
+    assert res["status"] == 0
+    z = g.z()
+    W = z[:24].reshape(12, 2)
+    bz = z[24]
+    xi = z[25:]
+    np.testing.assert_allclose(W, np.broadcast_to(W[0], W.shape), atol=1e-7)
+    cons = [dict(type="ineq", fun=lambda s: s[3:]),
+            dict(type="ineq", fun=lambda s: s[3:] - (1 - y * (X @ s[:2] + s[2])))]
+    s0 = np.concatenate([W[0], [bz], xi])
+    sol = minimize(lambda s: 0.5 * s[:2] @ s[:2] + C * s[3:].sum(), s0, constraints=cons,
+                   method="SLSQP", options=dict(ftol=1e-15, maxiter=2000))
+    np.testing.assert_allclose(W[0], sol.x[:2], atol=1e-5)
+    np.testing.assert_allclose(bz, sol.x[2], atol=1e-5)
+    np.testing.assert_allclose(xi, np.maximum(0.0, 1 - y * (X @ W[0] + bz)), atol=1e-6)
+
+
 def test_svm_small_matches_qp():
     X, y = inputs.svm_data(30, 3, seed=9)
     lam = 0.1

@@ -13,7 +13,7 @@ from scipy.optimize import minimize
 
 from oracle import (oracle_prox, T_PACK_PAIR, T_PACK_WALL, T_PACK_RADIUS_LIN,
                     T_PACK_RADIUS_QUAD, T_SVM_HINGE, T_SVM_L2, T_MPC_DYN, T_MPC_QUAD,
-                    T_MPC_BOX, T_FIX)
+                    T_MPC_BOX, T_FIX, T_SVM_MARGIN, T_SVM_SLACK, T_EQUAL)
 
 
 def _quad(s, n, rho):
@@ -155,6 +155,61 @@ def test_svm_hinge_inactive_is_identity():
     xi = np.array([1.0, 2.0]); n = np.array([1.0, 1.0, 0.0])
     x = oracle_prox(T_SVM_HINGE, [2, 1], np.concatenate([xi, [1.0, 1.0]]), np.ones(3), n)
     assert np.array_equal(x, n)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_svm_margin_matches_bruteforce(seed):
+    """Appendix C one-point margin: the projection of n onto
+    {y (w.x + b) >= 1 - xi} in the rho-weighted norm, against SLSQP on the
+    defining problem (per-edge rho, both labels, active and inactive)."""
+    rng = np.random.default_rng(300 + seed)
+    D = 3
+    xv = rng.standard_normal(D)
+    y = 1.0 if seed % 2 else -1.0
+    n = rng.standard_normal(D + 2) * (0.3 if seed < 7 else 2.0)
+    rho = rng.uniform(0.5, 2.0, D + 2)
+    x = oracle_prox(T_SVM_MARGIN, [D, 1, 1], np.concatenate([xv, [y]]), rho, n)
+    cons = [dict(type="ineq", fun=lambda v: y * (v[:D] @ xv + v[D]) - 1.0 + v[D + 1])]
+    best = _best_constrained(n, rho, cons, [n, n + 1.0, x])
+    np.testing.assert_allclose(x, best.x, atol=1e-6)
+    assert y * (x[:D] @ xv + x[D]) - 1.0 + x[D + 1] >= -1e-12
+
+
+def test_svm_margin_inactive_is_identity():
+    n = np.array([1.0, 1.0, 0.5, 0.0])      # y (w.x + b) = 1.5 + 0.5 >= 1
+    x = oracle_prox(T_SVM_MARGIN, [2, 1, 1], [1.0, 0.5, 1.0], np.ones(4), n)
+    assert np.array_equal(x, n)
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.3, 2.0])
+def test_svm_slack_matches_bruteforce(lam):
+    """Appendix C minimal error: argmin lam xi + rho/2 (xi - n)^2, xi >= 0,
+    against a bounded scalar minimiser per component."""
+    from scipy.optimize import minimize_scalar
+    rng = np.random.default_rng(17)
+    n = rng.standard_normal(6)
+    rho = rng.uniform(0.5, 2.0, 6)
+    x = oracle_prox(T_SVM_SLACK, [6], [lam], rho, n)
+    for j in range(6):
+        r = minimize_scalar(lambda t: lam * t + 0.5 * rho[j] * (t - n[j]) ** 2, bounds=(0.0, 10.0),
+                            method="bounded", options=dict(xatol=1e-12))
+        assert abs(x[j] - r.x) <= 1e-8
+    assert np.all(x >= 0.0)
+
+
+def test_equal_matches_constrained_minimiser():
+    """Appendix C equality: argmin sum rho/2 (v - n)^2 subject to v1 = v2, as
+    a projection onto the null space of [I  -I] in the rho-weighted norm
+    (SciPy null space, weighted least squares)."""
+    rng = np.random.default_rng(23)
+    d = 4
+    n = rng.standard_normal(2 * d)
+    rho = rng.uniform(0.5, 2.0, 2 * d)
+    x = oracle_prox(T_EQUAL, [d, d], None, rho, n)
+    N = null_space(np.hstack([np.eye(d), -np.eye(d)]))
+    Wh = np.diag(np.sqrt(rho))
+    c, *_ = np.linalg.lstsq(Wh @ N, Wh @ n, rcond=None)
+    np.testing.assert_allclose(x, N @ c, atol=1e-12)
 
 
 @pytest.mark.parametrize("lam", [1e-3, 1.0, 5.0])
