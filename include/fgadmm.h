@@ -80,7 +80,14 @@ extern "C" {
                                  lo <= v <= hi                                */
 #define FGA_FIX 9             /* (any vars) ; one value per scalar component ;
                                  indicator of v = value                       */
-#define FGA_NUM_TYPES 10
+#define FGA_SVM_MARGIN 10     /* (w:D, b:1, xi:1) ; D+1 = x[D], y ; indicator
+                                 of y (w.x + b) >= 1 - xi (Appendix C, one-
+                                 point minimal margin)                        */
+#define FGA_SVM_SLACK 11      /* (xi:any) ; 1 = lambda ; f = lambda sum xi_k
+                                 on xi >= 0 (Appendix C, minimal error)       */
+#define FGA_EQUAL 12          /* (v1:D, v2:D) ; 0 ; indicator of v1 = v2
+                                 (Appendix C, equality of two copies)         */
+#define FGA_NUM_TYPES 13
 
 /* ---- edge arrays for readout ------------------------------------------- */
 #define FGA_EDGE_X 0

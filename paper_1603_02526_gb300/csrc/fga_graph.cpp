@@ -196,6 +196,12 @@ static int expected_params(int type, const std::vector<int> &dims, int arity) {
         return 2;
     case FGA_FIX:
         return arity;
+    case FGA_SVM_MARGIN:
+        return (nv == 3 && dims[1] == 1 && dims[2] == 1) ? dims[0] + 1 : -1;
+    case FGA_SVM_SLACK:
+        return nv == 1 ? 1 : -1;
+    case FGA_EQUAL:
+        return (nv == 2 && dims[0] == dims[1]) ? 0 : -1;
     default:
         return -1;
     }
@@ -203,7 +209,7 @@ static int expected_params(int type, const std::vector<int> &dims, int arity) {
 
 static bool is_per_edge(int type) {
     return type == FGA_PACK_RADIUS_LIN || type == FGA_PACK_RADIUS_QUAD || type == FGA_SVM_L2 ||
-           type == FGA_MPC_QUAD || type == FGA_MPC_BOX || type == FGA_FIX;
+           type == FGA_MPC_QUAD || type == FGA_MPC_BOX || type == FGA_FIX || type == FGA_SVM_SLACK;
 }
 
 // ---------------------------------------------------------------------------
@@ -334,7 +340,7 @@ extern "C" int fga_add_factors(fga_graph *g, int32_t type, int64_t count, int32_
         for (int64_t f = 0; f < (b.shared ? 1 : count); ++f)
             if (!(b.param(f)[b.dims[0] + 1] >= 0.0)) return fail(FGA_EINVAL, "fga_add_factors: hinge weight c < 0");
     }
-    if (type == FGA_SVM_L2) {
+    if (type == FGA_SVM_L2 || type == FGA_SVM_SLACK) {
         for (int64_t f = 0; f < (b.shared ? 1 : count); ++f)
             if (!(b.param(f)[0] >= 0.0)) return fail(FGA_EINVAL, "fga_add_factors: lambda < 0");
     }
@@ -516,10 +522,10 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         for (int64_t f = 0; f < nf; ++f) {
             const FactorBatch &b = g->batches[bk.members[f].first];
             const double *p = b.param(bk.members[f].second);
-            // hinge parameters factor-major (a warp reads one factor's data
-            // point contiguously); every other type edge-major
-            for (int j = 0; j < bk.np; ++j)
-                prm[bk.type == FGA_SVM_HINGE ? (size_t)f * bk.np + j : (size_t)j * nf + f] = (R)p[j];
+            // hinge and margin parameters factor-major (a factor's data
+            // point read contiguously); every other type edge-major
+            const bool fmaj = bk.type == FGA_SVM_HINGE || bk.type == FGA_SVM_MARGIN;
+            for (int j = 0; j < bk.np; ++j) prm[fmaj ? (size_t)f * bk.np + j : (size_t)j * nf + f] = (R)p[j];
         }
         auto pb = std::make_unique<DevBuf>();
         if ((rc = upload_vec(*pb, prm))) return rc;
@@ -591,6 +597,11 @@ static int build_chunks(fga_graph *g, FastLayout &fl, int64_t items_per_chunk) {
             out.clear();
             if (bk.per_edge) {
                 out.push_back(bk.ebase + i);
+            } else if (bk.type == FGA_EQUAL) {
+                // item i = component j of factor f, i = j * nf + f
+                const int64_t j = i / nf, f = i % nf;
+                out.push_back(bk.ebase + j * nf + f);
+                out.push_back(bk.ebase + (j + bk.arity / 2) * nf + f);
             } else {
                 for (int k = 0; k < bk.arity; ++k)
                     out.push_back(bk.aos ? bk.ebase + i * bk.arity + k : bk.ebase + (int64_t)k * nf + i);
@@ -920,7 +931,7 @@ extern "C" int fga_finalize(fga_graph *g) {
             nb.arity = b.arity;
             nb.per_edge = is_per_edge(b.type);
             nb.aos = b.type == FGA_PACK_PAIR || b.type == FGA_PACK_WALL || b.type == FGA_MPC_DYN ||
-                     b.type == FGA_SVM_HINGE;
+                     b.type == FGA_SVM_HINGE || b.type == FGA_SVM_MARGIN;
             g->buckets.push_back(nb);
             found = (int)g->buckets.size() - 1;
         }
@@ -988,7 +999,9 @@ extern "C" int fga_finalize(fga_graph *g) {
         ebase = (ebase + 3) & ~int64_t(3);
         bk.ebase = ebase;
         bk.item0 = item;
-        bk.nitems = bk.per_edge ? nf * bk.arity : nf;
+        // per-edge types: one item per scalar edge; equality: one item per
+        // component pair; every other type: one item per factor
+        bk.nitems = bk.per_edge ? nf * bk.arity : bk.type == FGA_EQUAL ? nf * (bk.arity / 2) : nf;
         if (tp) g->tile_pair_ebase = ebase;
         for (int64_t f = 0; f < nf; ++f) {
             const FactorBatch &b = g->batches[bk.members[f].first];
@@ -1046,9 +1059,14 @@ extern "C" int fga_finalize(fga_graph *g) {
     CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
     g->blk = g->block ? g->block : 256;
     g->smem = g->zorder == 1 ? chunk_smem((int)g->rsize()).total : canonical_z_smem((int)g->rsize());
-    g->kind = 1;   // the kernel without hinge / dynamics paths when the graph has neither
-    for (const Bucket &bk : g->buckets)
-        if (bk.type == FGA_SVM_HINGE || bk.type == FGA_MPC_DYN) g->kind = 0;
+    // kernel variant: 1 = neither hinge / dynamics nor margin / equality
+    // paths, 2 = margin / equality paths only, 0 = every path
+    bool hd = false, me = false;
+    for (const Bucket &bk : g->buckets) {
+        hd = hd || bk.type == FGA_SVM_HINGE || bk.type == FGA_MPC_DYN;
+        me = me || bk.type == FGA_SVM_MARGIN || bk.type == FGA_EQUAL;
+    }
+    g->kind = hd ? 0 : me ? 2 : 1;
     if (tile) {
         g->blk = g->tile.W * 32;
         g->smem = tile_smem_bytes(g->tile);

@@ -612,6 +612,106 @@ __device__ __forceinline__ void item_svm_hinge_warp(const SweepArgs<R> &a, const
     }
 }
 
+// Appendix C one-point margin: the indicator of y (w.x + b) >= 1 - xi on
+// (w in R^D, b, xi), one thread per factor.  The prox is the rho-weighted
+// projection onto the half-space a.v >= 1 with a = (y x, y, 1):
+// v = n + lambda a / rho, lambda = (1 - a.n)^+ / sum_k a_k^2 / rho_k.  Two
+// passes over the factor's edges (the first forms a.n and the weight sum in
+// the order of a serial loop, the second writes x).  Parameters
+// factor-major: p[f*(D+1) + j] = x_j, then y.
+template <typename R, int MODE, bool FAST>
+__device__ __forceinline__ void item_svm_margin(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
+                                                int f, double &pri) {
+    const int D = B.arity - 2;
+    const R *p = B.prm + (long long)f * (D + 1);
+    const R y = p[D];
+    R an = R(0), awa = R(0);
+    for (int j = 0; j < D + 2; ++j) {
+        const int e = bedge(B, f, j);
+        R u;
+        unsigned ix;
+        const R n = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
+        const R aj = j < D ? y * p[j] : (j == D ? y : R(1));
+        an += aj * n;
+        awa += (aj * aj) / edge_rho(a, e);
+    }
+    if (MODE == F_U_ONLY) return;
+    const R viol = R(1) - an;
+    const R lam = viol > R(0) ? viol / awa : R(0);
+    for (int j = 0; j < D + 2; ++j) {
+        const int e = bedge(B, f, j);
+        const R u = a.u[e];
+        unsigned ix;
+        const R n = edge_z<R, FAST>(a, io, e, ix) - u;
+        const R aj = j < D ? y * p[j] : (j == D ? y : R(1));
+        edge_post<R, FAST>(a, io, e, ix, n + (lam * aj) / edge_rho(a, e), u);
+    }
+}
+
+// The margin operator with one warp per factor (fast order): lane l owns
+// the edges j = l, l + 32, ...; a.n and the weight sum are reduced with a
+// fixed shuffle tree; one pass, the factor's edges and data point read
+// contiguously (factor-major storage).
+template <typename R, int MODE>
+__device__ __forceinline__ void item_svm_margin_warp(const SweepArgs<R> &a, const BucketDev<R> &B,
+                                                     const EdgeIO<R> &io, int f, double &pri) {
+    constexpr int JMAX = 4;   // up to 128 edges per factor kept in registers
+    const int D = B.arity - 2;
+    const int lane = threadIdx.x & 31;
+    const R *p = B.prm + (long long)f * (D + 1);
+    const R y = p[D];
+    const int e0 = B.ebase + f * B.arity;
+    R n[JMAX], u[JMAX], rho[JMAX], av[JMAX];
+    unsigned ix[JMAX];
+    R an = R(0), awa = R(0);
+    #pragma unroll
+    for (int q = 0; q < JMAX; ++q) {
+        const int j = lane + 32 * q;
+        if (j > D + 1) continue;
+        const int e = e0 + j;
+        n[q] = edge_pre<R, MODE, true>(a, io, e, u[q], ix[q], pri);
+        rho[q] = edge_rho(a, e);
+        av[q] = j < D ? y * p[j] : (j == D ? y : R(1));
+        an += av[q] * n[q];
+        awa += (av[q] * av[q]) / rho[q];
+    }
+    if (MODE == F_U_ONLY) return;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        an += __shfl_xor_sync(0xffffffffu, an, o);
+        awa += __shfl_xor_sync(0xffffffffu, awa, o);
+    }
+    const R viol = R(1) - an;
+    const R lam = viol > R(0) ? viol / awa : R(0);
+    #pragma unroll
+    for (int q = 0; q < JMAX; ++q) {
+        const int j = lane + 32 * q;
+        if (j > D + 1) continue;
+        edge_post<R, true>(a, io, e0 + j, ix[q], n[q] + (lam * av[q]) / rho[q], u[q]);
+    }
+}
+
+// Appendix C equality of two copies v1, v2 in R^D: both become the
+// rho-weighted mean of the two messages, component by component.  One work
+// item per component pair, li = j * nf + f, edge-major storage (the pairs
+// of consecutive items sit side by side).
+template <typename R, int MODE, bool FAST>
+__device__ __forceinline__ void item_equal(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io, int li,
+                                           double &pri) {
+    const int D = B.arity >> 1;
+    const int j = li / B.nf, f = li - j * B.nf;
+    const int e1 = bedge(B, f, j), e2 = bedge(B, f, D + j);
+    R u1, u2;
+    unsigned i1, i2;
+    const R n1 = edge_pre<R, MODE, FAST>(a, io, e1, u1, i1, pri);
+    const R n2 = edge_pre<R, MODE, FAST>(a, io, e2, u2, i2, pri);
+    if (MODE == F_U_ONLY) return;
+    const R r1 = edge_rho(a, e1), r2 = edge_rho(a, e2);
+    const R v = (r1 * n1 + r2 * n2) / (r1 + r2);
+    edge_post<R, FAST>(a, io, e1, i1, v, u1);
+    edge_post<R, FAST>(a, io, e2, i2, v, u2);
+}
+
 // Appendix B dynamics: v = P n with P the rho-weighted projector onto
 // {x' = A x + B u}, precomputed per distinct (A, B, rho).  AC = compile-time
 // arity (n kept in registers), or 0 for any arity (n re-formed from u and z
@@ -689,6 +789,11 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
         if (x > hi) x = hi;
         break;
     }
+    case 11: {  // SVM_SLACK: f = lambda xi on xi >= 0
+        const R v = n - B.prm[f] / rho;
+        x = v > R(0) ? v : R(0);
+        break;
+    }
     default:  // 9, FIX
         x = B.prm[li];
         break;
@@ -696,9 +801,11 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
     edge_post<R, FAST>(a, io, e, ix, x, u);
 }
 
-// KIND 0: every factor type; KIND 1: graphs without hinge and dynamics
-// factors (packing), compiled without those paths so that their register
-// demand does not limit the packing kernel.
+// KIND 0: every factor type; KIND 1: graphs without hinge, dynamics, margin
+// and equality factors (packing); KIND 2: graphs with margin or equality
+// factors but no hinge or dynamics factors (the paper's SVM form).  Each
+// kernel is compiled without the paths its graphs lack, so that their
+// register demand does not limit it.
 template <typename R, int MODE, bool FAST, int KIND>
 __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                   int li, double &pri) {
@@ -714,6 +821,12 @@ __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const B
             else if (B.arity == 9) item_mpc_dyn<R, MODE, FAST, 9>(a, B, io, li, pri);   // 4 states, 1 input
             else item_mpc_dyn<R, MODE, FAST, 0>(a, B, io, li, pri);
         }
+        break;
+    case 10:
+        if constexpr (KIND != 1) item_svm_margin<R, MODE, FAST>(a, B, io, li, pri);
+        break;
+    case 12:
+        if constexpr (KIND != 1) item_equal<R, MODE, FAST>(a, B, io, li, pri);
         break;
     default: item_elementwise<R, MODE, FAST>(a, B, io, li, pri); break;
     }
@@ -817,6 +930,11 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, dou
         } else if (KIND == 0 && B.type == 4 && B.arity <= 128) {
             const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
             for (int i = warp; i < ch.nitems; i += nwarps) item_svm_hinge_warp<R, MODE>(a, B, io, f0 + i, pri);
+        } else if (KIND == 2 && B.type == 10 && B.arity >= 16 && B.arity <= 128) {
+            // a warp per margin factor once a factor fills half a warp;
+            // smaller factors keep one thread each
+            const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+            for (int i = warp; i < ch.nitems; i += nwarps) item_svm_margin_warp<R, MODE>(a, B, io, f0 + i, pri);
         } else {
             for (int i = threadIdx.x; i < ch.nitems; i += blockDim.x)
                 process_in_bucket<R, MODE, true, KIND>(a, B, io, f0 + i, pri);

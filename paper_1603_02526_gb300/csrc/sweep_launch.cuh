@@ -31,7 +31,14 @@ static cudaError_t allow_smem_k(int smem) {
 
 template <typename R>
 static cudaError_t allow_smem(int smem, int kind) {
-    return kind == 1 ? allow_smem_k<R, 1>(smem) : allow_smem_k<R, 0>(smem);
+    return kind == 1 ? allow_smem_k<R, 1>(smem) : kind == 2 ? allow_smem_k<R, 2>(smem) : allow_smem_k<R, 0>(smem);
+}
+
+template <typename R>
+static const void *persistent_fn(int kind) {
+    return kind == 1   ? (const void *)k_sweep_persistent<R, 1>
+           : kind == 2 ? (const void *)k_sweep_persistent<R, 2>
+                       : (const void *)k_sweep_persistent<R, 0>;
 }
 
 template <typename R>
@@ -42,8 +49,7 @@ cudaError_t sweep_persistent(const SweepArgs<R> &a, int grid, int block, int sme
     // Cooperative launch: the runtime refuses a grid that cannot be
     // co-resident, so the grid-wide barrier can never wait on a CTA that
     // was not scheduled.
-    const void *fn = kind == 1 ? (const void *)k_sweep_persistent<R, 1> : (const void *)k_sweep_persistent<R, 0>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, (size_t)smem, s);
+    return cudaLaunchCooperativeKernel(persistent_fn<R>(kind), dim3(grid), dim3(block), args, (size_t)smem, s);
 }
 
 template <typename R, int KIND>
@@ -61,6 +67,7 @@ cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int g
     cudaError_t e = allow_smem<R>(smem, kind);
     if (e != cudaSuccess) return e;
     if (kind == 1) phase_f_k<R, 1>(a, mode, xp, zp, grid, block, smem, s);
+    else if (kind == 2) phase_f_k<R, 2>(a, mode, xp, zp, grid, block, smem, s);
     else phase_f_k<R, 0>(a, mode, xp, zp, grid, block, smem, s);
     return cudaGetLastError();
 }
@@ -83,8 +90,8 @@ template <typename R>
 int sweep_max_blocks_per_sm(int block, int smem, int kind) {
     if (allow_smem<R>(smem, kind) != cudaSuccess) return 0;
     int n = 0;
-    const void *fn = kind == 1 ? (const void *)k_sweep_persistent<R, 1> : (const void *)k_sweep_persistent<R, 0>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, (size_t)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_fn<R>(kind), block, (size_t)smem) != cudaSuccess)
+        return 0;
     return n;
 }
 
