@@ -28,6 +28,7 @@ inline __host__ __device__ constexpr int align16(int v) { return (v + 15) & ~15;
 // Canonical z order: the staging rows of warp 0 (32 values plus one of pad,
 // which spreads the lanes' rows over the banks), two buffers.
 constexpr int kZRow = 33;
+constexpr int kZShort = 8;   // canonical z: rows up to this length summed by one thread each, unstaged
 inline __host__ __device__ constexpr int canonical_z_smem(int rsize) { return 2 * 32 * kZRow * rsize; }
 
 inline __host__ __device__ constexpr ChunkSmem chunk_smem(int rsize) {

@@ -985,20 +985,32 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     if (a.zorder == 0) {
-        // canonical: warp 0 of a CTA takes 32 consecutive variables, one per
-        // lane; the warp copies 32 values of each of the 32 rows at a time
-        // into shared memory (cp.async, zero past a row's end; two buffers,
-        // the next block in flight while this one is added) and each lane
-        // adds its own row's values one by one in creation order.  One lane
-        // per variable keeps every FP64 addition of a warp useful.
+        // canonical.  Rows of at most kZShort values: one thread per
+        // variable over the whole grid, its values added one by one in
+        // creation order straight from the variable-major array.
+        for (long long b = gtid; b < a.nz; b += gstride) {
+            const int k0 = a.row[b], k1 = a.row[b + 1];
+            if (k1 - k0 > kZShort) continue;
+            R S = R(0);
+            for (int k = k0; k < k1; ++k) S += ldg_l2(a.pvm + k);
+            z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
+        }
+        // Longer rows: warp 0 of a CTA takes 32 consecutive variables, one
+        // per lane; the warp copies 32 values of each of the 32 rows at a
+        // time into shared memory (cp.async, zero past a row's end; two
+        // buffers, the next block in flight while this one is added) and
+        // each lane adds its own row's values one by one in creation order.
+        // One lane per variable keeps every FP64 addition of a warp useful.
+        // Both paths add in the same order, so the sums are the same.
         if ((threadIdx.x >> 5) == 0) {
             extern __shared__ __align__(16) unsigned char zs_raw[];
             R *zbuf = reinterpret_cast<R *>(zs_raw);   // [2][32 rows][kZRow]
             const int lane = threadIdx.x & 31;
             for (long long base = (long long)blockIdx.x * 32; base < a.nz; base += (long long)gridDim.x * 32) {
                 const long long b = base + lane;
-                const bool valid = b < a.nz;
-                const int k0 = valid ? a.row[b] : 0, len = valid ? a.row[b + 1] - k0 : 0;
+                const int k0r = b < a.nz ? a.row[b] : 0, lenr = b < a.nz ? a.row[b + 1] - k0r : 0;
+                const bool valid = b < a.nz && lenr > kZShort;   // short rows are done above
+                const int k0 = valid ? k0r : 0, len = valid ? lenr : 0;
                 int maxlen = len;
                 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
