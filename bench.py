@@ -484,7 +484,8 @@ def run_extras(log=None):
 def run_profile(args):
     """One warm-up and one solve of --profile-iters iterations (the workload
     of the benchmark, or with --profile-workload svm the SVM of the extras,
-    or with mpc_one the slowest instance of the MPC batch alone, or with
+    mpc_horizon the K = 10^5 pendulum MPC, svm_paper the paper-form SVM
+    (100k x 64), mpc_one the slowest instance of the MPC batch alone, or
     mlp_forward the warm-start network's inference), at a length that suits
     an ncu capture."""
     import torch
@@ -523,6 +524,10 @@ def run_profile(args):
         return 0
     if args.profile_workload == "svm":
         p = inputs.svm_problem(100000, 64, seed=3000)
+    elif args.profile_workload == "mpc_horizon":
+        p = inputs.mpc_horizon_problem(100000)
+    elif args.profile_workload == "svm_paper":
+        p = inputs.svm_paper_problem(100000, 64, seed=3000, C=1000.0)
     else:
         p = inputs.packing_problem(N_DISKS, seed=SEED)
     opts = {_lib.FGA_OPT_STORE_M: 0}
@@ -549,7 +554,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the packing sweep (no SVM / MPC / warm start)")
     ap.add_argument("--zorder", type=int, default=None,
                     help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 disk tiles, 3 hinge bank)")
-    ap.add_argument("--profile-workload", default="packing", choices=["packing", "svm", "mpc_one", "mlp_forward"])
+    ap.add_argument("--profile-workload", default="packing",
+                    choices=["packing", "svm", "mpc_horizon", "svm_paper", "mpc_one", "mlp_forward"])
     ap.add_argument("--profile-threads", type=int, default=256, help="CTA size of the mpc_one profiling run")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")
