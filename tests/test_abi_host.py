@@ -112,3 +112,72 @@ def test_binding_counts_match_problem(lib):
     assert info["num_edges"] == p.num_edges == 1340
     assert info["num_factors"] == inputs.packing_counts(20)["factors"]
     assert info["num_vars"] == 40
+
+
+def test_paper_svm_types_validation(lib):
+    """Shapes and parameters of the margin, minimal-error and equality types
+    (Appendix C) are checked at registration."""
+    from paper_1603_02526_gb300._lib import FGA_EINVAL
+    from paper_1603_02526_gb300 import inputs
+    g = _new(lib, 0)
+    first = ctypes.c_int64()
+    assert lib.fga_add_variables(g, 2, 3, ctypes.byref(first)) == 0            # w copies: ids 0, 1
+    assert lib.fga_add_variables(g, 2, 1, ctypes.byref(first)) == 0            # b, xi: ids 2, 3
+    P = ctypes.c_void_p
+    eq_ok = np.array([[0, 1]], dtype=np.int64)
+    eq_bad = np.array([[0, 2]], dtype=np.int64)                               # dims 3 and 1
+    assert lib.fga_add_factors(g, inputs.EQUAL, 1, 2, P(eq_ok.ctypes.data), None, 0, 0, None) == 0
+    assert lib.fga_add_factors(g, inputs.EQUAL, 1, 2, P(eq_bad.ctypes.data), None, 0, 0, None) == FGA_EINVAL
+    mg = np.array([[0, 2, 3]], dtype=np.int64)
+    xy = np.array([0.5, -1.0, 2.0, 1.0])                                      # x[3], y
+    assert lib.fga_add_factors(g, inputs.SVM_MARGIN, 1, 3, P(mg.ctypes.data), P(xy.ctypes.data), 4, 0, None) == 0
+    assert lib.fga_add_factors(g, inputs.SVM_MARGIN, 1, 3, P(mg.ctypes.data), P(xy.ctypes.data), 3, 0,
+                               None) == FGA_EINVAL                            # parameter count
+    mg_bad = np.array([[0, 2, 1]], dtype=np.int64)                            # xi of dimension 3
+    assert lib.fga_add_factors(g, inputs.SVM_MARGIN, 1, 3, P(mg_bad.ctypes.data), P(xy.ctypes.data), 4, 0,
+                               None) == FGA_EINVAL
+    sl = np.array([[3]], dtype=np.int64)
+    lam_ok, lam_bad = np.array([0.5]), np.array([-1.0])
+    assert lib.fga_add_factors(g, inputs.SVM_SLACK, 1, 1, P(sl.ctypes.data), P(lam_ok.ctypes.data), 1, 0, None) == 0
+    assert lib.fga_add_factors(g, inputs.SVM_SLACK, 1, 1, P(sl.ctypes.data), P(lam_bad.ctypes.data), 1, 0,
+                               None) == FGA_EINVAL
+    assert lib.fga_destroy(g) == 0
+
+
+@pytest.mark.parametrize("which", ["svm_paper", "mpc_horizon"])
+def test_binding_counts_match_new_workloads(lib, which):
+    """The binding registers the paper-form SVM and the long-horizon MPC with
+    the counts their generators state."""
+    from paper_1603_02526_gb300 import inputs
+    from paper_1603_02526_gb300.graph import FactorGraph, _merge_var_blocks
+    if which == "svm_paper":
+        p = inputs.svm_paper_problem(50, 4, seed=1)
+        want = inputs.svm_paper_edges(50, 4)
+    else:
+        p = inputs.mpc_horizon_problem(300)
+        want = inputs.mpc_horizon_edges(300)
+    g = FactorGraph("f32")
+    for c, d in _merge_var_blocks(p.var_blocks):
+        g.fga_add_variables(c, d)
+    for b in p.factor_blocks:
+        g.fga_add_factors(b.ftype, b.var_ids, b.params if b.params.size else None)
+    info = g.fga_graph_info()
+    assert info["num_edges"] == p.num_edges == want
+    assert info["num_factors"] == p.num_factors
+    assert info["num_vars"] == p.num_vars
+
+
+def test_factor_type_numbers_agree():
+    """The factor-type numbers are an interface written down three times (the
+    C header, the input generators, the oracle); they must agree."""
+    import re
+    from paper_1603_02526_gb300 import inputs
+    import oracle.oracle as orc
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "fgadmm.h")).read()
+    names = ["PACK_PAIR", "PACK_WALL", "PACK_RADIUS_LIN", "PACK_RADIUS_QUAD", "SVM_HINGE", "SVM_L2", "MPC_DYN",
+             "MPC_QUAD", "MPC_BOX", "FIX", "SVM_MARGIN", "SVM_SLACK", "EQUAL"]
+    for n in names:
+        m = re.search(r"#define FGA_%s (\d+)" % n, hdr)
+        assert m, n
+        assert int(m.group(1)) == getattr(inputs, n) == getattr(orc, "T_" + n), n
+    assert int(re.search(r"#define FGA_NUM_TYPES (\d+)", hdr).group(1)) == len(names)

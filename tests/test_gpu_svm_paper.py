@@ -103,16 +103,3 @@ def test_svm_paper_converges_to_qp():
     np.testing.assert_allclose(W[0], sol.x[:2], atol=1e-5)
     np.testing.assert_allclose(bz, sol.x[2], atol=1e-5)
 
-
-def test_svm_paper_rejects_bad_shapes():
-    """Shape and parameter checks of the new types (no kernel runs)."""
-    from paper_1603_02526_gb300.graph import FactorGraph
-    g = FactorGraph("f32")
-    g.fga_add_variables(2, 3)
-    g.fga_add_variables(2, 1)
-    with pytest.raises(Exception):
-        g.fga_add_factors(inputs.EQUAL, np.array([[0, 2]]))                   # dims 3 and 1
-    with pytest.raises(Exception):
-        g.fga_add_factors(inputs.SVM_MARGIN, np.array([[0, 2, 1]]), np.zeros((1, 4)))  # xi of dim 3
-    with pytest.raises(Exception):
-        g.fga_add_factors(inputs.SVM_SLACK, np.array([[2]]), np.array([[-1.0]]))       # lambda < 0
