@@ -325,6 +325,7 @@ def run_extras(log=None):
     from paper_1603_02526_gb300 import inputs, _lib, warmstart
     from paper_1603_02526_gb300.graph import graph_from_problem
     from paper_1603_02526_gb300.mpc import batch_from_inputs
+    from paper_1603_02526_gb300.horizon import Horizon
     out = {}
     peak, peak_kind = _peaks()
     # packing N = 1000 in FP64 (canonical order: bit-exact with the serial
@@ -416,7 +417,8 @@ def run_extras(log=None):
     hz = {"workload": "inverted-pendulum MPC, one instance as one factor graph (FIX, DYN, stage and terminal "
                       "QUAD; 14 scalar edges per step), rho 1, z0 = 0; FP32 fast z order and FP64 canonical "
                       "order; per K: device time of 100 fused iterations",
-          "kernel": "k_sweep_persistent<float> / <double>", "per_K": {}}
+          "kernel": "k_sweep_persistent<float> / <double>; f32_grid: k_horizon (one step per thread, "
+                    "messages in registers, one grid barrier per iteration)", "per_K": {}}
     for K in (200, 1000, 10000, 50000, 100000):
         p = inputs.mpc_horizon_problem(K)
         row = {"scalar_edges": p.num_edges}
@@ -435,6 +437,21 @@ def run_extras(log=None):
                                            "status": r["status"], "ms": r["ms"], "r_pri": r["r_pri"],
                                            "r_dual": r["r_dual"]}
             del g
+        # the same graph with the horizon laid along the grid (fga_horizon_*)
+        h = Horizon.from_problem(p)
+        h.fga_horizon_init()
+        h.fga_horizon_solve(20, check_every=20)
+        h.fga_horizon_init()
+        r = h.fga_horizon_solve(100, check_every=100)
+        row["f32_grid"] = {"ms_100_iters": r["ms"], "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3),
+                           "frac_of_hbm": 20 * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak}
+        if K == 100000:
+            h.fga_horizon_init()
+            r = h.fga_horizon_solve(50000, 1e-5, 1e-5, check_every=10)
+            hz["solve_K100000_f32_grid"] = {"tol": 1e-5, "check_every": 10, "iters": r["iters"],
+                                            "status": r["status"], "ms": r["ms"], "r_pri": r["r_pri"],
+                                            "r_dual": r["r_dual"]}
+        del h
         hz["per_K"][str(K)] = row
     hz["peak_kind"] = peak_kind
     out["mpc_horizon"] = hz

@@ -239,6 +239,52 @@ int fga_read_edge_state(fga_graph *g, int32_t which, double *out, int64_t n);
 int fga_destroy(fga_graph *g);
 
 /* ==========================================================================
+ * One long-horizon MPC (Sec. V-B: the paper's sampled inverted pendulum,
+ * A 4 x 4, B 4 x 1, horizons up to 10^5) solved by Algorithm 2 in FP32 with
+ * the horizon laid along the grid: the factor graph
+ *   FIX(x_0) | DYN(x_t, u_t, x_{t+1}) t<K | QUAD(x_t, u_t) t<K | QUAD(x_K)
+ * (creation order; Appendix B operators: fixed value, the rho-weighted
+ * projection onto x' = A x + B u, f = 1/2 v' diag(q, r) v), uniform rho and
+ * alpha.  E = 14 K + 8 scalar edges, numbered in creation order (FIX 0..3,
+ * DYN_t from 4 + 9 t, QUAD_t from 4 + 9 K + 5 t, the terminal cost from
+ * 4 + 14 K); z = x_0..x_K (4 each), then u_0..u_{K-1}.  The same graph on
+ * the general path (fga_graph_*) gives the same iterates up to FP32
+ * rounding.  One thread per step, its messages in registers; one grid-wide
+ * barrier per iteration (one more on check iterations).
+ * ========================================================================== */
+typedef struct fga_horizon fga_horizon; /* opaque, library-owned */
+
+/* nx must be 4 and nu 1 (the pendulum); A (4 x 4) and B (4 x 1) row-major,
+ * q (4), r (1) the cost diagonals (>= 0), x0 the fixed state; rho, alpha
+ * > 0.  K steps need ceil(K / 224) co-resident CTAs (K up to about 10^5 on
+ * 152 SMs; FGA_EINVAL beyond).  Host pointers.  stream NULL: the object
+ * creates its own.  The state is undefined until fga_horizon_init. */
+int fga_horizon_create(fga_horizon **out, int32_t K, int32_t nx, int32_t nu, const double *A, const double *B,
+                       const double *q, const double *r, const double *x0, double rho, double alpha,
+                       int32_t device, void *cuda_stream);
+
+/* Cold start: z = 0, u = 0, x = 0 (n = z - u). */
+int fga_horizon_init(fga_horizon *h);
+
+/* Runs up to opts->max_iters iterations (opts as for fga_iterate; fused
+ * only), stopping at the first checked iteration whose RMS residuals meet
+ * both tolerances; the state after the call is the state after
+ * result->iters iterations, so calls chain.  FGA_ETIMEOUT when a grid-wide
+ * wait runs out (the state then needs fga_horizon_init). */
+int fga_horizon_solve(fga_horizon *h, const fga_iter_opts *opts, fga_iter_result *result);
+
+/* Readout in FP64 to host memory (any pointer may be NULL): z ((K+1) 4 + K
+ * values, variable order above), x and u (E values each, creation order). */
+int fga_horizon_read(fga_horizon *h, double *z, double *x_edges, double *u_edges);
+
+/* info[0] CTAs, info[1] steps (threads) per CTA, info[2] E, info[3] scalar
+ * variables.  n >= 4. */
+int fga_horizon_info(const fga_horizon *h, int64_t *info, int32_t n);
+
+/* Frees every resource of the object. */
+int fga_horizon_destroy(fga_horizon *h);
+
+/* ==========================================================================
  * Batched ragged MPC (Sec. V-B, Appendix B): many independent instances of
  *   minimise 1/2 sum_{t<T} (x_t' Q x_t + u_t' R u_t) + 1/2 x_T' Q x_T
  *   s.t. x_{t+1} = A x_t + B u_t, x_0 fixed, lo <= u_t <= hi (lo = -umax)

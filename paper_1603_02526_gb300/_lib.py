@@ -95,6 +95,12 @@ def _declare(lib):
         "fga_mpc_batch_autotune": [P, ctypes.c_char_p, i64, dbl, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_int32)],
         "fga_mpc_batch_destroy": [P],
+        "fga_horizon_create": [PP, i32, i32, i32, P, P, P, P, P, dbl, dbl, i32, P],
+        "fga_horizon_init": [P],
+        "fga_horizon_solve": [P, ctypes.POINTER(fga_iter_opts), ctypes.POINTER(fga_iter_result)],
+        "fga_horizon_read": [P, P, P, P],
+        "fga_horizon_info": [P, pi64, i32],
+        "fga_horizon_destroy": [P],
         "fga_mlp_create": [PP, i32, i32, i32, i32, i32, ctypes.c_uint64, i32, P],
         "fga_mlp_num_params": [P, pi64],
         "fga_mlp_set_params": [P, P, i64],

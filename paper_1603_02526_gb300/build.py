@@ -39,6 +39,7 @@ def _units():
         ("sweep_hinge.cu", nv),
         ("mpc_batch.cu", nv),
         ("mpc_noalloc.cu", nv),
+        ("mpc_horizon.cu", nv),
         ("mlp.cu", nv),
         ("fga_graph.cpp", None),
         ("fga_tile.cpp", None),
