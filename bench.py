@@ -501,7 +501,8 @@ def run_extras(log=None):
 def run_profile(args):
     """One warm-up and one solve of --profile-iters iterations (the workload
     of the benchmark, or with --profile-workload svm the SVM of the extras,
-    mpc_horizon the K = 10^5 pendulum MPC, svm_paper the paper-form SVM
+    mpc_horizon the K = 10^5 pendulum MPC (mpc_horizon_grid: with the
+    horizon along the grid), svm_paper the paper-form SVM
     (100k x 64), mpc_one the slowest instance of the MPC batch alone, or
     mlp_forward the warm-start network's inference), at a length that suits
     an ncu capture."""
@@ -539,6 +540,17 @@ def run_profile(args):
         print("profile run: MLP forward, 16384 rows, %d passes, %.3f ms each" % (
             args.profile_iters, e0.elapsed_time(e1) / args.profile_iters))
         return 0
+    if args.profile_workload == "mpc_horizon_grid":
+        # the K = 10^5 pendulum MPC with the horizon laid along the grid
+        from paper_1603_02526_gb300.horizon import Horizon
+        p = inputs.mpc_horizon_problem(100000)
+        h = Horizon.from_problem(p)
+        for _ in range(2):
+            h.fga_horizon_init()
+            r = h.fga_horizon_solve(args.profile_iters, check_every=args.profile_iters)
+        print("profile run: %d iterations, %.3f ms, %.3e edge-updates/s" % (
+            r["iters"], r["ms"], p.num_edges * r["iters"] / (r["ms"] * 1e-3)))
+        return 0
     if args.profile_workload == "svm":
         p = inputs.svm_problem(100000, 64, seed=3000)
     elif args.profile_workload == "mpc_horizon":
@@ -572,7 +584,8 @@ def main():
     ap.add_argument("--zorder", type=int, default=None,
                     help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 disk tiles, 3 hinge bank)")
     ap.add_argument("--profile-workload", default="packing",
-                    choices=["packing", "svm", "mpc_horizon", "svm_paper", "mpc_one", "mlp_forward"])
+                    choices=["packing", "svm", "mpc_horizon", "mpc_horizon_grid", "svm_paper", "mpc_one",
+                             "mlp_forward"])
     ap.add_argument("--profile-threads", type=int, default=256, help="CTA size of the mpc_one profiling run")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")
