@@ -181,3 +181,24 @@ def test_factor_type_numbers_agree():
         assert m, n
         assert int(m.group(1)) == getattr(inputs, n) == getattr(orc, "T_" + n), n
     assert int(re.search(r"#define FGA_NUM_TYPES (\d+)", hdr).group(1)) == len(names)
+
+
+def test_horizon_create_validation(lib):
+    """fga_horizon_create refuses bad shapes and parameters before it touches
+    a device."""
+    from paper_1603_02526_gb300._lib import FGA_EINVAL
+    P = ctypes.c_void_p
+    h = ctypes.c_void_p()
+    A, B = np.eye(4), np.ones((4, 1))
+    q, r, x0 = np.ones(4), np.ones(1), np.zeros(4)
+    ptrs = [P(v.ctypes.data) for v in (A, B, q, r, x0)]
+    assert lib.fga_horizon_create(ctypes.byref(h), 10, 12, 4, *ptrs, 1.0, 1.0, 0, None) == FGA_EINVAL
+    assert b"nx = 4" in lib.fga_last_error()
+    assert lib.fga_horizon_create(ctypes.byref(h), 0, 4, 1, *ptrs, 1.0, 1.0, 0, None) == FGA_EINVAL
+    assert lib.fga_horizon_create(ctypes.byref(h), 10, 4, 1, *ptrs, 0.0, 1.0, 0, None) == FGA_EINVAL
+    assert lib.fga_horizon_create(ctypes.byref(h), 10, 4, 1, None, *ptrs[1:], 1.0, 1.0, 0, None) == FGA_EINVAL
+    qn = -np.ones(4)
+    assert lib.fga_horizon_create(ctypes.byref(h), 10, 4, 1, ptrs[0], ptrs[1], P(qn.ctypes.data), ptrs[3], ptrs[4],
+                                  1.0, 1.0, 0, None) == FGA_EINVAL
+    assert lib.fga_horizon_init(None) == FGA_EINVAL
+    assert lib.fga_horizon_destroy(None) == 0
