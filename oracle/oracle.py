@@ -8,6 +8,7 @@ per iteration over factors, edges, variables, edges, edges, in FP64, with
 edge arrays in creation order (Sec. III) and each z-sum taken over the
 variable's edges in ascending creation order.
 """
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -59,32 +60,68 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build_oracle())
-        P = ctypes.c_void_p
-        i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-        dp = ctypes.POINTER(ctypes.c_double)
-        lp = ctypes.POINTER(ctypes.c_int64)
-        ip = ctypes.POINTER(ctypes.c_int32)
-        lib.og_new.restype = P
-        lib.og_free.argtypes = [P]
-        lib.og_add_vars.argtypes = [P, i64, i32]
-        lib.og_add_vars.restype = i64
-        lib.og_add_factors.argtypes = [P, i32, i64, i32, lp, i32, dp]
-        lib.og_add_factors.restype = i64
-        lib.og_num_edges.argtypes = [P]
-        lib.og_num_edges.restype = i64
-        lib.og_num_scalar_vars.argtypes = [P]
-        lib.og_num_scalar_vars.restype = i64
-        lib.og_finalize.argtypes = [P]
-        lib.og_set_rho_alpha.argtypes = [P, dp, dp, dbl, dbl]
-        lib.og_init.argtypes = [P, dp, dp]
-        lib.og_iterate.argtypes = [P, i64, dbl, dbl, i32, lp, dp, dp]
-        lib.og_get_edge.argtypes = [P, i32, dp]
-        lib.og_get_z.argtypes = [P, dp]
-        lib.og_get_edge_var.argtypes = [P, lp]
-        lib.og_prox.argtypes = [i32, i32, ip, dp, dp, dp, dp]
+        _lib = _declare(ctypes.CDLL(build_oracle()))
+        return _lib
+
+
+def build_variant(source_text, path):
+    """Compiles `source_text` (a modified copy of the oracle's C source) with
+    the oracle's flags into `path` and loads it.  For the planted-mistake
+    tests only: they check that the pins fail on such builds."""
+    src = path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
+                           "-fPIC", "-shared", "-o", path, src, "-lm"])
+    return _declare(ctypes.CDLL(path))
+
+
+@contextlib.contextmanager
+def using_build(lib):
+    """Routes every oracle call in the block to `lib` (a build_variant)."""
+    global _lib
+    _load()
+    with _lock:
+        saved = _lib
         _lib = lib
-        return lib
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
+
+
+def source_text():
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def _declare(lib):
+    """Argument and result types of the oracle's C entry points."""
+    P = ctypes.c_void_p
+    i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    lp = ctypes.POINTER(ctypes.c_int64)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib.og_new.restype = P
+    lib.og_free.argtypes = [P]
+    lib.og_add_vars.argtypes = [P, i64, i32]
+    lib.og_add_vars.restype = i64
+    lib.og_add_factors.argtypes = [P, i32, i64, i32, lp, i32, dp]
+    lib.og_add_factors.restype = i64
+    lib.og_num_edges.argtypes = [P]
+    lib.og_num_edges.restype = i64
+    lib.og_num_scalar_vars.argtypes = [P]
+    lib.og_num_scalar_vars.restype = i64
+    lib.og_finalize.argtypes = [P]
+    lib.og_set_rho_alpha.argtypes = [P, dp, dp, dbl, dbl]
+    lib.og_init.argtypes = [P, dp, dp]
+    lib.og_iterate.argtypes = [P, i64, dbl, dbl, i32, lp, dp, dp]
+    lib.og_get_edge.argtypes = [P, i32, dp]
+    lib.og_get_z.argtypes = [P, dp]
+    lib.og_get_edge_var.argtypes = [P, lp]
+    lib.og_prox.argtypes = [i32, i32, ip, dp, dp, dp, dp]
+    return lib
 
 
 def _dp(a):

@@ -1,0 +1,58 @@
+"""Planted mistakes in the oracle: each case builds a copy of the oracle with
+one plausible error (a wrong sign, swapped weights, a transposed operand, a
+dropped term) and runs the pins that cover that part against it; at least
+one of them must fail.  The mistakes exist only in temporary builds; the
+oracle itself is untouched."""
+import pytest
+
+from oracle import oracle as orc
+from tests import test_oracle_alg as alg
+from tests import test_oracle_prox as prox
+
+# (name, exact source text, replacement, pins that must catch it)
+MUTANTS = [
+    ("radius reward sign",
+     "x[0] = n[0] + p[0] / rho[0];", "x[0] = n[0] - p[0] / rho[0];",
+     [(prox.test_radius_rewards, dict(rho=r)) for r in (0.5, 1.0, 3.0)]),
+    ("wall weights swapped",
+     "double wc = 1.0 / rho[0], wr = 1.0 / rho[2];", "double wc = 1.0 / rho[2], wr = 1.0 / rho[0];",
+     [(prox.test_pack_wall_matches_bruteforce, dict(seed=s)) for s in range(10)]),
+    ("dynamics with B transposed",
+     "M[i * nvv + nx + j] = B[i * nu + j];", "M[i * nvv + nx + j] = B[j * nx + i];",
+     [(alg.test_mpc_inactive_box_is_lqr, {}), (alg.test_mpc_horizon_pendulum_is_lqr, {})]),
+    ("hinge step not clipped at c",
+     "if (gam > c) gam = c;", "",
+     [(prox.test_svm_hinge_matches_bruteforce, dict(seed=s)) for s in range(10)]),
+    ("z-update without the rho weights",
+     "S += g->rho[e] * g->m[e];", "S += g->m[e];",
+     [(alg.test_alg1_equals_alg2_scalar_consensus, {}), (alg.test_alg1_equals_alg2_mpc_without_box, {})]),
+    ("u-update with the wrong sign",
+     "g->u[e] = g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]);",
+     "g->u[e] = g->u[e] - g->alpha[e] * (g->x[e] - g->z[g->ez[e]]);",
+     [(alg.test_alg1_equals_alg2_scalar_consensus, {}), (alg.test_mpc_inactive_box_is_lqr, {})]),
+    ("margin: y dropped from the b update",
+     "x[d] = n[d] + (lam * y) / rho[d];", "x[d] = n[d] + lam / rho[d];",
+     [(prox.test_svm_margin_matches_bruteforce, dict(seed=s)) for s in range(10)]),
+    ("minimal error: threshold with the wrong sign",
+     "const double v = n[j] - p[0] / rho[j];", "const double v = n[j] + p[0] / rho[j];",
+     [(prox.test_svm_slack_matches_bruteforce, dict(lam=l)) for l in (0.0, 0.3, 2.0)]),
+    ("equality: weights swapped",
+     "const double v = (rho[j] * n[j] + rho[d + j] * n[d + j]) / (rho[j] + rho[d + j]);",
+     "const double v = (rho[d + j] * n[j] + rho[j] * n[d + j]) / (rho[j] + rho[d + j]);",
+     [(prox.test_equal_matches_constrained_minimiser, {})]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(tmp_path, name, old, new, pins):
+    src = orc.source_text()
+    assert src.count(old) == 1, "the planted line must match the oracle source exactly once"
+    lib = orc.build_variant(src.replace(old, new), str(tmp_path / "libmutant.so"))
+    failed = []
+    with orc.using_build(lib):
+        for pin, kw in pins:
+            try:
+                pin(**kw)
+            except Exception as e:   # an assertion, or a solver the mistake derailed
+                failed.append("%s(%s): %s" % (pin.__name__, kw, type(e).__name__))
+    assert failed, "no pin caught the planted mistake '%s'" % name
