@@ -397,3 +397,69 @@ def test_svm_small_matches_qp():
                    method="SLSQP", options=dict(ftol=1e-14, maxiter=2000))
     assert F(z) <= sol.fun + 1e-7
     np.testing.assert_allclose(z[:3], sol.x[:3], atol=1e-4)
+
+
+def test_two_factor_weighted_rho_and_alpha_by_hand():
+    """Per-edge rho and alpha, worked by hand (Algorithm 2's update rules,
+    Sec. II).  One scalar variable w; factor 1 is f = 1/2 w^2 (cost q = 1)
+    on an edge with rho 1, factor 2 fixes w = 4 on an edge with rho 3; both
+    edges take alpha = 1/2.  Start z = 0, u = 0, so n = 0.
+
+    Iteration 1: x = (rho n / (q + rho), 4) = (0, 4); m = x + u = (0, 4);
+      z = (1*0 + 3*4) / (1 + 3) = 3;  u = 0 + 1/2 (x - 3) = (-3/2, 1/2);
+      n = z - u = (9/2, 5/2).
+    Iteration 2: x = (1 * 9/2 / 2, 4) = (9/4, 4); m = (3/4, 9/2);
+      z = (3/4 + 27/2) / 4 = 57/16;  u = (-3/2 + 1/2 (9/4 - 57/16),
+      1/2 + 1/2 (4 - 57/16)) = (-69/32, 23/32);  n = (183/32, 91/32).
+    Every value is a dyadic rational, so FP64 holds it exactly.  An
+    unweighted mean would give z = 2 after iteration 1, and alpha taken as 1
+    would give u = (-3, 1)."""
+    g = OracleGraph()
+    g.add_variables(1, 1)
+    g.add_factors(inputs.MPC_QUAD, [[0]], [[1.0]])
+    g.add_factors(inputs.FIX, [[0]], [[4.0]])
+    g.finalize(np.array([1.0, 3.0]), np.array([0.5, 0.5]))
+    g.init(np.array([0.0]))
+    want = [
+        dict(x=[0.0, 4.0], m=[0.0, 4.0], z=[3.0], u=[-1.5, 0.5], n=[4.5, 2.5]),
+        dict(x=[2.25, 4.0], m=[0.75, 4.5], z=[57 / 16], u=[-69 / 32, 23 / 32], n=[183 / 32, 91 / 32]),
+    ]
+    for w in want:
+        g.iterate(1)
+        assert list(g.edge(EDGE_X)) == w["x"]
+        assert list(g.edge(EDGE_M)) == w["m"]
+        assert list(g.z()) == w["z"]
+        assert list(g.edge(EDGE_U)) == w["u"]
+        assert list(g.edge(EDGE_N)) == w["n"]
+    # the fixed point does not depend on rho or alpha: z -> 4, and the
+    # quadratic edge's x -> 4 as well (its u carries the cost's gradient)
+    g.iterate(2000)
+    np.testing.assert_allclose(g.z(), [4.0], rtol=1e-12)
+    np.testing.assert_allclose(g.edge(EDGE_X), [4.0, 4.0], rtol=1e-9)
+    # at the fixed point the cost edge has x = rho n / (q + rho) = z, so
+    # u_1 = z - n = -q z / rho_1 = -4; with one alpha and u0 = 0 the sum
+    # rho_1 u_1 + rho_2 u_2 stays 0 (next test)
+    u = g.edge(EDGE_U)
+    np.testing.assert_allclose(u[0], -4.0, rtol=1e-9)
+    np.testing.assert_allclose(1.0 * u[0] + 3.0 * u[1], 0.0, atol=1e-9)
+
+
+def test_weighted_dual_sum_decays_by_one_minus_alpha():
+    """With one alpha on every edge of a variable, sum_e rho_e u_e after an
+    iteration is (1 - alpha) times its value before (the z-update makes the
+    rho-weighted mean of x + u equal z); with u0 = 0 it stays 0.  Checked
+    on a three-factor scalar graph with unequal rho and alpha = 0.3."""
+    g = OracleGraph()
+    g.add_variables(1, 1)
+    g.add_factors(inputs.MPC_QUAD, [[0]], [[2.0]])
+    g.add_factors(inputs.PACK_RADIUS_LIN, [[0]], [[0.7]])
+    g.add_factors(inputs.FIX, [[0]], [[-1.25]])
+    rho = np.array([0.5, 2.0, 1.5])
+    g.finalize(rho, 0.3)
+    u0 = np.array([0.4, -0.1, 0.2])
+    g.init(np.array([0.25]), u0)
+    s = float(rho @ u0)
+    for _ in range(5):
+        g.iterate(1)
+        s *= 0.7
+        np.testing.assert_allclose(float(rho @ g.edge(EDGE_U)), s, rtol=1e-12, atol=1e-15)

@@ -40,6 +40,15 @@ MUTANTS = [
      "const double v = (rho[j] * n[j] + rho[d + j] * n[d + j]) / (rho[j] + rho[d + j]);",
      "const double v = (rho[d + j] * n[j] + rho[j] * n[d + j]) / (rho[j] + rho[d + j]);",
      [(prox.test_equal_matches_constrained_minimiser, {})]),
+    ("u-update ignores alpha",
+     "g->u[e] = g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]);",
+     "g->u[e] = g->u[e] + (g->x[e] - g->z[g->ez[e]]);",
+     [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {}),
+      (alg.test_weighted_dual_sum_decays_by_one_minus_alpha, {})]),
+    ("z-update as an unweighted mean",
+     "S += g->rho[e] * g->m[e];\n                R += g->rho[e];",
+     "S += g->m[e];\n                R += 1.0;",
+     [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {})]),
 ]
 
 
