@@ -239,6 +239,80 @@ int fga_read_edge_state(fga_graph *g, int32_t which, double *out, int64_t n);
 int fga_destroy(fga_graph *g);
 
 /* ==========================================================================
+ * Shards: one graph split across GPUs (one process per GPU).  The paper
+ * names multi-GPU execution as future work (Sec. VI); its z-update is the
+ * only step that couples factors, through the sums S_b = sum rho m and
+ * R_b = sum rho over each variable's edges (Sec. II), so the factors are cut
+ * into contiguous slices in creation order, one per rank, and the ranks
+ * exchange only those sums.
+ *
+ * Each rank builds the same variables (every rank calls fga_add_variables
+ * identically) and only its slice of the factors, in creation order, with
+ * FGA_OPT_ZORDER 0 or 1.  Its edges are then a contiguous run of the whole
+ * graph's creation order: rank r's edges follow rank r-1's.
+ *   Set-up: R_b and sum rho^2 are chained through the ranks in rank order
+ *     (fga_shard_rho_chain, host arrays: rank 0 from NULL, rank r from rank
+ *     r-1's output; the last rank's output is the graph-wide sum) and
+ *     handed to every rank by fga_shard_begin.
+ *   Iteration: fga_shard_xstep (deferred u- and n-update, x-update, m, and
+ *     this rank's running sums of rho m), an exchange of those sums by the
+ *     caller, fga_shard_zstep (z from the graph-wide sums).  Two exchanges
+ *     are supported:
+ *     - chain (canonical order, FGA_OPT_ZORDER 0): rank r passes rank r-1's
+ *       output as s_in; each rank adds its terms one by one onto it, so the
+ *       last rank's output equals the serial creation-order sum of the
+ *       whole graph bit for bit; it is then broadcast to every rank;
+ *     - gather (any order): every rank runs s_in = NULL, the outputs are
+ *       all-gathered and fga_shard_add_parts sums them in rank order.
+ *   Residuals: the x-step that follows a checked z-step (check_prev = 1),
+ *     or fga_shard_finish at the end, gives this rank's primal partial sum;
+ *     the checked z-step gives the graph-wide dual sum (the same value on
+ *     every rank); fga_shard_stop_rule applies the stop rule.  A stop after
+ *     an x-step leaves the state of the checked iteration (the x just
+ *     computed is discarded), as fga_iterate does.
+ * Device work is queued on the graph's stream and these calls return
+ * without waiting; s_in, s_out, parts and total are device arrays of the
+ * graph's precision (float for FGA_F32, double for FGA_F64) with one value
+ * per scalar variable; pri_out and dual_out are device doubles.  A shard
+ * graph cannot be run by fga_iterate (FGA_ESTATE).
+ * ========================================================================== */
+
+/* Host arrays of n = scalar variables: out = in + this graph's rho (and
+ * rho^2) added one by one in creation order (in may be NULL: zeros). */
+int fga_shard_rho_chain(const fga_graph *g, const double *srho_in, const double *srho2_in, double *srho_out,
+                        double *srho2_out);
+
+/* Switches a finalized graph into shard mode with the graph-wide sums (host
+ * arrays).  FGA_EINVAL for the disk-tile or hinge-bank orders. */
+int fga_shard_begin(fga_graph *g, const double *srho_total, const double *srho2_total);
+
+/* One x-step: the pending u- and n-update (after a z-step), the x-update of
+ * every factor of the shard, m = x + u, and s_out = s_in + this shard's
+ * rho m terms.  check_prev = 1 also writes this shard's primal residual sum
+ * sum (x - z)^2 of the pending iteration to *pri_out (needs a pending
+ * z-step). */
+int fga_shard_xstep(fga_graph *g, int32_t check_prev, const void *s_in, void *s_out, double *pri_out);
+
+/* total = parts[0] + parts[1] + ... + parts[n_shards - 1] per variable, in
+ * that order (parts: n_shards consecutive arrays). */
+int fga_shard_add_parts(fga_graph *g, const void *parts, int32_t n_shards, void *total);
+
+/* z = total / R per variable (a variable with R = 0 keeps z); with check,
+ * the graph-wide dual residual sum sum_b (sum_e rho^2) (z_b - z_b^prev)^2 to
+ * *dual_out.  Ends the iteration. */
+int fga_shard_zstep(fga_graph *g, const void *total, int32_t check, double *dual_out);
+
+/* The pending u-update at the end of a run, and this shard's primal
+ * residual sum of the last iteration to *pri_out. */
+int fga_shard_finish(fga_graph *g, double *pri_out);
+
+/* Stop rule on host values: RMS primal sqrt(sum_r pri_parts[r] / E) (the
+ * parts added in rank order), RMS dual sqrt(dual / E); *stop = 1 when both
+ * meet their tolerances or either is not finite. */
+int fga_shard_stop_rule(const double *pri_parts, int32_t n_shards, double dual, int64_t num_edges, double tol_pri,
+                        double tol_dual, double *r_pri, double *r_dual, int32_t *stop);
+
+/* ==========================================================================
  * One long-horizon MPC (Sec. V-B: the paper's sampled inverted pendulum,
  * A 4 x 4, B 4 x 1, horizons up to 10^5) solved by Algorithm 2 in FP32 with
  * the horizon laid along the grid: the factor graph
@@ -388,14 +462,19 @@ int fga_mpc_batch_destroy(fga_mpc_batch *b);
  * Cold start (z = u = x = 0) of n_inst instances of ONE system, FP32
  * messages, FP64 residuals; same model, factor graph and stopping rule as
  * fga_mpc_batch_solve with tol_pri = tol_dual = tol.  T: host array of
- * horizons.  A (nx x nx), B (nx x nu), q (nx), r (nu), x0 (n_inst x nx):
- * device FP32.  Outputs (device): z_out (sum of V = (nx + nu) T + nx values,
- * instances concatenated), iters_out and status_out per instance.  The work
- * is queued on `stream` (NULL: legacy default stream) and the call returns
- * without waiting; outputs are valid once the stream has synchronised.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any CUDA
- * graph capture.  All calls share the one array and every call overwrites
+ * horizons, read once during the call (the launch carries a copy, so the
+ * caller may change or free T as soon as the call returns).  A (nx x nx),
+ * B (nx x nu), q (nx), r (nu), x0 (n_inst x nx): device FP32, read when the
+ * work runs.  Outputs (device): z_out (sum of V = (nx + nu) T + nx values,
+ * instances concatenated), iters_out and status_out per instance; a
+ * non-finite A or B (a projector that cannot be formed) makes every
+ * status_out entry FGA_EINVAL.  The work is queued on `stream` (NULL: legacy
+ * default stream) and the call returns without waiting; outputs are valid
+ * once the stream has synchronised.  The first call on a device looks up
+ * the array's device address (once per device, with that device current)
+ * and keeps it for the life of the process: make that first call before any
+ * CUDA graph capture, and do not use this entry point across a
+ * cudaDeviceReset.  All calls share the one array and every call overwrites
  * it, so calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller. */
 int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t nx, int32_t nu, const float *A, const float *B,

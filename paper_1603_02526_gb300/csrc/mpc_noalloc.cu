@@ -12,6 +12,7 @@
 // library, for the life of the process.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,8 +33,12 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 
-// host-side device address of g_noalloc_scratch, per device (set up once)
-unsigned char *g_scratch_ptr[kNoAllocMaxDevices] = {};
+// host-side device address of g_noalloc_scratch, per device, looked up by
+// the first call on that device.  Threads that race on the first call store
+// the same value.  The address belongs to the device's current context: the
+// library must not be used across a cudaDeviceReset (the module may load
+// again at another address).
+std::atomic<unsigned char *> g_scratch_ptr[kNoAllocMaxDevices] = {};
 
 int nfail(int code, const char *fmt, ...) {
     char buf[384];
@@ -49,7 +54,9 @@ size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Projector onto {v : M v = 0}, M = [A B -I], uniform rho:
 // P = I - M^T (M M^T)^{-1} M, in FP64 by one CTA (Gauss-Jordan on M M^T in
 // shared memory), written as FP32.
-__global__ void k_projector(const float *A, const float *B, int nx, int nu, float *P) {
+// A non-finite A or B, or a zero pivot, sets *bad (the solve then reports
+// FGA_EINVAL for every instance, as the allocating path refuses the system).
+__global__ void k_projector(const float *A, const float *B, int nx, int nu, float *P, int *bad) {
     extern __shared__ double sh[];
     const int n = 2 * nx + nu;
     double *M = sh;                       // nx x n
@@ -73,6 +80,7 @@ __global__ void k_projector(const float *A, const float *B, int nx, int nu, floa
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        *bad = 0;
         for (int c = 0; c < nx; ++c) {
             int piv = c;
             for (int r = c + 1; r < nx; ++r)
@@ -84,6 +92,10 @@ __global__ void k_projector(const float *A, const float *B, int nx, int nu, floa
                     G[piv * 2 * nx + j] = t;
                 }
             const double d = G[c * 2 * nx + c];
+            if (!(fabs(d) > 0.0) || !isfinite(d)) {
+                *bad = 1;
+                break;
+            }
             for (int j = 0; j < 2 * nx; ++j) G[c * 2 * nx + j] /= d;
             for (int r = 0; r < nx; ++r) {
                 if (r == c) continue;
@@ -108,23 +120,40 @@ __global__ void k_projector(const float *A, const float *B, int nx, int nu, floa
     }
 }
 
-// instance offsets (prefix sums of the per-instance sizes), identity hand-out
-// order, every instance on system 0
-__global__ void k_offsets(const int *T, int n, int nx, int nu, long long *zoff, long long *eoff, int *order,
-                          int *sys) {
+// The horizons travel as a kernel parameter (16 KB, within the 32 KB
+// parameter limit): the launch copies them from the caller's array while the
+// call runs, so a later change to that array, or a replay of a captured
+// launch, cannot make the device tables disagree with the sizes the host
+// checked against the scratch array.
+struct HorizonTable {
+    int T[kNoAllocMaxInst];
+};
+static_assert(sizeof(HorizonTable) <= 32000, "kernel parameter limit");
+
+// horizons into scratch, instance offsets (prefix sums of the per-instance
+// sizes), identity hand-out order, every instance on system 0
+__global__ void k_offsets(const HorizonTable tbl, int n, int nx, int nu, int *T, long long *zoff,
+                          long long *eoff, int *order, int *sys) {
     if (threadIdx.x == 0) {
         long long z = 0, e = 0;
         for (int i = 0; i < n; ++i) {
             zoff[i] = z;
             eoff[i] = e;
-            z += (long long)(nx + nu) * T[i] + nx;
-            e += 2LL * nx + 3LL * (nx + nu) * T[i];
+            z += (long long)(nx + nu) * tbl.T[i] + nx;
+            e += 2LL * nx + 3LL * (nx + nu) * tbl.T[i];
         }
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        T[i] = tbl.T[i];
         order[i] = i;
         sys[i] = 0;
     }
+}
+
+// after the solve: a refused system overrides every instance's status
+__global__ void k_system_status(const int *bad, int n, int *status) {
+    if (*bad == 0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) status[i] = FGA_EINVAL;
 }
 
 }  // namespace
@@ -144,13 +173,18 @@ extern "C" int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t n
         return nfail(FGA_EINVAL, "fga_mpc_solve_noalloc: need 1 <= nx <= 32, nu >= 1, 2 nx + nu <= 64");
     if (!(umax > 0.f) || !(rho > 0.f) || !(alpha > 0.f) || max_iters < 0 || !(tol >= 0.0) || check_every < 1)
         return nfail(FGA_EINVAL, "fga_mpc_solve_noalloc: bad scalar argument");
+    // one read of the caller's horizons: the checks below and the launch
+    // parameter use this copy
+    HorizonTable tbl;
+    std::memcpy(tbl.T, T, (size_t)n_inst * sizeof(int));
     long long E = 0, Z = 0;
     int tmax = 0;
     for (int i = 0; i < n_inst; ++i) {
-        if (T[i] < 1 || T[i] > 100000) return nfail(FGA_EINVAL, "fga_mpc_solve_noalloc: horizon %d", T[i]);
-        E += 2LL * nx + 3LL * (nx + nu) * T[i];
-        Z += (long long)(nx + nu) * T[i] + nx;
-        tmax = T[i] > tmax ? T[i] : tmax;
+        const int t = tbl.T[i];
+        if (t < 1 || t > 100000) return nfail(FGA_EINVAL, "fga_mpc_solve_noalloc: horizon %d", t);
+        E += 2LL * nx + 3LL * (nx + nu) * t;
+        Z += (long long)(nx + nu) * t + nx;
+        tmax = t > tmax ? t : tmax;
     }
     (void)Z;
     const int Ad = 2 * nx + nu;
@@ -158,6 +192,8 @@ extern "C" int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t n
     size_t off = 0;
     const size_t o_queue = off;
     off = up256(off + sizeof(unsigned));
+    const size_t o_bad = off;
+    off = up256(off + sizeof(int));
     const size_t o_P = off;
     off = up256(off + (size_t)Ad * Ad * sizeof(float));
     const size_t o_T = off;
@@ -188,14 +224,15 @@ extern "C" int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t n
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return nfail(FGA_ECUDA, "fga_mpc_solve_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return nfail(FGA_EINVAL, "fga_mpc_solve_noalloc: device %d", dev);
-    if (!g_scratch_ptr[dev]) {
+    unsigned char *s = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!s) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr)
             return nfail(FGA_ECUDA, "fga_mpc_solve_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(ptr);
+        s = static_cast<unsigned char *>(ptr);
+        g_scratch_ptr[dev].store(s, std::memory_order_release);
     }
-    unsigned char *s = g_scratch_ptr[dev];
     cudaStream_t st = (cudaStream_t)stream;
     // inputs into scratch, derived tables, and the cold start (z, u, x = 0);
     // the array keeps the previous call's contents, so all of it is rewritten
@@ -204,11 +241,11 @@ extern "C" int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t n
         cudaError_t e_ = (call);                                                                            \
         if (e_ != cudaSuccess) return nfail(FGA_ECUDA, "fga_mpc_solve_noalloc: %s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
-    NA_TRY(cudaMemcpyAsync(s + o_T, T, (size_t)n_inst * sizeof(int), cudaMemcpyHostToDevice, st));
     const int psm = (nx * Ad + 2 * nx * nx + nx * Ad) * (int)sizeof(double);
-    k_projector<<<1, 128, psm, st>>>(A, B, nx, nu, reinterpret_cast<float *>(s + o_P));
+    k_projector<<<1, 128, psm, st>>>(A, B, nx, nu, reinterpret_cast<float *>(s + o_P),
+                                     reinterpret_cast<int *>(s + o_bad));
     NA_TRY(cudaGetLastError());
-    k_offsets<<<1, 256, 0, st>>>(reinterpret_cast<const int *>(s + o_T), n_inst, nx, nu,
+    k_offsets<<<1, 256, 0, st>>>(tbl, n_inst, nx, nu, reinterpret_cast<int *>(s + o_T),
                                  reinterpret_cast<long long *>(s + o_zoff), reinterpret_cast<long long *>(s + o_eoff),
                                  reinterpret_cast<int *>(s + o_order), reinterpret_cast<int *>(s + o_sys));
     NA_TRY(cudaGetLastError());
@@ -255,6 +292,9 @@ extern "C" int fga_mpc_solve_noalloc(int32_t n_inst, const int32_t *T, int32_t n
     NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = n_inst < bps * sms ? n_inst : bps * sms;
     NA_TRY(mpc_launch<float>(a, threads, grid, smem, st));
+    k_system_status<<<(n_inst + 255) / 256, 256, 0, st>>>(reinterpret_cast<const int *>(s + o_bad), n_inst,
+                                                          status_out);
+    NA_TRY(cudaGetLastError());
 #undef NA_TRY
     return FGA_OK;
 }
