@@ -157,28 +157,37 @@ def test_f32_packing_n20_objective():
     assert abs(fg - fo) <= 1e-4 * abs(fo), (fg, fo, rg, ro)
 
 
-def test_f32_n1000_bench_configuration_first_iterations():
-    """The benchmark's launch configuration (N=1000, FP32, fused, fast
-    z-order) against the FP64 oracle after 3 iterations.  z (an average of
-    ~1000 messages) must agree to 1e-5 of the variables' scale S.  Edge
-    messages are compared by distribution: the disk-pair prox divides by the
-    distance of two incoming centres, so FP32 rounding is amplified on the
-    few pairs whose messages come close; an FP32 emulation of the same
-    iterations (NumPy, exact sums) gives a median error of 7e-9, a 99.9th
-    percentile of 5e-7 and a maximum of 9e-5.  Bounds: 99.9th percentile
-    <= 1e-5 S, maximum <= 5e-3 S."""
+@pytest.mark.parametrize("iters", [3, 10])
+def test_f32_n1000_chunked_order_first_iterations(iters):
+    """N=1000 in FP32 through the chunked fast order (fused, m kept) against
+    the FP64 oracle after 3 and 10 iterations.  Its z sums are FP32 trees
+    (chunk partials, then warp and hub trees), so the yardstick is the FP32
+    emulation (tests/fp32_emulation.py) with pairwise FP32 sums: z, and every
+    edge message at the 99.9th percentile and at the maximum, within 4x the
+    emulation's own distance from the oracle (measured on GB300: at most
+    2.4x, the maximum after 10 iterations; 1.8x after 3).  The disk-pair operator divides by the distance of two incoming
+    centres, so the few pairs whose messages come close amplify rounding:
+    hence percentile and maximum apart."""
     from oracle.oracle import EDGE_X, EDGE_U, EDGE_N
+    from tests.fp32_emulation import PackingFP32
     p = inputs.packing_problem(1000)
     g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1})
-    g.fga_iterate(3)
+    assert g.fga_launch_info()["zorder"] == 1
+    g.fga_iterate(iters)
     o = oracle_from_problem(p)
-    o.iterate(3)
+    o.iterate(iters)
+    em = PackingFP32(p, sums="tree")
+    em.iterate(iters)
     S = float(np.max(np.abs(o.z())))
-    assert np.max(np.abs(g.fga_read_z() - o.z())) <= 1e-5 * S
-    for a, b in ((_lib.FGA_EDGE_X, EDGE_X), (_lib.FGA_EDGE_U, EDGE_U), (_lib.FGA_EDGE_N, EDGE_N)):
+    ez = np.abs(g.fga_read_z() - o.z()).max()
+    assert ez <= 4 * np.abs(em.z - o.z()).max(), (ez / S, np.abs(em.z - o.z()).max() / S)
+    for a, b, ref in ((_lib.FGA_EDGE_X, EDGE_X, em.x), (_lib.FGA_EDGE_U, EDGE_U, em.u),
+                      (_lib.FGA_EDGE_N, EDGE_N, em.n)):
         err = np.abs(g.fga_read_edge_state(a) - o.edge(b))
-        assert np.percentile(err, 99.9) <= 1e-5 * S, (a, np.percentile(err, 99.9))
-        assert err.max() <= 5e-3 * S, (a, err.max())
+        eref = np.abs(ref.astype(np.float64) - o.edge(b))
+        for q in (99.9, 100):
+            assert np.percentile(err, q) <= 4 * np.percentile(eref, q), (a, q, np.percentile(err, q) / S,
+                                                                            np.percentile(eref, q) / S)
 
 
 def test_f32_is_deterministic():

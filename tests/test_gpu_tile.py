@@ -51,22 +51,35 @@ def test_tile_order_is_the_f32_packing_default():
     assert graph_from_problem(q, "f64").fga_launch_info()["zorder"] == 0
 
 
-def test_tile_n1000_first_iterations_against_oracle():
-    """The benchmark graph after 3 iterations: z to 1e-5 S; edge messages
-    99.9th percentile <= 1e-5 S and maximum <= 5e-3 S (an FP32 emulation of
-    the same iterations gives 5e-7 S and 9e-5 S)."""
+@pytest.mark.parametrize("iters", [3, 10])
+def test_tile_n1000_first_iterations_against_oracle(iters):
+    """The benchmark graph after 3 and 10 iterations, against the FP64
+    oracle, with bounds set by what FP32 rounding alone does: the FP32
+    emulation (tests/fp32_emulation.py) with each z sum exact and rounded
+    once -- the tile order's fixed-point sums are exact too.  z, and every
+    edge message at the 99.9th percentile and at the maximum, within 2x the
+    emulation's own distance from the oracle (measured on GB300: at most
+    1.1x).  The disk-pair operator divides by the distance of two incoming
+    centres, so the few pairs whose messages come close amplify rounding:
+    hence percentile and maximum apart."""
+    from tests.fp32_emulation import PackingFP32
     p = inputs.packing_problem(1000)
     g = _tile(p)
-    r = g.fga_iterate(3)
-    assert r["iters"] == 3
+    r = g.fga_iterate(iters)
+    assert r["iters"] == iters
     o = oracle_from_problem(p)
-    ro = o.iterate(3)
+    ro = o.iterate(iters)
+    em = PackingFP32(p, sums="exact")
+    em.iterate(iters)
     S = float(np.max(np.abs(o.z())))
-    assert np.max(np.abs(g.fga_read_z() - o.z())) <= 1e-5 * S
-    for got, w in zip(_edges(g), (EDGE_X, EDGE_U, EDGE_N)):
+    ez = np.abs(g.fga_read_z() - o.z()).max()
+    assert ez <= 2 * np.abs(em.z - o.z()).max(), (ez / S, np.abs(em.z - o.z()).max() / S)
+    for got, w, ref in zip(_edges(g), (EDGE_X, EDGE_U, EDGE_N), (em.x, em.u, em.n)):
         err = np.abs(got - o.edge(w))
-        assert np.percentile(err, 99.9) <= 1e-5 * S, (w, np.percentile(err, 99.9))
-        assert err.max() <= 5e-3 * S, (w, err.max())
+        eref = np.abs(ref.astype(np.float64) - o.edge(w))
+        for q in (99.9, 100):
+            assert np.percentile(err, q) <= 2 * np.percentile(eref, q), (w, q, np.percentile(err, q) / S,
+                                                                            np.percentile(eref, q) / S)
     # residuals of the last iteration agree with the oracle's to FP32 level
     np.testing.assert_allclose([r["r_pri"], r["r_dual"]], [ro["r_pri"], ro["r_dual"]], rtol=1e-3)
 
