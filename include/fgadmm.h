@@ -223,6 +223,16 @@ int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result
  * n >= 7 info[6] the z-order in use (FGA_OPT_ZORDER values).  n >= 6. */
 int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n);
 
+/* Latency floor of the disk-tile order (FGA_OPT_ZORDER 2) on this graph's
+ * grid: device time of `iters` passes that do everything a pass does
+ * except the operators -- mode 1: each CTA's L2 loads of its variables'
+ * accumulators (the z gather), one fixed-point reduction per variable (the
+ * partial sums; the value added is zero) and the grid-wide barrier; mode
+ * 0: the barrier alone.  A measurement of the hardware's floor under a
+ * pass (the paper reports where an iteration's time goes, Sec. V-A); the
+ * graph's state is not changed.  *ms: device time (CUDA events). */
+int fga_latency_floor(fga_graph *g, int64_t iters, int32_t mode, float *ms);
+
 /* Residuals of the last checked iteration (NaN before any). */
 int fga_residuals(const fga_graph *g, double *r_pri, double *r_dual);
 

@@ -154,6 +154,10 @@ struct fga_graph {
     int64_t tile_pair_ebase = 0;
     bool uniform_rho = true, uniform_alpha = true;
     int grid = 1, blk = 256;
+    // shard mode (fga_shard_*): srho / srho2 hold the graph-wide sums; the
+    // u-update of the last z-step is pending until the next x-step
+    bool shard = false, shard_pending = false;
+    DevBuf shard_res;   // per-CTA dual partials of the z-step (fixed grid: equal on every rank)
 
     // state
     int64_t iters_done = 0;
@@ -1234,6 +1238,7 @@ extern "C" int fga_init(fga_graph *g, const double *z0, const double *u0) {
     g->xpar = 0;
     g->zpar = 0;
     g->tile_resume = false;
+    g->shard_pending = false;
     g->last_rp = g->last_rd = std::numeric_limits<double>::quiet_NaN();
     g->initialized = true;
     return FGA_OK;
@@ -1311,9 +1316,8 @@ static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
 }
 
 // Disk-tile order: one cooperative launch for the whole call (FP32).
-static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
+static void fill_tile_args(const fga_graph *g, TileArgs &a) {
     const TilePlan &T = g->tile;
-    TileArgs a;
     std::memset(&a, 0, sizeof a);
     a.G = T.G;
     a.U = T.U;
@@ -1352,6 +1356,11 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     a.E = g->ne;
     a.ctl = g->ctl.as<Ctl>();
     a.sync = g->bar.as<TileSync>();
+}
+
+static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
+    TileArgs a;
+    fill_tile_args(g, a);
     a.k0 = g->iters_done;
     a.K = o.max_iters;
     a.check_every = o.check_every;
@@ -1585,6 +1594,7 @@ extern "C" int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_res
         return fail(FGA_EINVAL, "fga_iterate: bad options");
     if (opts->fault_skip_block >= 0 && !opts->fused)
         return fail(FGA_EINVAL, "fga_iterate: fault_skip_block needs the fused kernel");
+    if (g->shard) return fail(FGA_ESTATE, "fga_iterate: the graph is a shard (use fga_shard_xstep / zstep)");
     if ((g->zorder == 2 || g->zorder == 3) && !opts->fused)
         return fail(FGA_EINVAL, "fga_iterate: the disk-tile and hinge-bank orders run as one persistent launch "
                                 "(fused = 1); set FGA_OPT_ZORDER 1 for one launch per phase");
@@ -1598,6 +1608,199 @@ extern "C" int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_res
                                    : iterate_typed<double>(g, *opts, r);
     *result = r;   // also on timeout / non-finite, so the caller sees the status
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// shard mode: one rank's slice of the factors of a graph split across GPUs
+// ---------------------------------------------------------------------------
+extern "C" int fga_shard_rho_chain(const fga_graph *g, const double *srho_in, const double *srho2_in,
+                                   double *srho_out, double *srho2_out) {
+    if (!g || !srho_out || !srho2_out) return fail(FGA_EINVAL, "fga_shard_rho_chain: NULL argument");
+    if (!g->finalized) return fail(FGA_ESTATE, "fga_shard_rho_chain: call fga_finalize first");
+    const int64_t Z = g->nz;
+    std::vector<double> r((size_t)Z, 0.0), r2((size_t)Z, 0.0);
+    for (int64_t b = 0; b < Z; ++b) {
+        if (srho_in) r[b] = srho_in[b];
+        if (srho2_in) r2[b] = srho2_in[b];
+    }
+    // this shard's edges in creation order, onto the incoming sums one by one
+    std::vector<int64_t> c2s((size_t)g->ne, -1);
+    for (int64_t s2 = 0; s2 < g->es; ++s2)
+        if (g->s2c[s2] >= 0) c2s[g->s2c[s2]] = s2;
+    for (int64_t c = 0; c < g->ne; ++c) {
+        const int32_t b = g->svar[c2s[c]];
+        const double v = edge_rho_c(g, c);
+        r[b] += v;
+        r2[b] += v * v;
+    }
+    std::memcpy(srho_out, r.data(), (size_t)Z * sizeof(double));
+    std::memcpy(srho2_out, r2.data(), (size_t)Z * sizeof(double));
+    return FGA_OK;
+}
+
+// The z-step's launch shape depends only on the number of variables, never
+// on the shard: every rank then sums the (graph-wide) dual residual in the
+// same order and takes the same stop decision.
+constexpr int kShardZGrid = 1024, kShardZBlock = 256;
+
+template <typename R>
+static int shard_begin_typed(fga_graph *g, const double *srho, const double *srho2) {
+    std::vector<R> v((size_t)g->nz);
+    for (int64_t b = 0; b < g->nz; ++b) v[b] = (R)srho[b];
+    std::vector<double> v2(srho2, srho2 + g->nz);
+    int rc;
+    if ((rc = upload_vec(g->srho, v))) return rc;
+    if ((rc = upload_vec(g->srho2, v2))) return rc;
+    CUDA_TRY(g->shard_res.alloc(kShardZGrid * sizeof(double)));
+    CUDA_TRY(cudaMemset(g->ctl.p, 0, sizeof(Ctl)));
+    return FGA_OK;
+}
+
+extern "C" int fga_shard_begin(fga_graph *g, const double *srho_total, const double *srho2_total) {
+    if (!g || !srho_total || !srho2_total) return fail(FGA_EINVAL, "fga_shard_begin: NULL argument");
+    if (!g->finalized) return fail(FGA_ESTATE, "fga_shard_begin: call fga_finalize first");
+    if (g->zorder != 0 && g->zorder != 1)
+        return fail(FGA_EINVAL, "fga_shard_begin: shards run the canonical or the fast z-order (FGA_OPT_ZORDER 0 "
+                                "or 1), not the disk-tile or hinge-bank kernels");
+    for (int64_t b = 0; b < g->nz; ++b)
+        if (!std::isfinite(srho_total[b]) || srho_total[b] < 0.0 || !std::isfinite(srho2_total[b]))
+            return fail(FGA_EINVAL, "fga_shard_begin: bad graph-wide rho sum at variable %lld", (long long)b);
+    int rc = set_device(g);
+    if (rc) return rc;
+    rc = g->precision == FGA_F32 ? shard_begin_typed<float>(g, srho_total, srho2_total)
+                                 : shard_begin_typed<double>(g, srho_total, srho2_total);
+    if (rc) return rc;
+    g->shard = true;
+    g->shard_pending = false;
+    return FGA_OK;
+}
+
+template <typename R>
+static int shard_xstep_typed(fga_graph *g, int check_prev, const void *s_in, void *s_out, double *pri_out) {
+    SweepArgs<R> a;
+    fill_args(g, a);
+    cudaStream_t s = g->stream;
+    const int mode = !g->shard_pending ? F_PROX : check_prev ? F_U_PROX_CHK : F_U_PROX;
+    CUDA_TRY(sweep_phase_f<R>(a, mode, g->xpar, g->zpar, g->grid, g->blk, g->smem, g->kind, s));
+    if (mode == F_U_PROX_CHK) CUDA_TRY(shard_total<R>(a.res_pri, g->grid, pri_out, s));
+    // the shard touches only some variables: the others pass s_in through
+    if (g->zorder == 1) {
+        if (s_in) CUDA_TRY(cudaMemcpyAsync(s_out, s_in, (size_t)g->nz * sizeof(R), cudaMemcpyDeviceToDevice, s));
+        else CUDA_TRY(cudaMemsetAsync(s_out, 0, (size_t)g->nz * sizeof(R), s));
+    }
+    CUDA_TRY(shard_sums<R>(a, static_cast<const R *>(s_in), static_cast<R *>(s_out), g->grid, g->blk, s));
+    g->shard_pending = false;
+    return FGA_OK;
+}
+
+extern "C" int fga_shard_xstep(fga_graph *g, int32_t check_prev, const void *s_in, void *s_out, double *pri_out) {
+    if (!g || !s_out) return fail(FGA_EINVAL, "fga_shard_xstep: NULL argument");
+    if (!g->shard || !g->initialized) return fail(FGA_ESTATE, "fga_shard_xstep: call fga_shard_begin and fga_init");
+    if (check_prev && (!g->shard_pending || !pri_out))
+        return fail(FGA_EINVAL, "fga_shard_xstep: no pending iteration to check, or NULL pri_out");
+    int rc = set_device(g);
+    if (rc) return rc;
+    return g->precision == FGA_F32 ? shard_xstep_typed<float>(g, check_prev, s_in, s_out, pri_out)
+                                   : shard_xstep_typed<double>(g, check_prev, s_in, s_out, pri_out);
+}
+
+extern "C" int fga_shard_add_parts(fga_graph *g, const void *parts, int32_t n_shards, void *total) {
+    if (!g || !parts || !total || n_shards < 1) return fail(FGA_EINVAL, "fga_shard_add_parts: bad argument");
+    if (!g->shard) return fail(FGA_ESTATE, "fga_shard_add_parts: call fga_shard_begin first");
+    int rc = set_device(g);
+    if (rc) return rc;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (g->nz + 255) / 256));
+    if (g->precision == FGA_F32)
+        CUDA_TRY(shard_add_parts<float>(static_cast<const float *>(parts), n_shards, g->nz, static_cast<float *>(total),
+                                        grid, g->stream));
+    else
+        CUDA_TRY(shard_add_parts<double>(static_cast<const double *>(parts), n_shards, g->nz,
+                                         static_cast<double *>(total), grid, g->stream));
+    return FGA_OK;
+}
+
+template <typename R>
+static int shard_zstep_typed(fga_graph *g, const void *total, int check, double *dual_out) {
+    SweepArgs<R> a;
+    fill_args(g, a);
+    cudaStream_t s = g->stream;
+    const int xp = g->xpar ^ 1;   // the x of the x-step just run
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(kShardZGrid, (g->nz + kShardZBlock - 1) /
+                                                                                  kShardZBlock));
+    a.res_dual = g->shard_res.as<double>();
+    CUDA_TRY(shard_z<R>(a, static_cast<const R *>(total), g->zpar, check, grid, kShardZBlock, s));
+    if (check) CUDA_TRY(shard_total<R>(a.res_dual, grid, dual_out, s));
+    g->xpar = xp;
+    g->zpar ^= 1;
+    g->iters_done += 1;
+    g->shard_pending = true;
+    return FGA_OK;
+}
+
+extern "C" int fga_shard_zstep(fga_graph *g, const void *total, int32_t check, double *dual_out) {
+    if (!g || !total || (check && !dual_out)) return fail(FGA_EINVAL, "fga_shard_zstep: NULL argument");
+    if (!g->shard || !g->initialized) return fail(FGA_ESTATE, "fga_shard_zstep: call fga_shard_begin and fga_init");
+    int rc = set_device(g);
+    if (rc) return rc;
+    return g->precision == FGA_F32 ? shard_zstep_typed<float>(g, total, check, dual_out)
+                                   : shard_zstep_typed<double>(g, total, check, dual_out);
+}
+
+template <typename R>
+static int shard_finish_typed(fga_graph *g, double *pri_out) {
+    SweepArgs<R> a;
+    fill_args(g, a);
+    CUDA_TRY(sweep_phase_f<R>(a, F_U_ONLY, g->xpar, g->zpar, g->grid, g->blk, g->smem, g->kind, g->stream));
+    CUDA_TRY(shard_total<R>(a.res_pri, g->grid, pri_out, g->stream));
+    g->shard_pending = false;
+    return FGA_OK;
+}
+
+extern "C" int fga_shard_finish(fga_graph *g, double *pri_out) {
+    if (!g || !pri_out) return fail(FGA_EINVAL, "fga_shard_finish: NULL argument");
+    if (!g->shard || !g->initialized) return fail(FGA_ESTATE, "fga_shard_finish: call fga_shard_begin and fga_init");
+    if (!g->shard_pending) return fail(FGA_ESTATE, "fga_shard_finish: no pending u-update");
+    int rc = set_device(g);
+    if (rc) return rc;
+    return g->precision == FGA_F32 ? shard_finish_typed<float>(g, pri_out) : shard_finish_typed<double>(g, pri_out);
+}
+
+extern "C" int fga_shard_stop_rule(const double *pri_parts, int32_t n_shards, double dual, int64_t num_edges,
+                                   double tol_pri, double tol_dual, double *r_pri, double *r_dual, int32_t *stop) {
+    if (!pri_parts || n_shards < 1 || num_edges < 0 || !r_pri || !r_dual || !stop)
+        return fail(FGA_EINVAL, "fga_shard_stop_rule: bad argument");
+    double sp = 0.0;
+    for (int32_t r = 0; r < n_shards; ++r) sp += pri_parts[r];   // rank order
+    const double E = num_edges > 0 ? (double)num_edges : 1.0;
+    *r_pri = std::sqrt(sp / E);
+    *r_dual = std::sqrt(dual / E);
+    const bool finite = std::isfinite(*r_pri) && std::isfinite(*r_dual);
+    *stop = !finite || (*r_pri <= tol_pri && *r_dual <= tol_dual);
+    return FGA_OK;
+}
+
+extern "C" int fga_latency_floor(fga_graph *g, int64_t iters, int32_t mode, float *ms) {
+    if (!g || !ms || iters < 1 || (mode != 0 && mode != 1)) return fail(FGA_EINVAL, "fga_latency_floor: bad argument");
+    if (!g->finalized) return fail(FGA_ESTATE, "fga_latency_floor: call fga_finalize first");
+    if (g->zorder != 2) return fail(FGA_EINVAL, "fga_latency_floor: the disk-tile order only");
+    int rc = set_device(g);
+    if (rc) return rc;
+    TileArgs a;
+    fill_tile_args(g, a);
+    a.timeout_ns = 2000000000LL;
+    cudaStream_t s = g->stream;
+    CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
+    CUDA_TRY(cudaEventRecord(g->ev0, s));
+    CUDA_TRY(tile_floor_launch(a, iters, mode, g->blk, g->smem, s));
+    CUDA_TRY(cudaEventRecord(g->ev1, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, g->ev0, g->ev1));
+    TileSync b;
+    CUDA_TRY(cudaMemcpy(&b, g->bar.p, sizeof b, cudaMemcpyDeviceToHost));
+    if (b.error) return fail(b.error, "fga_latency_floor: a grid-wide wait timed out");
+    *ms = t;
+    return FGA_OK;
 }
 
 extern "C" int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n) {

@@ -190,5 +190,16 @@ cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int
                         int grid_partials, cudaStream_t s);
 template <typename R>
 int sweep_max_blocks_per_sm(int block, int smem, int kind);
+// shard mode: this shard's running rho m sums, the rank-ordered sum of G
+// shards' own sums, z from graph-wide sums (+ dual partials), and one FP64
+// total of per-CTA partials
+template <typename R>
+cudaError_t shard_sums(const SweepArgs<R> &a, const R *s_in, R *s_out, int grid, int block, cudaStream_t s);
+template <typename R>
+cudaError_t shard_add_parts(const R *parts, int G, long long nz, R *total, int grid, cudaStream_t s);
+template <typename R>
+cudaError_t shard_z(const SweepArgs<R> &a, const R *total, int zp, int chk, int grid, int block, cudaStream_t s);
+template <typename R>
+cudaError_t shard_total(const double *part, int n, double *out, cudaStream_t s);
 
 }  // namespace fga

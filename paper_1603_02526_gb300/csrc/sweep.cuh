@@ -980,10 +980,31 @@ __device__ __forceinline__ void z_store(const SweepArgs<R> &a, int b, R S, const
     }
 }
 
-template <typename R, bool CHK>
-__device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *zn, double &dual) {
+// Shard mode (SHARD = true): instead of z, phase Z writes this shard's
+// running sums of rho m, s_out[b] = s_in[b] + (the shard's terms of b).  In
+// the canonical order the shard's terms are added one by one onto s_in[b]
+// (so shards taken in creation order reproduce the serial sum exactly); in
+// the fast order the shard's own sum is added to s_in[b] once.  s_in may
+// be null (start from zero).
+template <typename R, bool SHARD>
+__device__ __forceinline__ R shard_start(const R *s_in, long long b) {
+    if constexpr (SHARD) return s_in ? s_in[b] : R(0);
+    return R(0);
+}
+
+template <typename R, bool CHK, bool SHARD = false>
+__device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *zn, double &dual,
+                                        const R *s_in = nullptr, R *s_out = nullptr) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
+    auto finish = [&](int b, R S) {
+        if constexpr (SHARD) s_out[b] = S;
+        else z_store<R, CHK>(a, b, S, zo, zn, dual);
+    };
+    auto finish_sum = [&](int b, R S) {   // fast order: one sum per shard
+        if constexpr (SHARD) s_out[b] = s_in ? s_in[b] + S : S;
+        else z_store<R, CHK>(a, b, S, zo, zn, dual);
+    };
     if (a.zorder == 0) {
         // canonical.  Rows of at most kZShort values: one thread per
         // variable over the whole grid, its values added one by one in
@@ -991,9 +1012,9 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         for (long long b = gtid; b < a.nz; b += gstride) {
             const int k0 = a.row[b], k1 = a.row[b + 1];
             if (k1 - k0 > kZShort) continue;
-            R S = R(0);
+            R S = shard_start<R, SHARD>(s_in, b);
             for (int k = k0; k < k1; ++k) S += ldg_l2(a.pvm + k);
-            z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
+            finish((int)b, S);
         }
         // Longer rows: warp 0 of a CTA takes 32 consecutive variables, one
         // per lane; the warp copies 32 values of each of the 32 rows at a
@@ -1015,7 +1036,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
                 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
                 const int nch = (maxlen + 31) / 32;
-                R S = R(0);
+                R S = valid ? shard_start<R, SHARD>(s_in, b) : R(0);
                 auto issue = [&](int c) {
                     R *buf = zbuf + (c & 1) * 32 * kZRow;
                     #pragma unroll 4
@@ -1040,7 +1061,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
                     for (int t = 0; t < n; ++t) S += row[t];
                     __syncwarp();
                 }
-                if (valid) z_store<R, CHK>(a, (int)b, S, zo, zn, dual);
+                if (valid) finish((int)b, S);
             }
         }
         return;
@@ -1053,7 +1074,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         const int b = a.small_vars[i];
         R S = R(0);
         for (int k = row[b]; k < row[b + 1]; ++k) S += ldg_l2(src + k);
-        z_store<R, CHK>(a, b, S, zo, zn, dual);
+        finish_sum(b, S);
     }
     // ... the others one warp per item (a whole row, or one piece of a hub
     // row whose pieces are combined in piece order by the last warp done).
@@ -1066,7 +1087,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
         if (wi.w < 0) {
-            if (lane == 0) z_store<R, CHK>(a, wi.x, S, zo, zn, dual);
+            if (lane == 0) finish_sum(wi.x, S);
             continue;
         }
         const int h = wi.w;
@@ -1087,7 +1108,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
             for (int o = 16; o > 0; o >>= 1) T += __shfl_xor_sync(0xffffffffu, T, o);
             if (lane == 0) {
                 a.hub_ticket[h] = 0u;
-                z_store<R, CHK>(a, wi.x, T, zo, zn, dual);
+                finish_sum(wi.x, T);
             }
         }
     }
@@ -1246,6 +1267,50 @@ __global__ void __launch_bounds__(32) k_check(const SweepArgs<R> a, long long it
     if (*(volatile int *)&a.ctl->done) return;
     const CheckOut c = residual_check(a, nparts, (int)(it_checked & 1));
     if (c.stop || final_check) write_ctl(a, it_checked, c, xp, zp, final_check != 0 && !c.stop);
+}
+
+// ---------------------------------------------------------------------------
+// shard mode (the graph holds a contiguous slice of the factors; z needs the
+// rho m sums of every shard): phase F as above, then these kernels.
+// ---------------------------------------------------------------------------
+// This shard's running sums s_out = s_in + its terms (see phase_z).
+template <typename R>
+__global__ void __launch_bounds__(256) k_shard_sums(const SweepArgs<R> a, const R *s_in, R *s_out) {
+    double unused = 0.0;
+    phase_z<R, false, true>(a, nullptr, nullptr, unused, s_in, s_out);
+}
+
+// Rank-ordered sum of G shards' own sums: total[b] = ((p_0 + p_1) + p_2) ...
+template <typename R>
+__global__ void __launch_bounds__(256) k_shard_add_parts(const R *parts, int G, long long nz, R *total) {
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nz;
+         b += (long long)gridDim.x * blockDim.x) {
+        R S = parts[b];
+        for (int r = 1; r < G; ++r) S += parts[(long long)r * nz + b];
+        total[b] = S;
+    }
+}
+
+// z from the graph-wide sums (the graph's srho / srho2 hold the totals of
+// every shard); with CHK the dual residual's per-CTA partial sums.
+template <typename R, bool CHK>
+__global__ void __launch_bounds__(256) k_shard_z(const SweepArgs<R> a, const R *total, int zp) {
+    double dual = 0.0;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < a.nz;
+         b += (long long)gridDim.x * blockDim.x)
+        z_store<R, CHK>(a, (int)b, total[b], a.z[zp], a.z[zp ^ 1], dual);
+    if constexpr (CHK) {
+        const double s = block_sum(dual);
+        if (threadIdx.x == 0) a.res_dual[blockIdx.x] = s;
+    }
+}
+
+// n per-CTA partials added into one FP64 value by a fixed shuffle tree
+// (deterministic); one warp.
+template <typename R>
+__global__ void __launch_bounds__(32) k_shard_total(const double *part, int n, double *out) {
+    const double s = warp_sum_partials(part, n);
+    if (threadIdx.x == 0) *out = s;
 }
 
 }  // namespace fga

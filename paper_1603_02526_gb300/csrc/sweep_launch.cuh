@@ -87,6 +87,31 @@ cudaError_t sweep_check(const SweepArgs<R> &a, long long it_checked, int xp, int
 }
 
 template <typename R>
+cudaError_t shard_sums(const SweepArgs<R> &a, const R *s_in, R *s_out, int grid, int block, cudaStream_t s) {
+    k_shard_sums<R><<<grid, block, a.zorder == 0 ? canonical_z_smem((int)sizeof(R)) : 0, s>>>(a, s_in, s_out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t shard_add_parts(const R *parts, int G, long long nz, R *total, int grid, cudaStream_t s) {
+    k_shard_add_parts<R><<<grid, 256, 0, s>>>(parts, G, nz, total);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t shard_z(const SweepArgs<R> &a, const R *total, int zp, int chk, int grid, int block, cudaStream_t s) {
+    if (chk) k_shard_z<R, true><<<grid, block, 0, s>>>(a, total, zp);
+    else k_shard_z<R, false><<<grid, block, 0, s>>>(a, total, zp);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t shard_total(const double *part, int n, double *out, cudaStream_t s) {
+    k_shard_total<R><<<1, 32, 0, s>>>(part, n, out);
+    return cudaGetLastError();
+}
+
+template <typename R>
 int sweep_max_blocks_per_sm(int block, int smem, int kind) {
     if (allow_smem<R>(smem, kind) != cudaSuccess) return 0;
     int n = 0;
