@@ -81,6 +81,7 @@ def _declare(lib):
         "fga_iterate": [P, ctypes.POINTER(fga_iter_opts), ctypes.POINTER(fga_iter_result)],
         "fga_residuals": [P, pdbl, pdbl],
         "fga_launch_info": [P, pi64, i32],
+        "fga_latency_floor": [P, i64, i32, ctypes.POINTER(ctypes.c_float)],
         "fga_read_z": [P, P, i64],
         "fga_read_edge_state": [P, i32, P, i64],
         "fga_destroy": [P],

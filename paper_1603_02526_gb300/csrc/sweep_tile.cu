@@ -743,6 +743,49 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     }
 }
 
+// ---------------------------------------------------------------------------
+// Latency floor of one pass on the same grid (a measurement, not part of a
+// solve).  MODE 0: the grid-wide barrier alone.  MODE 1: what a pass costs
+// besides the operators -- every CTA reads its variables' accumulators (the
+// z gather's L2 loads), adds one fixed-point value per variable (the partial
+// sums' reductions; the value added is 0, so no accumulator changes), and
+// the barrier.  The graph's state is not touched.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_floor(const TileArgs a, long long iters) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const TileSmem L = tile_smem_layout(a.smax, a.svmax, a.locmax, a.clmax, a.stgmax);
+    int4 *sv = reinterpret_cast<int4 *>(tsm + L.sv);
+    float *zt = reinterpret_cast<float *>(tsm + L.z4);
+    const TileCta C = a.cta[blockIdx.x];
+    for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) {
+        sv[i] = a.sv[C.sv0 + i];
+        zt[i] = 0.f;
+    }
+    __syncthreads();
+    const unsigned long long G = (unsigned long long)a.G;
+    for (long long it = 1; it <= iters; ++it) {
+        if (MODE == 1) {
+            const long long *src = a.acc + (size_t)((it + 2) % 3) * a.ptot;
+            for (int i = threadIdx.x; i < C.nsv; i += blockDim.x)
+                zt[i] += __fmul_rn(__ll2float_rn(__ldcg(src + sv[i].x)), kTileFixInv);
+            __syncthreads();
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.acc + (size_t)(it % 3) * a.ptot);
+            for (int i = threadIdx.x; i < C.nsv; i += blockDim.x)
+                red_add_u64(dst + sv[i].x, zt[i] == 12345.f ? 1ull : 0ull);   // adds 0 (never 1)
+        }
+        if (!tile_barrier(a.sync, G * (unsigned long long)it, a.timeout_ns, false)) return;
+    }
+}
+
+cudaError_t tile_floor_launch(const TileArgs &a, long long iters, int mode, int block, int smem, cudaStream_t s) {
+    const void *fn = mode == 0 ? (const void *)k_tile_floor<0> : (const void *)k_tile_floor<1>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&a, (void *)&iters};
+    return cudaLaunchCooperativeKernel(fn, dim3(a.G), dim3(block), args, (size_t)smem, s);
+}
+
 static const void *tile_kernel(bool a1) {
     return a1 ? (const void *)k_tile_sweep<true> : (const void *)k_tile_sweep<false>;
 }

@@ -194,6 +194,9 @@ int tile_plan(const TileInput &in, TilePlan &P, std::string &why);
 
 // Kernel launch (sweep_tile.cu) and the warps per CTA it can run with.
 cudaError_t tile_sweep_launch(const TileArgs &a, int block, int smem, cudaStream_t s);
+// The latency floor of a pass on the same grid (mode 0: barrier; 1: gather
+// loads, accumulator reductions and barrier), `iters` passes.
+cudaError_t tile_floor_launch(const TileArgs &a, long long iters, int mode, int block, int smem, cudaStream_t s);
 int tile_max_warps();
 int tile_smem_bytes(const TilePlan &P);
 

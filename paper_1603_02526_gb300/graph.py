@@ -136,6 +136,12 @@ class FactorGraph:
         return dict(grid=info[0], block=info[1], smem=info[2], blocks_per_sm=info[3], chunks=info[4],
                     buckets=info[5], zorder=info[6])
 
+    def fga_latency_floor(self, iters, mode=1):
+        """Device ms of `iters` operator-free passes on the disk-tile grid."""
+        ms = ctypes.c_float()
+        check(self._lib.fga_latency_floor(self._g, int(iters), int(mode), ctypes.byref(ms)), "fga_latency_floor")
+        return ms.value
+
     def fga_residuals(self):
         a, b = ctypes.c_double(), ctypes.c_double()
         check(self._lib.fga_residuals(self._g, ctypes.byref(a), ctypes.byref(b)), "fga_residuals")
