@@ -101,7 +101,14 @@ typedef struct og_graph {
     int finalized;
     int64_t iters_done;
     double last_rpri, last_rdual;
+    /* weight mode: 0 = fixed rho (Algorithm 2 as printed); 1 = three weights
+     * (each x-update gives each edge a weight class, see twa_classes) */
+    int weights;
+    int8_t *cls;         /* [ne] weight class of each edge's last message     */
 } og_graph;
+
+/* Weight classes of a message (three-weight reading, see og_set_weights). */
+enum { OW_ZERO = 0, OW_STD = 1, OW_INF = 2 };
 
 static int grow(void **p, int64_t *cap, int64_t need, size_t elem)
 {
@@ -127,7 +134,7 @@ void og_free(og_graph *g)
     free(g->vdim); free(g->voff); free(g->fac); free(g->fvars); free(g->params);
     free(g->ez); free(g->rho); free(g->alpha);
     free(g->x); free(g->m); free(g->u); free(g->n); free(g->z); free(g->zprev);
-    free(g->row); free(g->col);
+    free(g->row); free(g->col); free(g->cls);
     free(g);
 }
 
@@ -254,9 +261,11 @@ int og_finalize(og_graph *g)
     g->zprev = (double *)calloc((size_t)(Z ? Z : 1), sizeof(double));
     g->row = (int64_t *)calloc((size_t)Z + 1, sizeof(int64_t));
     g->col = (int64_t *)malloc(sizeof(int64_t) * (size_t)(E ? E : 1));
+    g->cls = (int8_t *)malloc((size_t)(E ? E : 1));
     if (!g->ez || !g->rho || !g->alpha || !g->x || !g->m || !g->u || !g->n || !g->z ||
-        !g->zprev || !g->row || !g->col)
+        !g->zprev || !g->row || !g->col || !g->cls)
         return OR_ENOMEM;
+    for (int64_t e = 0; e < E; ++e) g->cls[e] = OW_STD;
     for (int64_t a = 0; a < g->nfac; ++a) {
         const ofactor *f = &g->fac[a];
         int64_t e = f->edge0;
@@ -292,6 +301,30 @@ int og_set_rho_alpha(og_graph *g, const double *rho, const double *alpha, double
         g->rho[e] = r;
         g->alpha[e] = a;
     }
+    return OR_OK;
+}
+
+/* Weight mode.  The paper keeps rho and alpha fixed per edge and notes that
+ * improved update schemes exist which its framework can run (Sec. II, the
+ * three-weight algorithm of Derbinsky et al.); it states none.  Reading
+ * (mode 1, "three weights"): each x-update gives each of the factor's edges
+ * a weight class --
+ *   infinite: the factor fixes the value whatever it receives (FIX);
+ *   zero: a constraint-type factor (disk pair, wall, box, hinge, margin)
+ *         whose proximal step left that edge's message unchanged (the
+ *         constraint does not act on it: no opinion);
+ *   standard: every other edge;
+ * the z-update averages only the infinite-weight messages m if there are
+ * any, else the standard ones with weights rho, else (all zero) all of them
+ * as in mode 0; and the u-update sets u = 0 on an edge of zero or infinite
+ * weight (a fixed value's scaled dual, and an inactive constraint's, are
+ * zero) and runs u += alpha (x - z) on the others. */
+int og_set_weights(og_graph *g, int32_t mode)
+{
+    if (!g->finalized) return OR_ESTATE;
+    if (mode != 0 && mode != 1) return OR_EINVAL;
+    g->weights = mode;
+    for (int64_t e = 0; e < g->ne; ++e) g->cls[e] = OW_STD;
     return OR_OK;
 }
 
@@ -608,6 +641,22 @@ static int factor_prox(og_graph *g, const ofactor *f)
 /* Runs Algorithm 2 until max_iters iterations have been done in this call
  * or the residuals of a checked iteration are both within tolerance.
  * Returns the number of iterations done and the last residuals (RMS). */
+/* Weight classes of factor f's edges after its x-update (mode 1). */
+static void twa_classes(og_graph *g, const ofactor *f)
+{
+    for (int32_t k = 0; k < f->arity; ++k) {
+        const int64_t e = f->edge0 + k;
+        int8_t c = OW_STD;
+        if (f->type == OT_FIX) {
+            c = OW_INF;
+        } else if (f->type == OT_PACK_PAIR || f->type == OT_PACK_WALL || f->type == OT_MPC_BOX ||
+                   f->type == OT_SVM_HINGE || f->type == OT_SVM_MARGIN) {
+            if (g->x[e] == g->n[e]) c = OW_ZERO;
+        }
+        g->cls[e] = c;
+    }
+}
+
 int og_iterate(og_graph *g, int64_t max_iters, double tol_pri, double tol_dual,
                int32_t check_every, int64_t *iters_out, double *rpri_out, double *rdual_out)
 {
@@ -622,22 +671,54 @@ int og_iterate(og_graph *g, int64_t max_iters, double tol_pri, double tol_dual,
         for (int64_t a = 0; a < g->nfac; ++a) {
             int rc = factor_prox(g, &g->fac[a]);
             if (rc != OR_OK) return rc;
+            if (g->weights) twa_classes(g, &g->fac[a]);
         }
         /* m-update */
         for (int64_t e = 0; e < E; ++e) g->m[e] = g->x[e] + g->u[e];
         /* z-update: rho-weighted average over each variable's edges */
-        for (int64_t b = 0; b < Z; ++b) {
-            double S = 0.0, R = 0.0;
-            for (int64_t k = g->row[b]; k < g->row[b + 1]; ++k) {
-                int64_t e = g->col[k];
-                S += g->rho[e] * g->m[e];
-                R += g->rho[e];
+        if (!g->weights) {
+            for (int64_t b = 0; b < Z; ++b) {
+                double S = 0.0, R = 0.0;
+                for (int64_t k = g->row[b]; k < g->row[b + 1]; ++k) {
+                    int64_t e = g->col[k];
+                    S += g->rho[e] * g->m[e];
+                    R += g->rho[e];
+                }
+                g->zprev[b] = g->z[b];
+                if (R > 0.0) g->z[b] = S / R; /* a variable with no edge keeps z */
             }
-            g->zprev[b] = g->z[b];
-            if (R > 0.0) g->z[b] = S / R; /* a variable with no edge keeps z */
+        } else {
+            /* three weights: infinite-weight messages first, then standard
+             * ones, then all of them (each sum in ascending edge order) */
+            for (int64_t b = 0; b < Z; ++b) {
+                double S = 0.0, R = 0.0, Ss = 0.0, Rs = 0.0, Si = 0.0, Ni = 0.0;
+                for (int64_t k = g->row[b]; k < g->row[b + 1]; ++k) {
+                    int64_t e = g->col[k];
+                    if (g->cls[e] == OW_INF) {
+                        Si += g->m[e];
+                        Ni += 1.0;
+                    } else {
+                        S += g->rho[e] * g->m[e];
+                        R += g->rho[e];
+                        if (g->cls[e] == OW_STD) {
+                            Ss += g->rho[e] * g->m[e];
+                            Rs += g->rho[e];
+                        }
+                    }
+                }
+                g->zprev[b] = g->z[b];
+                if (Ni > 0.0) g->z[b] = Si / Ni;
+                else if (Rs > 0.0) g->z[b] = Ss / Rs;
+                else if (R > 0.0) g->z[b] = S / R;
+            }
         }
         /* u-update */
-        for (int64_t e = 0; e < E; ++e) g->u[e] = g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]);
+        if (!g->weights) {
+            for (int64_t e = 0; e < E; ++e) g->u[e] = g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]);
+        } else {
+            for (int64_t e = 0; e < E; ++e)
+                g->u[e] = g->cls[e] == OW_STD ? g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]) : 0.0;
+        }
         /* n-update */
         for (int64_t e = 0; e < E; ++e) g->n[e] = g->z[g->ez[e]] - g->u[e];
         ++it;

@@ -121,6 +121,7 @@ def _declare(lib):
     lib.og_get_z.argtypes = [P, dp]
     lib.og_get_edge_var.argtypes = [P, lp]
     lib.og_prox.argtypes = [i32, i32, ip, dp, dp, dp, dp]
+    lib.og_set_weights.argtypes = [P, i32]
     return lib
 
 
@@ -214,6 +215,14 @@ class OracleGraph:
         if rc != 0:
             raise ValueError("oracle: bad rho/alpha")
 
+    def set_weights(self, mode):
+        """0: fixed rho per edge (Algorithm 2 as printed); 1: three weights
+        (weight classes zero / standard / infinite set by each x-update;
+        see og_set_weights in fga_oracle.c)."""
+        rc = self._lib.og_set_weights(self._g, int(mode))
+        if rc != 0:
+            raise ValueError("oracle: bad weight mode")
+
     @property
     def num_edges(self):
         return int(self._lib.og_num_edges(self._g))
@@ -262,14 +271,17 @@ class OracleGraph:
         return out
 
 
-def from_problem(problem, z0=True):
+def from_problem(problem, z0=True, weights=0):
     """Loads a problem description (variable blocks, factor blocks, rho,
-    alpha, start point) into a fresh oracle graph and initialises it."""
+    alpha, start point) into a fresh oracle graph and initialises it;
+    weights: the weight mode (set_weights)."""
     g = OracleGraph()
     for count, dim in problem.var_blocks:
         g.add_variables(count, dim)
     for blk in problem.factor_blocks:
         g.add_factors(blk.ftype, blk.var_ids, blk.params)
     g.finalize(problem.rho, problem.alpha)
+    if weights:
+        g.set_weights(weights)
     g.init(problem.z0 if z0 else None)
     return g

@@ -8,6 +8,7 @@ import pytest
 from oracle import oracle as orc
 from tests import test_oracle_alg as alg
 from tests import test_oracle_prox as prox
+from tests import test_oracle_twa as twa
 
 # (name, exact source text, replacement, pins that must catch it)
 MUTANTS = [
@@ -24,7 +25,10 @@ MUTANTS = [
      "if (gam > c) gam = c;", "",
      [(prox.test_svm_hinge_matches_bruteforce, dict(seed=s)) for s in range(10)]),
     ("z-update without the rho weights",
-     "S += g->rho[e] * g->m[e];", "S += g->m[e];",
+     "double S = 0.0, R = 0.0;\n                for (int64_t k = g->row[b]; k < g->row[b + 1]; ++k) {\n"
+     "                    int64_t e = g->col[k];\n                    S += g->rho[e] * g->m[e];",
+     "double S = 0.0, R = 0.0;\n                for (int64_t k = g->row[b]; k < g->row[b + 1]; ++k) {\n"
+     "                    int64_t e = g->col[k];\n                    S += g->m[e];",
      [(alg.test_alg1_equals_alg2_scalar_consensus, {}), (alg.test_alg1_equals_alg2_mpc_without_box, {})]),
     ("u-update with the wrong sign",
      "g->u[e] = g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]);",
@@ -46,9 +50,19 @@ MUTANTS = [
      [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {}),
       (alg.test_weighted_dual_sum_decays_by_one_minus_alpha, {})]),
     ("z-update as an unweighted mean",
-     "S += g->rho[e] * g->m[e];\n                R += g->rho[e];",
-     "S += g->m[e];\n                R += 1.0;",
+     "S += g->rho[e] * g->m[e];\n                    R += g->rho[e];\n                }",
+     "S += g->m[e];\n                    R += 1.0;\n                }",
      [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {})]),
+    ("three weights: infinite weight treated as standard",
+     "if (g->cls[e] == OW_INF) {", "if (0) {",
+     [(twa.test_infinite_weight_decides_z, {})]),
+    ("three weights: zero-weight messages averaged",
+     "if (g->cls[e] == OW_STD) {\n                            Ss", "if (1) {\n                            Ss",
+     [(twa.test_inactive_box_by_hand, {})]),
+    ("three weights: u not reset on non-standard edges",
+     "g->cls[e] == OW_STD ? g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]) : 0.0",
+     "g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]])",
+     [(twa.test_inactive_box_by_hand, {}), (twa.test_infinite_weight_decides_z, {})]),
 ]
 
 
