@@ -123,7 +123,22 @@ extern "C" {
 #define FGA_OPT_STORE_M 1     /* 1 = keep m per edge so FGA_EDGE_M can be read
                                  back (default 1 for FGA_F64, 0 for FGA_F32)  */
 #define FGA_OPT_BLOCK 2       /* threads per CTA of the sweep (0 = library
-                                 choice; 64..1024, multiple of 32)           */
+                                 choice; 64..256, multiple of 32)            */
+#define FGA_OPT_WEIGHTS 3     /* 0 = rho fixed per edge (Algorithm 2 as
+                                 printed); 1 = three weights: each x-update
+                                 gives every edge a weight class -- infinite
+                                 for FGA_FIX, zero on an edge of a disk
+                                 pair, wall, box, hinge or margin factor
+                                 whose x equals its n (the constraint does
+                                 not act on it), standard otherwise; z is
+                                 the mean of the infinite-weight messages m
+                                 if any, else the rho-weighted mean of the
+                                 standard ones, else of all; u is reset to 0
+                                 on zero- and infinite-weight edges.  The
+                                 paper allows such improved rho schemes
+                                 (Sec. II) without stating one; this is the
+                                 library's reading.  Canonical z-order only
+                                 (FGA_OPT_ZORDER 0, the default with it).   */
 
 typedef struct fga_graph fga_graph; /* opaque, library-owned */
 
@@ -419,7 +434,7 @@ typedef struct {
     int64_t max_iters;          /* budget per instance                      */
     double tol_pri, tol_dual;   /* RMS residual tolerances per instance     */
     int32_t check_every;        /* 0 = autotuned value (default 1)          */
-    int32_t threads;            /* CTA size 64/128/256/512; 0 = autotuned (128) */
+    int32_t threads;            /* CTA size 64/128/224/256/448/512; 0 = autotuned (128) */
     int32_t use_graph;          /* 1 = launch from a cached CUDA graph      */
     int32_t reserved;
 } fga_mpc_opts;
@@ -447,7 +462,7 @@ int fga_mpc_batch_read(fga_mpc_batch *b, double *z, double *u, int64_t *iters, i
  * horizon, [4] tuned CTA size, [5] tuned check interval.  n >= 6. */
 int fga_mpc_batch_info(const fga_mpc_batch *b, int64_t *info, int32_t n);
 
-/* Autotuner: times CTA sizes {64,128,256,512} x check intervals {1,2,5,10} on
+/* Autotuner: times CTA sizes {64,128,224,256,448,512} x check intervals {1,2,5,10} on
  * the batch from its current start point (which it restores) and keeps the
  * fastest for later solves.  cache_path (may be NULL): a text file of
  * previous results keyed by GPU, precision and problem shape; a hit skips

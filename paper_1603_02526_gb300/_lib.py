@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "FGA_OK", -1: "FGA_EINVAL", -2: "FGA_ENOMEM", -3: "FGA_ECUDA"
 FGA_F32 = 0
 FGA_F64 = 1
 FGA_EDGE_X, FGA_EDGE_M, FGA_EDGE_U, FGA_EDGE_N = 0, 1, 2, 3
-FGA_OPT_ZORDER, FGA_OPT_STORE_M, FGA_OPT_BLOCK = 0, 1, 2
+FGA_OPT_ZORDER, FGA_OPT_STORE_M, FGA_OPT_BLOCK, FGA_OPT_WEIGHTS = 0, 1, 2, 3
 
 
 class FgaError(RuntimeError):

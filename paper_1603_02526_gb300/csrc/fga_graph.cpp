@@ -157,6 +157,9 @@ struct fga_graph {
     // shard mode (fga_shard_*): srho / srho2 hold the graph-wide sums; the
     // u-update of the last z-step is pending until the next x-step
     bool shard = false, shard_pending = false;
+    // weight mode (FGA_OPT_WEIGHTS): 1 = three weights (canonical order)
+    int weights = 0;
+    DevBuf wcls, pwcls, prho;
     DevBuf shard_res;   // per-CTA dual partials of the z-step (fixed grid: equal on every rank)
 
     // state
@@ -249,6 +252,10 @@ extern "C" int fga_set_option(fga_graph *g, int32_t option, int64_t value) {
         return FGA_OK;
     case FGA_OPT_STORE_M:
         g->store_m = value ? 1 : 0;
+        return FGA_OK;
+    case FGA_OPT_WEIGHTS:
+        if (value != 0 && value != 1) return fail(FGA_EINVAL, "FGA_OPT_WEIGHTS must be 0 or 1");
+        g->weights = (int)value;
         return FGA_OK;
     case FGA_OPT_BLOCK:
         if (value != 0 && (value < 64 || value > 256 || value % 32))
@@ -489,6 +496,16 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         if ((rc = upload_vec(g->row, rowp))) return rc;
         CUDA_TRY(g->pvm.alloc(eb));
         CUDA_TRY(cudaMemset(g->pvm.p, 0, eb));
+        if (g->weights) {
+            CUDA_TRY(g->wcls.alloc((size_t)std::max<int64_t>(ES, 1)));
+            CUDA_TRY(g->pwcls.alloc((size_t)std::max<int64_t>(g->ne, 1)));
+            if (!g->uniform_rho) {
+                std::vector<R> pr((size_t)std::max<int64_t>(g->ne, 1), R(1));
+                for (int64_t s2 = 0; s2 < ES; ++s2)
+                    if (g->s2c[s2] >= 0) pr[pos[s2]] = (R)g->rho_c[g->s2c[s2]];
+                if ((rc = upload_vec(g->prho, pr))) return rc;
+            }
+        }
     } else {
         if ((rc = upload_vec(g->chunks, fl.chunks))) return rc;
         if ((rc = upload_vec(g->slot_var, fl.slot_var))) return rc;
@@ -898,6 +915,11 @@ extern "C" int fga_finalize(fga_graph *g) {
     if (g->finalized) return fail(FGA_ESTATE, "fga_finalize: graph already finalized");
     int rc = set_device(g);
     if (rc) return rc;
+    if (g->weights) {
+        // three weights run in the canonical order
+        if (g->zorder > 0) return fail(FGA_EINVAL, "fga_finalize: FGA_OPT_WEIGHTS 1 needs FGA_OPT_ZORDER 0");
+        g->zorder = 0;
+    }
     const int zreq = g->zorder;   // -1: library choice
     if (zreq == 2 && g->precision != FGA_F32)
         return fail(FGA_EINVAL, "fga_finalize: FGA_OPT_ZORDER 2 (disk tiles) needs FGA_F32");
@@ -1216,6 +1238,10 @@ static int init_typed(fga_graph *g, const std::vector<double> &z0, const std::ve
         CUDA_TRY(cudaMemsetAsync(g->x[0].p, 0, (size_t)g->es * sizeof(R), st));
         if (g->store_m) CUDA_TRY(cudaMemsetAsync(g->m[0].p, 0, (size_t)g->es * sizeof(R), st));
     }
+    if (g->weights) {   // every message starts with standard weight
+        CUDA_TRY(cudaMemsetAsync(g->wcls.p, 1, g->wcls.bytes, st));
+        CUDA_TRY(cudaMemsetAsync(g->pwcls.p, 1, g->pwcls.bytes, st));
+    }
     CUDA_TRY(cudaStreamSynchronize(st));
     return FGA_OK;
 }
@@ -1308,6 +1334,9 @@ static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
     a.hub_off = g->hub_off.as<int>();
     a.hub_part = g->hub_part.as<R>();
     a.hub_ticket = g->hub_ticket.as<unsigned int>();
+    a.wcls = g->weights ? g->wcls.as<unsigned char>() : nullptr;
+    a.pwcls = g->weights ? g->pwcls.as<unsigned char>() : nullptr;
+    a.prho = g->weights && !g->uniform_rho ? g->prho.as<R>() : nullptr;
     a.res_pri = g->res_pri.as<double>();
     a.res_dual = g->res_dual.as<double>();
     a.gmax = g->grid;
@@ -1662,6 +1691,7 @@ extern "C" int fga_shard_begin(fga_graph *g, const double *srho_total, const dou
     if (g->zorder != 0 && g->zorder != 1)
         return fail(FGA_EINVAL, "fga_shard_begin: shards run the canonical or the fast z-order (FGA_OPT_ZORDER 0 "
                                 "or 1), not the disk-tile or hinge-bank kernels");
+    if (g->weights) return fail(FGA_EINVAL, "fga_shard_begin: shards run fixed weights (FGA_OPT_WEIGHTS 0)");
     for (int64_t b = 0; b < g->nz; ++b)
         if (!std::isfinite(srho_total[b]) || srho_total[b] < 0.0 || !std::isfinite(srho2_total[b]))
             return fail(FGA_EINVAL, "fga_shard_begin: bad graph-wide rho sum at variable %lld", (long long)b);

@@ -158,6 +158,14 @@ struct SweepArgs {
     R *hub_part;
     unsigned int *hub_ticket;
 
+    // three-weight mode (canonical order only; null otherwise): weight
+    // class of each edge's last message (0 zero, 1 standard, 2 infinite) in
+    // storage order and at the edge's variable-major position, and rho at
+    // the variable-major position (null: uniform rho_u)
+    unsigned char *wcls;
+    unsigned char *pwcls;
+    const R *prho;
+
     // residual partial sums, one per CTA
     double *res_pri;      // [gmax]
     double *res_dual;     // [2][gmax]

@@ -340,9 +340,38 @@ __device__ __forceinline__ R update_un(const SweepArgs<R> &a, const EdgeIO<R> &i
             const double dd = (double)xo - (double)z;
             pri += dd * dd;
         }
-        u = u + al * d;
+        // three weights: an edge whose last message had zero or infinite
+        // weight restarts from u = 0
+        u = (a.wcls && a.wcls[e] != 1) ? R(0) : u + al * d;
     }
     return z - u;
+}
+
+// Three-weight mode: the weight class of the messages an item just sent,
+// read back by the thread that wrote them -- infinite for FIX (its rho m
+// slot then holds m itself), zero on an edge of a constraint-type factor
+// (disk pair, wall, box, hinge, margin) whose x equals its n, standard
+// otherwise (standard classes are set once by fga_init).
+template <typename R>
+__device__ __forceinline__ void twa_mark(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io, int li) {
+    const int t = B.type;
+    const bool cons = t == 0 || t == 1 || t == 4 || t == 8 || t == 10;
+    if (!cons && t != 9) return;
+    const int ne = B.per_edge ? 1 : B.arity;
+    for (int k = 0; k < ne; ++k) {
+        const int e = B.per_edge ? B.ebase + li : bedge(B, li, k);
+        const R u = a.u[e], x = io.xout[e];
+        unsigned char c;
+        if (t == 9) {
+            c = 2;
+            a.pvm[a.pos[e]] = x + u;
+        } else {
+            const R n = ldg_l2(io.zc + a.svar[e]) - u;
+            c = x == n ? 0 : 1;
+        }
+        a.wcls[e] = c;
+        a.pwcls[a.pos[e]] = c;
+    }
 }
 
 // One scalar edge, start of phase F: returns n; u holds the updated u
@@ -861,6 +890,7 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, dou
             int b = 0;
             while (b + 1 < a.nb && it >= a.bk[b + 1].item0) ++b;
             process_in_bucket<R, MODE, false, KIND>(a, a.bk[b], io, it - a.bk[b].item0, pri);
+            if (MODE != F_U_ONLY && a.wcls) twa_mark<R>(a, a.bk[b], io, it - a.bk[b].item0);
         }
         return;
     }
@@ -1005,6 +1035,41 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         if constexpr (SHARD) s_out[b] = s_in ? s_in[b] + S : S;
         else z_store<R, CHK>(a, b, S, zo, zn, dual);
     };
+    if (!SHARD && a.zorder == 0 && a.wcls) {
+        // canonical, three weights: per variable, in creation order, the
+        // infinite-weight messages (m), the others (rho m) and among them
+        // the standard ones; z from the first non-empty group
+        for (long long b = gtid; b < a.nz; b += gstride) {
+            R S = R(0), Rr = R(0), Ss = R(0), Rs = R(0), Si = R(0), Ni = R(0);
+            for (int k = a.row[b]; k < a.row[b + 1]; ++k) {
+                const R v = ldg_l2(a.pvm + k);
+                const int c = a.pwcls[k];
+                if (c == 2) {
+                    Si += v;
+                    Ni += R(1);
+                } else {
+                    const R r = a.prho ? a.prho[k] : a.rho_u;
+                    S += v;
+                    Rr += r;
+                    if (c == 1) {
+                        Ss += v;
+                        Rs += r;
+                    }
+                }
+            }
+            const R zold = zo[b];
+            R znew = zold;
+            if (Ni > R(0)) znew = Si / Ni;
+            else if (Rs > R(0)) znew = Ss / Rs;
+            else if (Rr > R(0)) znew = S / Rr;
+            zn[b] = znew;
+            if constexpr (CHK) {
+                const double dz = (double)znew - (double)zold;
+                dual += a.srho2[b] * dz * dz;
+            }
+        }
+        return;
+    }
     if (a.zorder == 0) {
         // canonical.  Rows of at most kZShort values: one thread per
         // variable over the whole grid, its values added one by one in
