@@ -362,8 +362,8 @@ static int solve_typed(fga_mpc_batch *b, const fga_mpc_opts &o, fga_mpc_result &
     a.tol_dual = o.tol_dual;
     const int threads = o.threads > 0 ? o.threads : b->tuned_threads;
     a.check_every = o.check_every > 0 ? o.check_every : b->tuned_ce;
-    if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
-        return bfail(FGA_EINVAL, "fga_mpc_batch_solve: threads must be 64, 128, 256 or 512");
+    if (threads != 64 && threads != 128 && threads != 224 && threads != 256 && threads != 448 && threads != 512)
+        return bfail(FGA_EINVAL, "fga_mpc_batch_solve: threads must be 64, 128, 224, 256, 448 or 512");
     int rc;
     BCUDA(cudaEventRecord(b->ev0, b->stream));
     if (o.use_graph) {
@@ -470,7 +470,7 @@ static std::string tune_key(const fga_mpc_batch *b, long long K, double tol) {
     cudaDeviceProp p;
     cudaGetDeviceProperties(&p, b->device);
     std::ostringstream k;
-    k << p.name << "|sm" << p.major << p.minor << "|p" << b->precision << "|nx" << b->nx << "|nu" << b->nu << "|n"
+    k << "v2|" << p.name << "|sm" << p.major << p.minor << "|p" << b->precision << "|nx" << b->nx << "|nu" << b->nu << "|n"
       << b->n << "|tmax" << b->tmax << "|sys" << b->nsys << "|K" << K << "|tol" << tol;
     std::string s = k.str();
     for (char &c : s)
@@ -507,7 +507,7 @@ extern "C" int fga_mpc_batch_autotune(fga_mpc_batch *b, const char *cache_path, 
     BCUDA(cudaMemcpy(z0.p, b->dz.p, b->dz.bytes, cudaMemcpyDeviceToDevice));
     BCUDA(cudaMemcpy(u0.p, b->du.p, b->du.bytes, cudaMemcpyDeviceToDevice));
     BCUDA(cudaMemcpy(x0.p, b->dx.p, b->dx.bytes, cudaMemcpyDeviceToDevice));
-    const int th_c[4] = {64, 128, 256, 512};
+    const int th_c[6] = {64, 128, 224, 256, 448, 512};
     const int ce_c[4] = {1, 2, 5, 10};
     double best = std::numeric_limits<double>::infinity();
     int bt = 128, bc = 1;

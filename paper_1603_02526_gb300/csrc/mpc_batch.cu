@@ -473,14 +473,20 @@ __global__ void __launch_bounds__(NT) k_mpc_batch(const MpcArgs<R> a) {
 
 template <typename R>
 static const void *mpc_kernel(int threads, bool fixed) {
+    // 224 and 448 threads: 8 and 16 dynamics factors of 28 rows per pass,
+    // every lane busy in the x phase for 12 states and 4 inputs
     if (fixed)
         return threads == 64    ? (const void *)k_mpc_batch<R, 64, 12, 4>
                : threads == 128 ? (const void *)k_mpc_batch<R, 128, 12, 4>
+               : threads == 224 ? (const void *)k_mpc_batch<R, 224, 12, 4>
                : threads == 256 ? (const void *)k_mpc_batch<R, 256, 12, 4>
+               : threads == 448 ? (const void *)k_mpc_batch<R, 448, 12, 4>
                                 : (const void *)k_mpc_batch<R, 512, 12, 4>;
     return threads == 64    ? (const void *)k_mpc_batch<R, 64, 0, 0>
            : threads == 128 ? (const void *)k_mpc_batch<R, 128, 0, 0>
+           : threads == 224 ? (const void *)k_mpc_batch<R, 224, 0, 0>
            : threads == 256 ? (const void *)k_mpc_batch<R, 256, 0, 0>
+           : threads == 448 ? (const void *)k_mpc_batch<R, 448, 0, 0>
                             : (const void *)k_mpc_batch<R, 512, 0, 0>;
 }
 

@@ -131,7 +131,7 @@ def test_autotune_and_cache(tmp_path):
     b = batch_from_inputs(d, "f32")
     cache = tmp_path / "mpc_tune.txt"
     th, ce = b.fga_mpc_batch_autotune(2000, 1e-4, cache)
-    assert th in (64, 128, 256, 512) and ce in (1, 2, 5, 10)
+    assert th in (64, 128, 224, 256, 448, 512) and ce in (1, 2, 5, 10)
     assert cache.exists() and cache.read_text().strip()
     b2 = batch_from_inputs(d, "f32")
     assert b2.fga_mpc_batch_autotune(2000, 1e-4, cache) == (th, ce)     # cache hit
