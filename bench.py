@@ -362,6 +362,59 @@ def run_ours(args):
     return 0
 
 
+def run_shard(args):
+    """--shard: the packing graph (N=1000) split into WORLD_SIZE contiguous
+    factor slices, one per GPU (paper_1603_02526_gb300/shard.py), FP32 fast
+    z-order, the ranks' sums of rho m all-gathered every iteration and added in
+    rank order (NCCL under torchrun).  Strong scaling of one graph; the rank
+    exchange takes host round trips every iteration, so a step is 200
+    iterations."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    if "RANK" not in os.environ:
+        s = socket.socket()
+        s.bind(("127.0.0.1", 0))
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(s.getsockname()[1]), RANK="0",
+                          WORLD_SIZE="1", LOCAL_RANK="0")
+        s.close()
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    from paper_1603_02526_gb300 import build, inputs
+    from paper_1603_02526_gb300.shard import DistGroup, ShardGraph, ShardedSweep, split_problem
+    build.build()
+    iters = 200
+    p = inputs.packing_problem(N_DISKS, seed=SEED)
+    E = p.num_edges
+    parts, _ = split_problem(p, ws)
+    sh = ShardGraph(parts[rank], "f32", zorder=1, device=local)
+    sw = ShardedSweep(DistGroup(sh), E, exchange="gather")
+    for _ in range(args.warmup):
+        sw.init()
+        sw.iterate(iters, check_every=iters)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sw.init()
+        r = sw.iterate(iters, check_every=iters)
+    torch.cuda.synchronize()
+    dist.barrier()
+    dt = _max_over_ranks(time.perf_counter() - t0, ws)
+    if rank == 0:
+        v = E * iters * args.steps / dt
+        print(json.dumps({"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+                          "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "circle packing N=%d, %d iterations, split into %d shards of "
+                                                 "contiguous factors, gather exchange every iteration"
+                                                 % (N_DISKS, iters, ws), "parallelism": "shards"},
+                          "r_pri": r["r_pri"], "r_dual": r["r_dual"], "timing": "host clock, max over ranks"}))
+    dist.destroy_process_group()
+    return 0
+
+
 def run_extras(log=None):
     """The other workloads of the path, each to its stated tolerance: the
     packing solve in FP64, the SVM (100k x 64), the batched ragged MPC
@@ -661,6 +714,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the packing sweep (no SVM / MPC / warm start)")
+    ap.add_argument("--shard", action="store_true",
+                    help="one packing graph split across the ranks' GPUs (multi-GPU shards) instead of replicas")
     ap.add_argument("--zorder", type=int, default=None,
                     help="profiling run: force FGA_OPT_ZORDER (1 chunked, 2 disk tiles, 3 hinge bank)")
     ap.add_argument("--profile-workload", default="packing",
@@ -674,6 +729,8 @@ def main():
         return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard:
+        return run_shard(args)
     return run_ours(args)
 
 

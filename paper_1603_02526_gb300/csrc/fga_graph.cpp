@@ -1086,13 +1086,16 @@ extern "C" int fga_finalize(fga_graph *g) {
     g->blk = g->block ? g->block : 256;
     g->smem = g->zorder == 1 ? chunk_smem((int)g->rsize()).total : canonical_z_smem((int)g->rsize());
     // kernel variant: 1 = neither hinge / dynamics nor margin / equality
-    // paths, 2 = margin / equality paths only, 0 = every path
-    bool hd = false, me = false;
+    // paths, 2 = margin / equality paths only, 3 = dynamics of at most 9
+    // edges and elementwise paths, 0 = every path
+    bool has_hinge = false, dyn = false, dyn_big = false, me = false;
     for (const Bucket &bk : g->buckets) {
-        hd = hd || bk.type == FGA_SVM_HINGE || bk.type == FGA_MPC_DYN;
+        has_hinge = has_hinge || bk.type == FGA_SVM_HINGE;
+        dyn = dyn || bk.type == FGA_MPC_DYN;
+        dyn_big = dyn_big || (bk.type == FGA_MPC_DYN && bk.arity > 9);
         me = me || bk.type == FGA_SVM_MARGIN || bk.type == FGA_EQUAL;
     }
-    g->kind = hd ? 0 : me ? 2 : 1;
+    g->kind = (has_hinge || dyn_big || (dyn && me)) ? 0 : dyn ? 3 : me ? 2 : 1;
     if (tile) {
         g->blk = g->tile.W * 32;
         g->smem = tile_smem_bytes(g->tile);

@@ -832,9 +832,12 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
 
 // KIND 0: every factor type; KIND 1: graphs without hinge, dynamics, margin
 // and equality factors (packing); KIND 2: graphs with margin or equality
-// factors but no hinge or dynamics factors (the paper's SVM form).  Each
-// kernel is compiled without the paths its graphs lack, so that their
-// register demand does not limit it.
+// factors but no hinge or dynamics factors (the paper-form SVM); KIND 3:
+// dynamics factors of up to 9 edges (4 states, 1 input) and elementwise
+// factors, no hinge, margin or equality (the long-horizon MPC): without the
+// 28-edge dynamics path the kernel needs fewer registers and fits 4 CTAs
+// per SM.  Each kernel is compiled without the paths its graphs lack, so
+// that their register demand does not limit it.
 template <typename R, int MODE, bool FAST, int KIND>
 __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                   int li, double &pri) {
@@ -848,6 +851,9 @@ __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const B
         if constexpr (KIND == 0) {
             if (B.arity == 28) item_mpc_dyn<R, MODE, FAST, 28>(a, B, io, li, pri);
             else if (B.arity == 9) item_mpc_dyn<R, MODE, FAST, 9>(a, B, io, li, pri);   // 4 states, 1 input
+            else item_mpc_dyn<R, MODE, FAST, 0>(a, B, io, li, pri);
+        } else if constexpr (KIND == 3) {
+            if (B.arity == 9) item_mpc_dyn<R, MODE, FAST, 9>(a, B, io, li, pri);
             else item_mpc_dyn<R, MODE, FAST, 0>(a, B, io, li, pri);
         }
         break;
@@ -1248,7 +1254,7 @@ __device__ __forceinline__ EdgeIO<R> make_io(const SweepArgs<R> &a, int xp, int 
 // the persistent kernel: a whole call in one launch
 // ---------------------------------------------------------------------------
 template <typename R, int KIND>
-__global__ void __launch_bounds__(256, 3) k_sweep_persistent(const SweepArgs<R> a) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && (KIND == 1 || KIND == 3)) ? 4 : 3) k_sweep_persistent(const SweepArgs<R> a) {
     unsigned int gen = 0;
     const unsigned int G = gridDim.x;
     bool skip = (a.skip_block == (int)blockIdx.x);

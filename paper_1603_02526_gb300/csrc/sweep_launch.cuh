@@ -31,13 +31,17 @@ static cudaError_t allow_smem_k(int smem) {
 
 template <typename R>
 static cudaError_t allow_smem(int smem, int kind) {
-    return kind == 1 ? allow_smem_k<R, 1>(smem) : kind == 2 ? allow_smem_k<R, 2>(smem) : allow_smem_k<R, 0>(smem);
+    return kind == 1   ? allow_smem_k<R, 1>(smem)
+           : kind == 2 ? allow_smem_k<R, 2>(smem)
+           : kind == 3 ? allow_smem_k<R, 3>(smem)
+                       : allow_smem_k<R, 0>(smem);
 }
 
 template <typename R>
 static const void *persistent_fn(int kind) {
     return kind == 1   ? (const void *)k_sweep_persistent<R, 1>
            : kind == 2 ? (const void *)k_sweep_persistent<R, 2>
+           : kind == 3 ? (const void *)k_sweep_persistent<R, 3>
                        : (const void *)k_sweep_persistent<R, 0>;
 }
 
@@ -68,6 +72,7 @@ cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int g
     if (e != cudaSuccess) return e;
     if (kind == 1) phase_f_k<R, 1>(a, mode, xp, zp, grid, block, smem, s);
     else if (kind == 2) phase_f_k<R, 2>(a, mode, xp, zp, grid, block, smem, s);
+    else if (kind == 3) phase_f_k<R, 3>(a, mode, xp, zp, grid, block, smem, s);
     else phase_f_k<R, 0>(a, mode, xp, zp, grid, block, smem, s);
     return cudaGetLastError();
 }
