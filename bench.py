@@ -329,9 +329,11 @@ def run_ours(args):
                 "frac": floor_us / us_iter, "traffic": traffic, "kernel": "k_tile_sweep",
                 "floor_us": floor_us, "barrier_us": bar_us, "us_per_iter": us_iter,
                 "note": "peak = the latency floor of one iteration on the kernel's own grid (fga_latency_floor: "
-                        "every pass of the kernel except the operators -- the z gather's L2 loads, the fixed-point "
-                        "reductions and the grid barrier; barrier_us: the barrier alone), measured in this run; "
-                        "frac = floor / measured iteration; traffic = DRAM bytes per launch (ncu)",
+                        "what an unchecked pass does besides the operators -- every CTA adds one count-and-sum "
+                        "contribution per variable it holds and polls its variables' words until all holders' "
+                        "contributions are in; barrier_us: the grid-wide barrier alone, which only checked passes "
+                        "take), measured in this run; frac = floor / measured iteration; traffic = DRAM bytes per "
+                        "launch (ncu)",
                 "hbm_metric": hbm}
     if rank != 0:
         if ws > 1:
@@ -447,6 +449,21 @@ def run_extras(log=None):
                     "algorithmic_gbs": f64_bytes / (r["ms"] * 1e-3) / 1e9,
                     "frac_of_hbm": f64_bytes / (r["ms"] * 1e-3) / 1e9 / peak, "peak_kind": peak_kind}
         del g
+    # packing above the disk-tile limit (about 1,050 disks on 152 SMs):
+    # N = 2000 (about 12M scalar edges) through the chunked fast order, the
+    # time of 100 iterations
+    p = inputs.packing_problem(2000, seed=SEED)
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 0})
+    g.fga_iterate(20, check_every=20)
+    g.fga_init(p.z0)
+    r = g.fga_iterate(100, check_every=100)
+    out["packing_n2000_f32"] = {"workload": "circle packing N=2000, FP32, 100 iterations (above the disk-tile limit: "
+                                            "the chunked fast z order)", "scalar_edges": p.num_edges,
+                                "zorder": g.fga_launch_info()["zorder"], "ms_100_iters": r["ms"],
+                                "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3),
+                                "frac_of_hbm": 20 * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak,
+                                "kernel": "k_sweep_persistent<float, 1>", "peak_kind": peak_kind}
+    del g
     # SVM
     p = inputs.svm_problem(100000, 64, seed=3000)
     g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 0})

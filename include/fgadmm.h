@@ -239,13 +239,14 @@ int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result
 int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n);
 
 /* Latency floor of the disk-tile order (FGA_OPT_ZORDER 2) on this graph's
- * grid: device time of `iters` passes that do everything a pass does
- * except the operators -- mode 1: each CTA's L2 loads of its variables'
- * accumulators (the z gather), one fixed-point reduction per variable (the
- * partial sums; the value added is zero) and the grid-wide barrier; mode
- * 0: the barrier alone.  A measurement of the hardware's floor under a
- * pass (the paper reports where an iteration's time goes, Sec. V-A); the
- * graph's state is not changed.  *ms: device time (CUDA events). */
+ * grid: device time of `iters` passes that do everything an unchecked pass
+ * does except the operators -- mode 1: each CTA adds one count-and-sum
+ * contribution (value zero) per variable it holds and polls its variables'
+ * words until every holder's contribution is in (the z exchange); mode 0:
+ * the grid-wide barrier alone (which checked passes add).  A measurement of
+ * the hardware's floor under a pass (the paper reports where an
+ * iteration's time goes, Sec. V-A); the graph's variables and messages are
+ * not changed.  *ms: device time (CUDA events). */
 int fga_latency_floor(fga_graph *g, int64_t iters, int32_t mode, float *ms);
 
 /* Residuals of the last checked iteration (NaN before any). */
@@ -434,7 +435,13 @@ typedef struct {
     int64_t max_iters;          /* budget per instance                      */
     double tol_pri, tol_dual;   /* RMS residual tolerances per instance     */
     int32_t check_every;        /* 0 = autotuned value (default 1)          */
-    int32_t threads;            /* CTA size 64/128/224/256/448/512; 0 = autotuned (128) */
+    int32_t threads;            /* CTA size 64/128/224/256/448/512 (one CTA
+                                   per instance at a time); 32 = one lane
+                                   per time step, its state in registers
+                                   (FP32, 12 states, 4 inputs, horizons up
+                                   to 64: a warp per instance of up to 32
+                                   steps, two warps up to 64); 0 =
+                                   autotuned (128)                           */
     int32_t use_graph;          /* 1 = launch from a cached CUDA graph      */
     int32_t reserved;
 } fga_mpc_opts;
@@ -462,7 +469,7 @@ int fga_mpc_batch_read(fga_mpc_batch *b, double *z, double *u, int64_t *iters, i
  * horizon, [4] tuned CTA size, [5] tuned check interval.  n >= 6. */
 int fga_mpc_batch_info(const fga_mpc_batch *b, int64_t *info, int32_t n);
 
-/* Autotuner: times CTA sizes {64,128,224,256,448,512} x check intervals {1,2,5,10} on
+/* Autotuner: times CTA sizes {32 (where it applies),64,128,224,256,448,512} x check intervals {1,2,5,10} on
  * the batch from its current start point (which it restores) and keeps the
  * fastest for later solves.  cache_path (may be NULL): a text file of
  * previous results keyed by GPU, precision and problem shape; a hit skips

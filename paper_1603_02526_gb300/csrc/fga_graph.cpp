@@ -482,7 +482,7 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         if ((rc = upload_vec(g->t_cptr, T.cptr))) return rc;
         if ((rc = upload_vec(g->t_clist, T.clist))) return rc;
         if ((rc = upload_vec(g->t_loc, T.loc))) return rc;
-        CUDA_TRY(g->t_part.alloc((size_t)3 * T.ptot * sizeof(long long)));
+        CUDA_TRY(g->t_part.alloc((size_t)2 * T.ptot * sizeof(unsigned long long)));
         CUDA_TRY(cudaMemset(g->t_part.p, 0, g->t_part.bytes));
         CUDA_TRY(g->t_dsave.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
         CUDA_TRY(g->t_dres.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
@@ -1380,7 +1380,7 @@ static void fill_tile_args(const fga_graph *g, TileArgs &a) {
     a.xout = g->x[a.xw].as<float>();
     a.zin = g->z[g->zpar].as<float>();
     a.zout = g->z[a.zw].as<float>();
-    a.acc = g->t_part.as<long long>();
+    a.acc = g->t_part.as<unsigned long long>();
     a.ptot = T.ptot;
     a.res = g->t_res.as<double>();
     a.pair_ebase = (int)g->tile_pair_ebase;
@@ -1411,7 +1411,7 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     }
     CUDA_TRY(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), s));
     CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
-    CUDA_TRY(cudaMemsetAsync(g->t_part.p, 0, g->t_part.bytes, s));   // the fixed-point accumulators
+    CUDA_TRY(cudaMemsetAsync(g->t_part.p, 0, g->t_part.bytes, s));   // the count-and-sum words
     // z of variables outside every tile (none in a qualifying graph) keep
     // their value in the buffer the call writes
     CUDA_TRY(cudaMemcpyAsync(a.zout, a.zin, (size_t)g->nz * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -1823,6 +1823,7 @@ extern "C" int fga_latency_floor(fga_graph *g, int64_t iters, int32_t mode, floa
     a.timeout_ns = 2000000000LL;
     cudaStream_t s = g->stream;
     CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
+    CUDA_TRY(cudaMemsetAsync(g->t_part.p, 0, g->t_part.bytes, s));   // the next solve zeroes them again
     CUDA_TRY(cudaEventRecord(g->ev0, s));
     CUDA_TRY(tile_floor_launch(a, iters, mode, g->blk, g->smem, s));
     CUDA_TRY(cudaEventRecord(g->ev1, s));

@@ -27,11 +27,13 @@
 //
 // z-update (deterministic, no float atomics): each CTA sums the staged unit
 // and local-factor contributions per variable in a fixed order and adds
-// that partial, as a 64-bit fixed-point integer, into the variable's
-// accumulator; integer addition is exact and associative, so after the
-// grid-wide barrier every CTA reads the same sum whatever the order of the
-// additions.  One grid barrier per iteration.  The residuals (FP64 sums)
-// ride on the same barrier: the check of iteration k-1 is evaluated during
+// that partial, as a 64-bit fixed-point integer together with a count of
+// one, into the variable's word; integer addition is exact and associative,
+// so every CTA reads the same sum whatever the order of the additions.  A
+// CTA starts its next pass once each of its variables' words counts all the
+// variable's holders (tile_gather): there is no grid-wide barrier on an
+// unchecked pass.  A checked pass adds one, so that every CTA decides on the
+// same residual sums (FP64): the check of iteration k-1 is evaluated during
 // iteration k.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -84,19 +86,51 @@ static __device__ __forceinline__ float radius_disp(int type, float n, float p0)
 // ---------------------------------------------------------------------------
 // z gather: z <- z + (sum of the variable's partials) / deg, the old z kept
 // as z_prev and, for the alpha = 1 form, y = 2 z - z_prev (the old y kept as
-// y_prev).  Owners write z out (checks) and add the dual residual
-// rho^2 (z - z_prev)^2 of their variables.
+// y_prev).  Each variable's new partials are the difference between its
+// accumulator word of the previous pass's parity and the value that word
+// had when read two passes before (pv); the thread polls the word until
+// that difference counts all the variable's holders, which is the only wait
+// between the CTAs of an unchecked pass.  Owners write z
+// out (checks) and add the dual residual rho^2 (z - z_prev)^2 of their
+// variables.  Returns false when a poll ran out of time (the error word is
+// then set and the launch ends).
 // ---------------------------------------------------------------------------
+static __device__ __forceinline__ unsigned tile_count(unsigned long long diff) {
+    return (unsigned)(((diff + (1ull << 55)) >> 56) & 0xffull);
+}
+
 template <bool CHK, bool A1>
-static __device__ __forceinline__ void tile_gather(const TileArgs &a, int nsv, const int4 *sv, const float *zden,
-                                                   float *zt, float *zpt, float *yt, float *ypt, int rbuf, int cbuf,
-                                                   double &dual) {
-    const long long *src = a.acc + (size_t)rbuf * a.ptot;
-    long long *clr = a.acc + (size_t)cbuf * a.ptot;
+static __device__ __forceinline__ bool tile_gather(const TileArgs &a, int nsv, const int4 *sv, const float *zden,
+                                                   float *zt, float *zpt, float *yt, float *ypt,
+                                                   unsigned long long *pv, int par, double &dual) {
+    bool ok = true;
+    const unsigned long long *src = a.acc + (size_t)par * a.ptot;
+    pv += (size_t)par * nsv;
     for (int i = threadIdx.x; i < nsv; i += blockDim.x) {
         const int4 d = sv[i];
-        const float S = __fmul_rn(__ll2float_rn(__ldcg(src + d.x)), kTileFixInv);
-        const int s = i / 3, q = i - 3 * s, o = 4 * s + q;
+        const unsigned long long p = pv[i], want = (unsigned long long)d.y;
+        unsigned long long w = ld_relaxed_u64(src + d.x);
+        if (tile_count(w - p) != (unsigned)want) {
+            const unsigned long long t0 = global_ns();
+            unsigned int spins = 0;
+            for (;;) {
+                w = ld_relaxed_u64(src + d.x);
+                if (tile_count(w - p) == (unsigned)want) break;
+                if ((++spins & 63u) == 0u) {
+                    if (*(volatile int *)&a.sync->error ||
+                        global_ns() - t0 > (unsigned long long)a.timeout_ns || spins > (1u << 30)) {
+                        atomicCAS(&a.sync->error, 0, kETimeout);
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            if (!ok) break;
+        }
+        pv[i] = w;
+        const long long q = (long long)(w - p - want * kTileCountUnit);
+        const float S = __fmul_rn(__ll2float_rn(q), kTileFixInv);
+        const int s = i / 3, qq = i - 3 * s, o = 4 * s + qq;
         const float zo = zt[o];
         const float zn = __fadd_rn(zo, __fdiv_rn(S, zden[i]));
         zpt[o] = zo;
@@ -105,17 +139,14 @@ static __device__ __forceinline__ void tile_gather(const TileArgs &a, int nsv, c
             ypt[o] = yt[o];
             yt[o] = __fmaf_rn(2.f, zn, -zo);
         }
-        if (d.w < 0) {
-            // the owner clears the accumulator read in the previous pass
-            __stcg(clr + d.x, 0ll);
-            if (CHK) {
-                a.zout[d.x] = zn;
-                if (A1) a.zpout[d.x] = zo;
-                const double dz = (double)zn - (double)zo;
-                dual += __ldg(a.srho2 + d.x) * dz * dz;
-            }
+        if (CHK && d.w < 0) {
+            a.zout[d.x] = zn;
+            if (A1) a.zpout[d.x] = zo;
+            const double dz = (double)zn - (double)zo;
+            dual += __ldg(a.srho2 + d.x) * dz * dz;
         }
     }
+    return ok;
 }
 
 // Register slot j of lane l holds column j ^ mp, mp = (l >> 2) & 7, of the
@@ -550,6 +581,7 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     int *cptr = reinterpret_cast<int *>(tsm + L.cptr);
     int *clist = reinterpret_cast<int *>(tsm + L.clist);
     float *stg = reinterpret_cast<float *>(tsm + L.stg);
+    unsigned long long *pv = reinterpret_cast<unsigned long long *>(tsm + L.pv);
     float *zt = reinterpret_cast<float *>(z4);
     float *zpt = reinterpret_cast<float *>(zp4);
     float *yt = reinterpret_cast<float *>(y4);
@@ -601,6 +633,8 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) {
         const int4 d = a.sv[C.sv0 + i];
         sv[i] = d;
+        pv[i] = 0ull;   // the words are zeroed before the launch
+        pv[C.nsv + i] = 0ull;
         zden[i] = a.zden[C.sv0 + i];
         const int s = i / 3, q = i - 3 * s;
         const float z0 = a.zin[d.x];
@@ -634,6 +668,8 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     // resuming (alpha = 1): the first pass is an ordinary one, from the
     // displacements and the two z of the previous call's last iteration
     const bool res1 = A1 && a.resume;
+    __shared__ int s_ok;
+    int nchk = 0;   // checks so far: their residual partials alternate between two buffers
     for (long long it = 1; it <= a.K + 1; ++it) {
         const bool fin = it == a.K + 1;
         const bool pend = it > 1;
@@ -642,12 +678,16 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
         const bool save = A1 && (pend || res1) && !fin && (it == a.K || (a.k0 + it) % a.check_every == 0);
         const bool reload = it == 2 && !res1;
         double pri = 0.0, dual = 0.0;
+        if (threadIdx.x == 0) s_ok = 1;
+        __syncthreads();
         if (pend) {
-            const int rb = (int)((it - 1) % 3), cb = (int)((it + 1) % 3);
-            if (chk) tile_gather<true, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, rb, cb, dual);
-            else tile_gather<false, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, rb, cb, dual);
+            const int par = (int)((it - 1) & 1);   // the words the previous pass added into
+            const bool ok = chk ? tile_gather<true, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, pv, par, dual)
+                                : tile_gather<false, A1>(a, C.nsv, sv, zden, zt, zpt, yt, ypt, pv, par, dual);
+            if (!ok) s_ok = 0;
         }
         __syncthreads();
+        if (!s_ok) return;   // a wait ran out of time (error word set)
         PassMode pm;
         pm.mode = !pend ? (res1 ? T_MID : T_FIRST) : fin ? T_FINAL : chk ? T_CHK : T_MID;
         pm.reload = reload && (chk || fin);
@@ -661,7 +701,7 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
         if (!fin) {
             // one partial per (CTA, variable): staged contributions in list
             // order, added in fixed point into the variable's accumulator
-            unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.acc + (size_t)(it % 3) * a.ptot);
+            unsigned long long *dst = a.acc + (size_t)(it & 1) * a.ptot;
             bool ovf = false;
             for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) {
                 const int j1 = cptr[i + 1];
@@ -681,7 +721,8 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
                 long long q = 0;
                 if (fabsf(S) < kTileFixMax) q = __float2ll_rn(__fmul_rn(S, kTileFixScale));
                 else ovf = true;
-                red_add_u64(dst + sv[i].x, (unsigned long long)q);
+                // one contribution: its count and its value in one addition
+                red_add_u64(dst + sv[i].x, kTileCountUnit + (unsigned long long)q);
             }
             if (ovf) atomicOr(&a.sync->overflow, 1);
         }
@@ -691,16 +732,20 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
             const double sp = (double)bs.x + (double)bs.y;
             const double sd = (double)bs.z + (double)bs.w;
             if (threadIdx.x == 0) {
-                double *r = a.res + (size_t)(it & 1) * 2 * a.G;
+                double *r = a.res + (size_t)(nchk & 1) * 2 * a.G;
                 r[blockIdx.x] = sp;
                 r[a.G + blockIdx.x] = sd;
             }
         }
-        if (!tile_barrier(a.sync, G * (unsigned long long)it, a.timeout_ns, skip)) return;
+        // the grid-wide barrier only where the residual decision needs
+        // every CTA's partials; otherwise the next pass's polls are the wait
+        if (!chk) continue;
+        ++nchk;
+        if (!tile_barrier(a.sync, G * (unsigned long long)nchk, a.timeout_ns, skip)) return;
         skip = false;
-        if (chk) {
+        {
             if (threadIdx.x < 32) {
-                const double *r = a.res + (size_t)(it & 1) * 2 * a.G;
+                const double *r = a.res + (size_t)((nchk - 1) & 1) * 2 * a.G;
                 const double sp = warp_sum_partials(r, a.G);
                 const double sd = warp_sum_partials(r + a.G, a.G);
                 if (threadIdx.x == 0) {
@@ -745,36 +790,58 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
 
 // ---------------------------------------------------------------------------
 // Latency floor of one pass on the same grid (a measurement, not part of a
-// solve).  MODE 0: the grid-wide barrier alone.  MODE 1: what a pass costs
-// besides the operators -- every CTA reads its variables' accumulators (the
-// z gather's L2 loads), adds one fixed-point value per variable (the partial
-// sums' reductions; the value added is 0, so no accumulator changes), and
-// the barrier.  The graph's state is not touched.
+// solve).  MODE 0: the grid-wide barrier alone (what a checked pass adds).
+// MODE 1: what an unchecked pass costs besides the operators -- every CTA
+// adds one contribution to each variable it holds (count and a value of 0),
+// then polls its variables' words until every holder's contribution of the
+// pass is counted.  Needs the accumulator words zeroed before the launch.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_floor(const TileArgs a, long long iters) {
     extern __shared__ __align__(16) unsigned char tsm[];
     const TileSmem L = tile_smem_layout(a.smax, a.svmax, a.locmax, a.clmax, a.stgmax);
     int4 *sv = reinterpret_cast<int4 *>(tsm + L.sv);
-    float *zt = reinterpret_cast<float *>(tsm + L.z4);
+    unsigned long long *pv = reinterpret_cast<unsigned long long *>(tsm + L.pv);
     const TileCta C = a.cta[blockIdx.x];
     for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) {
         sv[i] = a.sv[C.sv0 + i];
-        zt[i] = 0.f;
+        pv[i] = 0ull;
+        pv[C.nsv + i] = 0ull;
     }
+    __shared__ int s_ok;
     __syncthreads();
     const unsigned long long G = (unsigned long long)a.G;
     for (long long it = 1; it <= iters; ++it) {
         if (MODE == 1) {
-            const long long *src = a.acc + (size_t)((it + 2) % 3) * a.ptot;
-            for (int i = threadIdx.x; i < C.nsv; i += blockDim.x)
-                zt[i] += __fmul_rn(__ll2float_rn(__ldcg(src + sv[i].x)), kTileFixInv);
+            // the pass's contributions into the words of its parity, then
+            // the wait for every holder's
+            unsigned long long *acc = a.acc + (size_t)(it & 1) * a.ptot;
+            unsigned long long *pp = pv + (size_t)(it & 1) * C.nsv;
+            for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) red_add_u64(acc + sv[i].x, kTileCountUnit);
+            if (threadIdx.x == 0) s_ok = 1;
             __syncthreads();
-            unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.acc + (size_t)(it % 3) * a.ptot);
-            for (int i = threadIdx.x; i < C.nsv; i += blockDim.x)
-                red_add_u64(dst + sv[i].x, zt[i] == 12345.f ? 1ull : 0ull);   // adds 0 (never 1)
+            for (int i = threadIdx.x; i < C.nsv; i += blockDim.x) {
+                const unsigned long long p = pp[i];
+                const unsigned want = (unsigned)sv[i].y;
+                unsigned long long w = ld_relaxed_u64(acc + sv[i].x);
+                const unsigned long long t0 = global_ns();
+                unsigned int spins = 0;
+                while (tile_count(w - p) != want) {
+                    if ((++spins & 63u) == 0u &&
+                        (*(volatile int *)&a.sync->error || global_ns() - t0 > (unsigned long long)a.timeout_ns)) {
+                        atomicCAS(&a.sync->error, 0, kETimeout);
+                        s_ok = 0;
+                        break;
+                    }
+                    w = ld_relaxed_u64(acc + sv[i].x);
+                }
+                pp[i] = w;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+        } else if (!tile_barrier(a.sync, G * (unsigned long long)it, a.timeout_ns, false)) {
+            return;
         }
-        if (!tile_barrier(a.sync, G * (unsigned long long)it, a.timeout_ns, false)) return;
     }
 }
 

@@ -27,16 +27,28 @@ constexpr int kTileCols = 8;                                // disks per column 
 constexpr int kUnitEdges = kTileRows * kTileCols * 6;       // storage slots of one unit
 constexpr int kUnitStage = 3 * kTileRows + 3 * kTileCols;   // staged partial sums of one unit
 constexpr int kTileMaxWarps = 16;                           // units (warps) per CTA, at most
-constexpr int kTileMaxHolders = 256;                        // CTAs holding one variable, at most
-// Per-CTA partial sums are added into one 64-bit fixed-point accumulator per
-// variable (scale 2^32): integer addition is exact and associative, so the
-// sum does not depend on the order in which the CTAs' additions land.  A
-// partial of magnitude 2^22 or more (or not finite) is reported as a
-// non-finite residual; with at most kTileMaxHolders partials the sum stays
-// below 2^62.
+constexpr int kTileMaxHolders = 255;                        // CTAs holding one variable, at most
+// Per-CTA partial sums are added into one 64-bit word per variable: the
+// count of contributions in the top 8 bits (2^56 per contribution, modulo
+// 256) and the sum in fixed point (scale 2^32) below, both by one integer
+// addition of 2^56 + q.  Integer addition is exact and associative, so the
+// sum does not depend on the order in which the CTAs' additions land, and a
+// reader knows from the word alone when every holder has added.  Two words
+// per variable: pass p adds into word p mod 2, pass p + 1 reads it.  A word
+// only grows (it is never cleared during a launch), and a CTA reads each
+// variable's new contributions as the difference to the word it saw two
+// passes before, complete when that difference counts the variable's
+// holders.  No contribution of a later pass can be in it yet: a holder adds
+// to the same word again only in pass p + 2, after its own pass p + 1
+// gather, which waits for this CTA's pass p + 1 contribution to the same
+// variable, made after this read.
+// A partial of magnitude 2^14 or more (or not finite) is reported as a
+// non-finite residual; with at most kTileMaxHolders partials one pass's sum
+// stays below 2^54 in magnitude, clear of the count bits.
 constexpr float kTileFixScale = 4294967296.0f;              // 2^32
 constexpr float kTileFixInv = 2.3283064365386963e-10f;      // 2^-32
-constexpr float kTileFixMax = 4194304.0f;                   // 2^22
+constexpr float kTileFixMax = 16384.0f;                     // 2^14
+constexpr unsigned long long kTileCountUnit = 1ull << 56;
 
 // A wall or radius factor, processed by one thread of the CTA it is given
 // to.  p: wall Qx, Qy, Vx, Vy, 1 / (|Q|^2 + 1); linear reward w / rho;
@@ -76,7 +88,7 @@ static_assert(offsetof(TileSync, error) == offsetof(Barrier, error), "error word
 // walls and rewards with their u, the edge counts, the contribution lists,
 // and the staging area of the partial sums.
 struct TileSmem {
-    int z4, zp4, y4, yp4, sv, loc, uloc, zden, cptr, clist, stg, total;
+    int z4, zp4, y4, yp4, sv, loc, uloc, zden, cptr, clist, stg, pv, total;
 };
 inline __host__ __device__ constexpr int tile_align16(int v) { return (v + 15) & ~15; }
 inline __host__ __device__ TileSmem tile_smem_layout(int smax, int svmax, int locmax, int clmax, int stgmax) {
@@ -104,6 +116,8 @@ inline __host__ __device__ TileSmem tile_smem_layout(int smax, int svmax, int lo
     o = tile_align16(o + clmax * 4);
     L.stg = o;
     o = tile_align16(o + stgmax * 4);
+    L.pv = o;   // per slot-var and word: the value seen the last time
+    o = tile_align16(o + svmax * 16);
     L.total = o;
     return L;
 }
@@ -137,9 +151,8 @@ struct TileArgs {
     float *xout;                     // x buffer written at checks and at the end
     const float *zin;                // z at the start of the call
     float *zout;                     // z written at checks and at the end
-    long long *acc;                  // [3][ptot] fixed-point sums per variable; pass p adds
-                                     // into buffer p % 3, pass p + 1 reads it, the owners
-                                     // clear it during pass p + 2
+    unsigned long long *acc;         // [2][ptot] count and fixed-point sum per variable (see
+                                     // kTileCountUnit), zeroed before a launch
     int ptot;                        // scalar variables
     double *res;                     // [2][2][G] residual partial sums (pri, dual)
     int pair_ebase;                  // storage index of unit 0
