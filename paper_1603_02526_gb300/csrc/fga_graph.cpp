@@ -468,7 +468,7 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         CUDA_TRY(g->h_l2save.alloc((size_t)kHingeMaxL2 * kHingeD * sizeof(float)));
         CUDA_TRY(g->h_l2res.alloc((size_t)kHingeMaxL2 * kHingeD * sizeof(float)));
         CUDA_TRY(cudaMemset(g->h_l2res.p, 0, g->h_l2res.bytes));
-        CUDA_TRY(g->h_acc.alloc((size_t)3 * (g->hin.D + 1) * kHingeAccStride * sizeof(long long)));
+        CUDA_TRY(g->h_acc.alloc((size_t)2 * (g->hin.D + 1) * kHingeAccStride * sizeof(unsigned long long)));
         CUDA_TRY(cudaMemset(g->h_acc.p, 0, g->h_acc.bytes));
         CUDA_TRY(g->t_zprev.alloc((size_t)std::max<int64_t>(g->nz, 1) * sizeof(float)));
     } else if (g->zorder == 2) {
@@ -1480,7 +1480,7 @@ static int iterate_hinge(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
     a.hb_e0 = (int)g->hinge_e0;
     a.l2_e0 = (int)g->l2_e0;
     a.l2_nf = (int)g->l2_nf;
-    a.acc = g->h_acc.as<long long>();
+    a.acc = g->h_acc.as<unsigned long long>();
     a.gsave = g->h_gsave.as<float>();
     a.gres = g->h_gres.as<float>();
     a.l2save = g->h_l2save.as<float>();
@@ -1508,7 +1508,7 @@ static int iterate_hinge(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
     }
     CUDA_TRY(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), s));
     CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
-    CUDA_TRY(cudaMemsetAsync(g->h_acc.p, 0, g->h_acc.bytes, s));   // the fixed-point accumulators
+    CUDA_TRY(cudaMemsetAsync(g->h_acc.p, 0, g->h_acc.bytes, s));   // the count-and-sum words
     CUDA_TRY(cudaMemcpyAsync(a.zout, a.zin, (size_t)g->nz * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaEventRecord(g->ev0, s));
     CUDA_TRY(hinge_sweep_launch(a, g->smem, s));

@@ -42,6 +42,10 @@ int hinge_plan(const HingeInput &in, HingePlan &P, std::string &why) {
         return 1;
     }
     const int G = (int)((N + rows - 1) / rows);
+    if (G > kTileMaxHolders) {   // every CTA adds to every variable: the word counts at most 255
+        why = "more CTAs than a count-and-sum word counts";
+        return 1;
+    }
     P.G = G;
     P.rows_max = (int)rows;
     P.cta.resize((size_t)G);

@@ -52,7 +52,8 @@ struct HingeArgs {
     int vw, vb;                      // scalar ids of w_0 and of b
     int hb_e0;                       // storage of hinge factor f, edge j: hb_e0 + f (D + 1) + j
     int l2_e0, l2_nf;                // storage of L2 factor f, edge j: l2_e0 + j l2_nf + f
-    long long *acc;                  // [3][(D + 1) * kHingeAccStride] fixed-point sums
+    unsigned long long *acc;         // [2][(D + 1) * kHingeAccStride] count-and-sum words by pass
+                                     // parity (see kTileCountUnit), zeroed before a launch
     float *gsave;                    // [2][N] g kept for the next check (by pass parity)
     float *gres;                     // [N] g of the stored state
     float *l2save, *l2res;           // [nl2][64] the same for the L2 factors

@@ -54,6 +54,12 @@ static __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsign
     return v;
 }
 
+// Count of contributions in the difference of two count-and-sum words
+// (kTileCountUnit per contribution, the sum in the low bits).
+static __device__ __forceinline__ unsigned tile_count(unsigned long long diff) {
+    return (unsigned)(((diff + (1ull << 55)) >> 56) & 0xffull);
+}
+
 // The CTA's writes before the barrier are ordered by bar.sync and the
 // cumulative release of the arrival; the waiting thread polls with relaxed
 // loads and takes one acquire load once the count is reached, which orders

@@ -34,7 +34,7 @@ namespace fga {
 // Shared memory: data rows, per-factor (y, c, |x|^2 + 1), z / z_prev / y /
 // y_prev per component, the warps' staged sums, the L2 state.
 struct HingeSmem {
-    int X, meta, z, zp, y, yp, stg, l2d, l2s, total;
+    int X, meta, z, zp, y, yp, stg, l2d, l2s, pv, total;
 };
 static __host__ __device__ HingeSmem hinge_smem_layout(int rows) {
     HingeSmem L{};
@@ -57,6 +57,8 @@ static __host__ __device__ HingeSmem hinge_smem_layout(int rows) {
     o += kHingeMaxL2 * kHingeD * 4;
     L.l2s = o;
     o += kHingeMaxL2 * kHingeD * 4;
+    L.pv = o;   // per variable and word parity: the value seen the last time
+    o += 2 * 80 * 8;
     L.total = o;
     return L;
 }
@@ -238,7 +240,9 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
     float *stg = reinterpret_cast<float *>(hsm + L.stg);
     float *l2d = reinterpret_cast<float *>(hsm + L.l2d);
     float *l2s = reinterpret_cast<float *>(hsm + L.l2s);
+    unsigned long long *pv = reinterpret_cast<unsigned long long *>(hsm + L.pv);
     __shared__ double s_res[2];
+    __shared__ int s_ok;
     __shared__ int s_dec[2];
     __shared__ ResidualTest s_rt[2];   // primal, dual; read by thread 0 at checks
     if (threadIdx.x == 0) {
@@ -270,6 +274,8 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
         zpt[j] = zp0;
         yt[j] = a.resume ? __fmaf_rn(2.f, z0, -zp0) : 0.f;
         ypt[j] = 0.f;
+        pv[j] = 0ull;   // the words are zeroed before the launch
+        pv[80 + j] = 0ull;
     }
     if (blockIdx.x == 0)
         for (int q = threadIdx.x; q < kHingeMaxL2 * kHingeD; q += blockDim.x) {
@@ -289,6 +295,7 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
     const float inv_fix = kTileFixInv;
     bool skip = a.skip_block == (int)blockIdx.x;
     const bool res1 = a.resume != 0;
+    int nchk = 0;   // checks so far: their residual partials alternate between two buffers
     for (long long it = 1; it <= a.K + 1; ++it) {
         const bool fin = it == a.K + 1;
         const bool pend = it > 1;
@@ -296,11 +303,35 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
         const bool save = (pend || res1) && !fin && (it == a.K || (a.k0 + it) % a.check_every == 0);
         const bool reload = it == 2 && !res1;
         double pri = 0.0, dual = 0.0;
+        if (threadIdx.x == 0) s_ok = 1;
+        __syncthreads();
         if (pend && threadIdx.x < NV) {
-            // z <- z + sum / deg from the accumulators of the previous pass
+            // z <- z + sum / deg from the words of the previous pass: every
+            // CTA holds every variable, so the word of the previous pass's
+            // parity is complete when it counts G contributions more than
+            // when this CTA read it two passes before (see kTileCountUnit)
             const int j = threadIdx.x;
-            const long long *src = a.acc + (size_t)((it - 1) % 3) * NV * kHingeAccStride;
-            const float S = __fmul_rn(__ll2float_rn(__ldcg(src + (size_t)j * kHingeAccStride)), inv_fix);
+            const int par = (int)((it - 1) & 1);
+            const unsigned long long *src = a.acc + (size_t)par * NV * kHingeAccStride + (size_t)j * kHingeAccStride;
+            const unsigned long long p = pv[par * 80 + j];
+            unsigned long long w = ld_relaxed_u64(src);
+            if (tile_count(w - p) != (unsigned)G) {
+                const unsigned long long t0 = global_ns();
+                unsigned int spins = 0;
+                for (;;) {
+                    w = ld_relaxed_u64(src);
+                    if (tile_count(w - p) == (unsigned)G) break;
+                    if ((++spins & 63u) == 0u &&
+                        (*(volatile int *)&a.sync->error ||
+                         global_ns() - t0 > (unsigned long long)a.timeout_ns || spins > (1u << 30))) {
+                        atomicCAS(&a.sync->error, 0, kETimeout);
+                        s_ok = 0;
+                        break;
+                    }
+                }
+            }
+            pv[par * 80 + j] = w;
+            const float S = __fmul_rn(__ll2float_rn((long long)(w - p - G * kTileCountUnit)), inv_fix);
             const float zo = zt[j];
             const int deg = j < D ? a.deg_w : a.deg_b;
             const float zn = __fadd_rn(zo, __fdiv_rn(S, (float)deg));
@@ -309,9 +340,7 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
             ypt[j] = yt[j];
             yt[j] = __fmaf_rn(2.f, zn, -zo);
             if (blockIdx.x == 0) {
-                // CTA 0 owns the variables: clears the accumulator read in
-                // the previous pass, stores z at checks, adds the dual residual
-                __stcg(a.acc + (size_t)((it + 1) % 3) * NV * kHingeAccStride + (size_t)j * kHingeAccStride, 0ll);
+                // CTA 0 owns the variables: stores z at checks, adds the dual residual
                 if (chk) {
                     const int v = j < D ? a.vw + j : a.vb;
                     a.zout[v] = zn;
@@ -322,6 +351,7 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
             }
         }
         __syncthreads();
+        if (!s_ok) return;   // a wait ran out of time (error word set)
         PassMode pm;
         pm.mode = !pend ? (res1 ? T_MID : T_FIRST) : fin ? T_FINAL : chk ? T_CHK : T_MID;
         pm.reload = reload && (chk || fin);
@@ -363,21 +393,28 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
                 long long q = 0;
                 if (fabsf(S) < kTileFixMax) q = __float2ll_rn(__fmul_rn(S, kTileFixScale));
                 else atomicOr(&a.sync->overflow, 1);
-                red_add_u64(reinterpret_cast<unsigned long long *>(a.acc + (size_t)(it % 3) * NV * kHingeAccStride +
-                                                                   (size_t)j * kHingeAccStride),
-                            (unsigned long long)q);
+                // one contribution: its count and its value in one addition
+                red_add_u64(a.acc + (size_t)(it & 1) * NV * kHingeAccStride + (size_t)j * kHingeAccStride,
+                            kTileCountUnit + (unsigned long long)q);
             }
         }
         if (chk) {
-            // the CTA's two sums as float pairs, one float4 per CTA and pass parity
+            // the CTA's two sums as float pairs, one float4 per CTA and check parity
             const float4 bs = block_sum2_ff(pri, dual);
-            if (threadIdx.x == 0) reinterpret_cast<float4 *>(a.res)[(size_t)(it & 1) * a.G + blockIdx.x] = bs;
+            if (threadIdx.x == 0) reinterpret_cast<float4 *>(a.res)[(size_t)(nchk & 1) * a.G + blockIdx.x] = bs;
         }
-        if (!tile_barrier(a.sync, G * (unsigned long long)it, a.timeout_ns, skip)) return;
+        // the grid-wide barrier only where the residual decision needs every
+        // CTA's partials; otherwise the next pass's polls are the wait
+        if (!chk) {
+            skip = false;
+            continue;
+        }
+        ++nchk;
+        if (!tile_barrier(a.sync, G * (unsigned long long)nchk, a.timeout_ns, skip)) return;
         skip = false;
-        if (chk) {
+        {
             if (threadIdx.x < 32) {
-                const float4 *r4 = reinterpret_cast<const float4 *>(a.res) + (size_t)(it & 1) * a.G;
+                const float4 *r4 = reinterpret_cast<const float4 *>(a.res) + (size_t)((nchk - 1) & 1) * a.G;
                 const float2 tp = warp_sum_partial_ff(r4, a.G, 0);
                 const float2 td = warp_sum_partial_ff(r4, a.G, 1);
                 if (threadIdx.x == 0) {

@@ -95,10 +95,6 @@ static __device__ __forceinline__ float radius_disp(int type, float n, float p0)
 // variables.  Returns false when a poll ran out of time (the error word is
 // then set and the launch ends).
 // ---------------------------------------------------------------------------
-static __device__ __forceinline__ unsigned tile_count(unsigned long long diff) {
-    return (unsigned)(((diff + (1ull << 55)) >> 56) & 0xffull);
-}
-
 template <bool CHK, bool A1>
 static __device__ __forceinline__ bool tile_gather(const TileArgs &a, int nsv, const int4 *sv, const float *zden,
                                                    float *zt, float *zpt, float *yt, float *ypt,
