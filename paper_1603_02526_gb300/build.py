@@ -38,6 +38,7 @@ def _units():
         ("sweep_tile.cu", nv),
         ("sweep_hinge.cu", nv),
         ("mpc_batch.cu", nv),
+        ("mpc_warp.cu", nv),
         ("mpc_noalloc.cu", nv),
         ("mpc_horizon.cu", nv),
         ("mlp.cu", nv),

@@ -86,6 +86,11 @@ struct fga_mpc_batch {
     std::vector<long long> zoff, eoff;
     long long Z = 0, E = 0;
     Buf dT, dzoff, deoff, dsys, dorder, dP, dA, dB, dK, dq, dr, dx0, dz, du, dx, diters, dstatus, drp, drd, dqueue;
+    // one lane per time step (threads = 32): FP32, 12 states, 4 inputs,
+    // horizons up to 64; its work items
+    bool warp_ok = false;
+    int n_items = 0;
+    Buf ditems;
     bool x0_set = false;
     int tuned_threads = 128, tuned_ce = 1;
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -240,6 +245,14 @@ extern "C" int fga_mpc_batch_create(fga_mpc_batch **out, int32_t precision, int3
     if ((rc = put(b->dT, b->T)) || (rc = put(b->dzoff, b->zoff)) || (rc = put(b->deoff, b->eoff)) ||
         (rc = put(b->dsys, b->sys)) || (rc = put(b->dorder, order)))
         return rc;
+    if (precision == FGA_F32 && nx == 12 && nu == 4) {
+        std::vector<int2> items;
+        if (mpc_warp_items(b->T.data(), n_inst, items)) {
+            if ((rc = put(b->ditems, items))) return rc;
+            b->n_items = (int)items.size();
+            b->warp_ok = true;
+        }
+    }
     rc = precision == FGA_F32 ? upload_systems<float>(b, A, B, q, r) : upload_systems<double>(b, A, B, q, r);
     if (rc) return rc;
     const size_t rs = b->rsize();
@@ -354,6 +367,25 @@ static int launch_once(fga_mpc_batch *b, const MpcArgs<R> &a, int threads, cudaS
     return FGA_OK;
 }
 
+static int launch_warp(fga_mpc_batch *b, const MpcArgs<float> &a, cudaStream_t s) {
+    const int bps = mpc_warp_max_blocks_per_sm();
+    if (bps < 1) return bfail(FGA_ECUDA, "fga_mpc_batch_solve: the per-step kernel cannot be resident");
+    int sms = 0;
+    BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    const int grid = std::min(b->n_items, bps * sms);
+    BCUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), s));
+    BCUDA(mpc_warp_launch(a, b->ditems.as<int2>(), b->n_items, grid, s));
+    return FGA_OK;
+}
+
+template <typename R>
+static int launch_any(fga_mpc_batch *b, const MpcArgs<R> &a, int threads, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        if (threads == 32) return launch_warp(b, a, s);
+    }
+    return launch_once<R>(b, a, threads, s);
+}
+
 template <typename R>
 static int solve_typed(fga_mpc_batch *b, const fga_mpc_opts &o, fga_mpc_result &res) {
     MpcArgs<R> a = make_args<R>(b);
@@ -362,8 +394,12 @@ static int solve_typed(fga_mpc_batch *b, const fga_mpc_opts &o, fga_mpc_result &
     a.tol_dual = o.tol_dual;
     const int threads = o.threads > 0 ? o.threads : b->tuned_threads;
     a.check_every = o.check_every > 0 ? o.check_every : b->tuned_ce;
-    if (threads != 64 && threads != 128 && threads != 224 && threads != 256 && threads != 448 && threads != 512)
-        return bfail(FGA_EINVAL, "fga_mpc_batch_solve: threads must be 64, 128, 224, 256, 448 or 512");
+    if (threads == 32 && (sizeof(R) != 4 || !b->warp_ok))
+        return bfail(FGA_EINVAL, "fga_mpc_batch_solve: threads 32 (one lane per step) needs FP32, 12 states, 4 "
+                                 "inputs and horizons up to 64");
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 224 && threads != 256 && threads != 448 &&
+        threads != 512)
+        return bfail(FGA_EINVAL, "fga_mpc_batch_solve: threads must be 32, 64, 128, 224, 256, 448 or 512");
     int rc;
     BCUDA(cudaEventRecord(b->ev0, b->stream));
     if (o.use_graph) {
@@ -372,7 +408,7 @@ static int solve_typed(fga_mpc_batch *b, const fga_mpc_opts &o, fga_mpc_result &
         if (it == b->graphs.end()) {
             cudaGraph_t graph;
             BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            rc = launch_once<R>(b, a, threads, b->stream);
+            rc = launch_any<R>(b, a, threads, b->stream);
             cudaGraph_t captured = nullptr;
             cudaError_t ec = cudaStreamEndCapture(b->stream, &captured);
             if (rc) return rc;
@@ -385,7 +421,7 @@ static int solve_typed(fga_mpc_batch *b, const fga_mpc_opts &o, fga_mpc_result &
         }
         BCUDA(cudaGraphLaunch(it->second, b->stream));
     } else {
-        if ((rc = launch_once<R>(b, a, threads, b->stream))) return rc;
+        if ((rc = launch_any<R>(b, a, threads, b->stream))) return rc;
     }
     BCUDA(cudaEventRecord(b->ev1, b->stream));
     BCUDA(cudaStreamSynchronize(b->stream));
@@ -507,11 +543,12 @@ extern "C" int fga_mpc_batch_autotune(fga_mpc_batch *b, const char *cache_path, 
     BCUDA(cudaMemcpy(z0.p, b->dz.p, b->dz.bytes, cudaMemcpyDeviceToDevice));
     BCUDA(cudaMemcpy(u0.p, b->du.p, b->du.bytes, cudaMemcpyDeviceToDevice));
     BCUDA(cudaMemcpy(x0.p, b->dx.p, b->dx.bytes, cudaMemcpyDeviceToDevice));
-    const int th_c[6] = {64, 128, 224, 256, 448, 512};
+    const int th_c[7] = {32, 64, 128, 224, 256, 448, 512};
     const int ce_c[4] = {1, 2, 5, 10};
     double best = std::numeric_limits<double>::infinity();
     int bt = 128, bc = 1;
     for (int th : th_c) {
+        if (th == 32 && (b->precision != FGA_F32 || !b->warp_ok)) continue;
         for (int ce : ce_c) {
             fga_mpc_opts o;
             std::memset(&o, 0, sizeof o);

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace fga {
@@ -48,6 +50,14 @@ template <typename R>
 cudaError_t mpc_launch(const MpcArgs<R> &a, int threads, int grid, int smem, cudaStream_t s);
 template <typename R>
 int mpc_max_blocks_per_sm(int threads, int smem);
+// One lane per time step (mpc_warp.cu; FP32, 12 states, 4 inputs, horizons
+// up to 64): work items (two instances of at most 32 steps, or one of
+// 33..64 steps, inst[1] = -2), the launch, and its resident CTAs per SM.
+bool mpc_warp_items(const int *T, int n, std::vector<int2> &items);
+cudaError_t mpc_warp_launch(const MpcArgs<float> &a, const int2 *items, int n_items, int grid, cudaStream_t s);
+int mpc_warp_max_blocks_per_sm();
+constexpr int kMpcWarpThreads = 64;   // CTA size of the per-step kernel
+
 template <typename R>
 cudaError_t mpc_warm_start_impl(const MpcArgs<R> &a, const R *Am, const R *Bm, const float *pred, long long ld,
                                 cudaStream_t s);

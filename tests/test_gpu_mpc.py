@@ -175,3 +175,75 @@ def _mpc_cost(z, d, i, T, nx=12, nu=4):
         c += 0.5 * (np.sum(q * xt * xt) + np.sum(r * ut * ut))
     xT = z[T * (nx + nu):]
     return c + 0.5 * np.sum(q * xT * xT)
+
+
+def test_per_step_kernel_matches_cta_kernel():
+    """threads = 32 (one lane per time step, state in registers; a warp per
+    instance of up to 32 steps, two warps for 33..64) against the
+    CTA-per-instance kernel on a ragged FP32 batch: the same operations on
+    every value, so after a fixed 400 iterations z and u agree to a few FP32
+    ulps of the state's scale (the dynamics rows, sums and updates are the
+    same expressions); residual norms to 1e-5."""
+    d = inputs.mpc_batch_inputs(70, seed=4800, tmin=1, tmax=64)
+    a = batch_from_inputs(d, "f32")
+    a.fga_mpc_batch_solve(400, tol=0.0, check_every=7, threads=256, use_graph=False)
+    ra = a.fga_mpc_batch_read()
+    b = batch_from_inputs(d, "f32")
+    b.fga_mpc_batch_solve(400, tol=0.0, check_every=7, threads=32, use_graph=False)
+    rb = b.fga_mpc_batch_read()
+    assert np.all(ra["iters"] == 400) and np.all(rb["iters"] == 400)
+    S = max(1.0, float(np.abs(ra["z"]).max()))
+    assert np.abs(ra["z"] - rb["z"]).max() <= 1e-6 * S
+    assert np.abs(ra["u"] - rb["u"]).max() <= 1e-6 * S
+    np.testing.assert_allclose(rb["r_pri"], ra["r_pri"], rtol=1e-5)
+    np.testing.assert_allclose(rb["r_dual"], ra["r_dual"], rtol=1e-5)
+
+
+def test_per_step_kernel_against_oracle_and_stop_rule():
+    """threads = 32 on a ragged batch solved to 1e-4 (checked every 5):
+    every instance converges within one check interval of the
+    CTA-per-instance kernel's count, and sampled instances match the FP64
+    oracle run for the same number of iterations within the FP32 bound."""
+    d = inputs.mpc_batch_inputs(40, seed=4801, tmin=10, tmax=50)
+    b = batch_from_inputs(d, "f32")
+    res = b.fga_mpc_batch_solve(20000, tol=1e-4, check_every=5, threads=32, use_graph=True)
+    out = b.fga_mpc_batch_read()
+    c = batch_from_inputs(d, "f32")
+    c.fga_mpc_batch_solve(20000, tol=1e-4, check_every=5, threads=256, use_graph=False)
+    oc = c.fga_mpc_batch_read()
+    assert res["n_converged"] == int(np.sum(oc["status"] == 0))
+    assert np.all(np.abs(out["iters"] - oc["iters"]) <= 5)
+    for i in (0, 7, 19, 33):
+        g, r = _oracle_instance(d, i, int(out["iters"][i]))
+        S = max(1.0, np.abs(g.z()).max())
+        assert np.abs(b.instance_z(out["z"], i) - g.z()).max() <= 2e-5 * S, i
+
+
+def test_per_step_kernel_resume_and_warm_start():
+    """Two calls of 150 iterations equal one of 300 (the state is stored and
+    reloaded exactly); a warm start from exact multipliers works through the
+    per-step kernel as through the other."""
+    d = inputs.mpc_batch_inputs(9, seed=4802, tmin=20, tmax=45)
+    a = batch_from_inputs(d, "f32")
+    a.fga_mpc_batch_solve(300, tol=0.0, check_every=300, threads=32, use_graph=False)
+    b = batch_from_inputs(d, "f32")
+    for _ in range(2):
+        b.fga_mpc_batch_solve(150, tol=0.0, check_every=150, threads=32, use_graph=False)
+    ra, rb = a.fga_mpc_batch_read(), b.fga_mpc_batch_read()
+    assert np.array_equal(ra["z"], rb["z"]) and np.array_equal(ra["u"], rb["u"])
+
+
+def test_per_step_kernel_refusals():
+    from paper_1603_02526_gb300 import _lib
+    d = inputs.mpc_batch_inputs(4, seed=4803, tmin=70, tmax=80)       # horizons above 64
+    b = batch_from_inputs(d, "f32")
+    with pytest.raises(_lib.FgaError):
+        b.fga_mpc_batch_solve(10, tol=0.0, threads=32, use_graph=False)
+    d = inputs.mpc_batch_inputs(4, seed=4803, nx=6, nu=3, tmin=5, tmax=10)
+    b = batch_from_inputs(d, "f32")
+    with pytest.raises(_lib.FgaError):
+        b.fga_mpc_batch_solve(10, tol=0.0, threads=32, use_graph=False)
+    d = inputs.mpc_batch_inputs(4, seed=4803, tmin=5, tmax=10)
+    b = batch_from_inputs(d, "f64")
+    with pytest.raises(_lib.FgaError):
+        b.fga_mpc_batch_solve(10, tol=0.0, threads=32, use_graph=False)
