@@ -506,7 +506,7 @@ static std::string tune_key(const fga_mpc_batch *b, long long K, double tol) {
     cudaDeviceProp p;
     cudaGetDeviceProperties(&p, b->device);
     std::ostringstream k;
-    k << "v2|" << p.name << "|sm" << p.major << p.minor << "|p" << b->precision << "|nx" << b->nx << "|nu" << b->nu << "|n"
+    k << "v3|" << p.name << "|sm" << p.major << p.minor << "|p" << b->precision << "|nx" << b->nx << "|nu" << b->nu << "|n"
       << b->n << "|tmax" << b->tmax << "|sys" << b->nsys << "|K" << K << "|tol" << tol;
     std::string s = k.str();
     for (char &c : s)
@@ -535,14 +535,25 @@ extern "C" int fga_mpc_batch_autotune(fga_mpc_batch *b, const char *cache_path, 
         }
     }
     BCUDA(cudaSetDevice(b->device));
-    // keep the start point: every candidate starts from it
+    // keep the start point: every candidate starts from it.  The copies go
+    // on the batch's own stream (created non-blocking, so copies on the
+    // legacy stream would not be ordered before the candidate's kernel and
+    // a candidate could start from its predecessor's converged state).
     Buf z0, u0, x0;
     BCUDA(z0.alloc(b->dz.bytes));
     BCUDA(u0.alloc(b->du.bytes));
     BCUDA(x0.alloc(b->dx.bytes));
-    BCUDA(cudaMemcpy(z0.p, b->dz.p, b->dz.bytes, cudaMemcpyDeviceToDevice));
-    BCUDA(cudaMemcpy(u0.p, b->du.p, b->du.bytes, cudaMemcpyDeviceToDevice));
-    BCUDA(cudaMemcpy(x0.p, b->dx.p, b->dx.bytes, cudaMemcpyDeviceToDevice));
+    auto copy_state = [&](bool save) -> int {
+        const Buf *src[3] = {&b->dz, &b->du, &b->dx}, *dst[3] = {&z0, &u0, &x0};
+        for (int i = 0; i < 3; ++i) {
+            if (save) BCUDA(cudaMemcpyAsync(dst[i]->p, src[i]->p, src[i]->bytes, cudaMemcpyDeviceToDevice, b->stream));
+            else BCUDA(cudaMemcpyAsync(src[i]->p, dst[i]->p, src[i]->bytes, cudaMemcpyDeviceToDevice, b->stream));
+        }
+        BCUDA(cudaStreamSynchronize(b->stream));
+        return FGA_OK;
+    };
+    int rc;
+    if ((rc = copy_state(true))) return rc;
     const int th_c[7] = {32, 64, 128, 224, 256, 448, 512};
     const int ce_c[4] = {1, 2, 5, 10};
     double best = std::numeric_limits<double>::infinity();
@@ -558,25 +569,25 @@ extern "C" int fga_mpc_batch_autotune(fga_mpc_batch *b, const char *cache_path, 
             o.check_every = ce;
             o.use_graph = 0;
             double tbest = std::numeric_limits<double>::infinity();
+            bool finite = true;
             for (int rep = 0; rep < 2; ++rep) {
-                BCUDA(cudaMemcpy(b->dz.p, z0.p, b->dz.bytes, cudaMemcpyDeviceToDevice));
-                BCUDA(cudaMemcpy(b->du.p, u0.p, b->du.bytes, cudaMemcpyDeviceToDevice));
-                BCUDA(cudaMemcpy(b->dx.p, x0.p, b->dx.bytes, cudaMemcpyDeviceToDevice));
+                if ((rc = copy_state(false))) return rc;
                 fga_mpc_result r;
-                int rc = b->precision == FGA_F32 ? solve_typed<float>(b, o, r) : solve_typed<double>(b, o, r);
+                rc = b->precision == FGA_F32 ? solve_typed<float>(b, o, r) : solve_typed<double>(b, o, r);
                 if (rc) return rc;
                 tbest = std::min(tbest, (double)r.ms);
+                finite = finite && r.n_nonfinite == 0;
             }
-            if (tbest < best) {
+            // a candidate whose solve produced a non-finite instance is not
+            // a faster way to the same answer
+            if (finite && tbest < best) {
                 best = tbest;
                 bt = th;
                 bc = ce;
             }
         }
     }
-    BCUDA(cudaMemcpy(b->dz.p, z0.p, b->dz.bytes, cudaMemcpyDeviceToDevice));
-    BCUDA(cudaMemcpy(b->du.p, u0.p, b->du.bytes, cudaMemcpyDeviceToDevice));
-    BCUDA(cudaMemcpy(b->dx.p, x0.p, b->dx.bytes, cudaMemcpyDeviceToDevice));
+    if ((rc = copy_state(false))) return rc;
     b->tuned_threads = bt;
     b->tuned_ce = bc;
     if (cache_path) {

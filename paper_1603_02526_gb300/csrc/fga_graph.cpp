@@ -1685,6 +1685,9 @@ static int shard_begin_typed(fga_graph *g, const double *srho, const double *srh
     if ((rc = upload_vec(g->srho2, v2))) return rc;
     CUDA_TRY(g->shard_res.alloc(kShardZGrid * sizeof(double)));
     CUDA_TRY(cudaMemset(g->ctl.p, 0, sizeof(Ctl)));
+    // the uploads and the memset ran on the legacy stream, which a
+    // non-blocking caller stream does not wait for
+    CUDA_TRY(cudaDeviceSynchronize());
     return FGA_OK;
 }
 

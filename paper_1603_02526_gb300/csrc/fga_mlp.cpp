@@ -53,6 +53,14 @@ struct DBuf {
     T *as() const { return static_cast<T *>(p); }
 };
 
+// A host-to-device copy on the MLP's stream, finished before the host buffer
+// can go away (a copy on the legacy stream would not be ordered before the
+// kernels of a non-blocking stream).
+static cudaError_t h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+
 // splitmix64 -> uniform (0, 1) -> standard normal (Box-Muller)
 struct Rng {
     uint64_t s;
@@ -157,10 +165,10 @@ extern "C" int fga_mlp_create(fga_mlp **outp, int32_t in, int32_t h1, int32_t h2
         const double sd = std::sqrt(2.0 / dims[li][1]);
         for (int r = 0; r < l.rows; ++r)
             for (int c = 0; c < dims[li][1]; ++c) w[(size_t)r * l.cols + c] = (float)(sd * rng.normal());
-        MCUDA(cudaMemcpy(l.w.p, w.data(), w.size() * 4, cudaMemcpyHostToDevice));
+        MCUDA(h2d(l.w.p, w.data(), w.size() * 4, m->stream));
     }
     std::vector<float> ones((size_t)out, 1.f);
-    MCUDA(cudaMemcpy(m->stdv.p, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice));
+    MCUDA(h2d(m->stdv.p, ones.data(), ones.size() * 4, m->stream));
     if ((rc = refresh_bf16(m.get()))) return rc;
     MCUDA(cudaDeviceSynchronize());
     *outp = m.release();
@@ -188,9 +196,9 @@ static int copy_params(fga_mlp *m, float *host, bool to_device, bool grads) {
                 if (to_device) w[(size_t)r * l.cols + c] = host[off + (size_t)r * in_cols[li] + c];
                 else host[off + (size_t)r * in_cols[li] + c] = w[(size_t)r * l.cols + c];
             }
-        if (to_device) MCUDA(cudaMemcpy(dw, w.data(), w.size() * 4, cudaMemcpyHostToDevice));
+        if (to_device) MCUDA(h2d(dw, w.data(), w.size() * 4, m->stream));
         off += (size_t)l.rows * in_cols[li];
-        if (to_device) MCUDA(cudaMemcpy(db, host + off, (size_t)l.rows * 4, cudaMemcpyHostToDevice));
+        if (to_device) MCUDA(h2d(db, host + off, (size_t)l.rows * 4, m->stream));
         else MCUDA(cudaMemcpy(host + off, db, (size_t)l.rows * 4, cudaMemcpyDeviceToHost));
         off += l.rows;
     }
@@ -231,6 +239,8 @@ extern "C" int fga_mlp_fit_normalization(fga_mlp *m, float *Y, int64_t rows) {
 
 extern "C" int fga_mlp_get_normalization(fga_mlp *m, float *mean, float *stdv) {
     if (!m) return mfail(FGA_EINVAL, "fga_mlp_get_normalization: NULL");
+    MCUDA(cudaSetDevice(m->device));
+    MCUDA(cudaStreamSynchronize(m->stream));
     if (mean) MCUDA(cudaMemcpy(mean, m->mean.p, (size_t)m->out * 4, cudaMemcpyDeviceToHost));
     if (stdv) MCUDA(cudaMemcpy(stdv, m->stdv.p, (size_t)m->out * 4, cudaMemcpyDeviceToHost));
     return FGA_OK;
@@ -251,7 +261,8 @@ static int check_gemm_err(fga_mlp *m) {
     int h = 0;
     MCUDA(cudaMemcpy(&h, m->err.p, sizeof h, cudaMemcpyDeviceToHost));
     if (h) {
-        MCUDA(cudaMemset(m->err.p, 0, sizeof(int)));
+        MCUDA(cudaMemsetAsync(m->err.p, 0, sizeof(int), m->stream));
+        MCUDA(cudaStreamSynchronize(m->stream));
         return mfail(FGA_ETIMEOUT, "MLP GEMM: a tensor-core wait timed out; outputs are not valid");
     }
     return FGA_OK;

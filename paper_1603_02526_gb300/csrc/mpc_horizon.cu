@@ -470,6 +470,9 @@ extern "C" int fga_horizon_create(fga_horizon **out, int32_t K, int32_t nx, int3
         cudaMemcpy(h->x0.p, x0f.data(), x0f.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
         return bad(hfail(FGA_ECUDA, "fga_horizon_create: upload"));
+    // the uploads ran on the legacy stream, which the solver's non-blocking
+    // stream does not wait for
+    if (cudaDeviceSynchronize() != cudaSuccess) return bad(hfail(FGA_ECUDA, "fga_horizon_create: upload"));
     *out = h;
     return FGA_OK;
 }
