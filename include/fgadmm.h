@@ -115,9 +115,25 @@ extern "C" {
                                  slice of the data rows in shared memory and
                                  one value of state per hinge factor in
                                  registers, one grid-wide barrier per
-                                 iteration; fused launches only.  Default: 0
-                                 for FGA_F64; for FGA_F32, 2 or 3 when the
-                                 graph qualifies, else 1.  Asking for 2 or 3
+                                 iteration; fused launches only; 4 =
+                                 scatter: each edge's rho*m goes straight to
+                                 a per-variable column (the variable's k-th
+                                 edge in creation order to column k < W, W
+                                 <= 15 chosen at fga_finalize from the
+                                 degrees) or past the columns to the
+                                 variable's overflow row; z sums the columns
+                                 in column order (for a variable of degree
+                                 <= W the serial creation-order sum, as in
+                                 0), then the overflow row by a warp tree
+                                 (hub rows in pieces); items are grid-wide,
+                                 factor-major, no chunks -- for graphs of
+                                 low-degree variables; fewer than 2^28
+                                 scalar variables.  Default: 0 for FGA_F64;
+                                 for FGA_F32, 2 or 3 when the graph
+                                 qualifies, else 4 when at least three
+                                 quarters of the edges fit in the columns
+                                 and the columns hold at most twice the
+                                 edges, else 1.  Asking for 2 or 3
                                  on a graph that does not qualify makes
                                  fga_finalize return FGA_EINVAL.             */
 #define FGA_OPT_STORE_M 1     /* 1 = keep m per edge so FGA_EDGE_M can be read
@@ -234,7 +250,8 @@ int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result
 /* Launch configuration chosen at fga_finalize, for reports: info[0] CTAs,
  * info[1] threads per CTA, info[2] dynamic shared memory per CTA (bytes),
  * info[3] co-resident CTAs per SM, info[4] work chunks (fast z-order), disk
- * tiles (tile order) or 0 (canonical order), info[5] type buckets, and when
+ * tiles (tile order), hinge-bank CTAs (hinge order), columns W (scatter
+ * order) or 0 (canonical order), info[5] type buckets, and when
  * n >= 7 info[6] the z-order in use (FGA_OPT_ZORDER values).  n >= 6. */
 int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n);
 

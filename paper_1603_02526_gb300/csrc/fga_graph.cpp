@@ -141,6 +141,11 @@ struct fga_graph {
     int n_small = 0, n_witems = 0, n_hubs = 0;
     DevBuf chunks, slot_var, ppos, lrow, lidx, part, prow;
     int nchunks = 0, smem = 0, bps = 0, kind = 0;
+    // scatter order (zorder 4): per-edge variable | column words, the
+    // overflow flags per variable, the column count and overflow entries
+    DevBuf d_ev, zovf;
+    int colw = 0;
+    int64_t novf = 0;
     // disk-tile order (zorder 2): the plan and its device copies
     TilePlan tile;
     DevBuf t_cta, t_rowslot, t_colslot, t_mask, t_sv, t_zden, t_cptr, t_clist, t_loc, t_part, t_res, t_dsave;
@@ -247,7 +252,7 @@ extern "C" int fga_set_option(fga_graph *g, int32_t option, int64_t value) {
     if (g->finalized) return fail(FGA_ESTATE, "fga_set_option: graph already finalized");
     switch (option) {
     case FGA_OPT_ZORDER:
-        if (value < 0 || value > 3) return fail(FGA_EINVAL, "FGA_OPT_ZORDER must be 0, 1, 2 or 3");
+        if (value < 0 || value > 4) return fail(FGA_EINVAL, "FGA_OPT_ZORDER must be 0, 1, 2, 3 or 4");
         g->zorder = (int)value;
         return FGA_OK;
     case FGA_OPT_STORE_M:
@@ -417,6 +422,10 @@ struct FastLayout {
     std::vector<ChunkDev> chunks;
     std::vector<int32_t> slot_var, ppos, lrow, prow;
     std::vector<uint32_t> lidx;   // slot | padded buffer position << 16
+    // scatter order: per storage edge variable | column << kEvColShift, and
+    // per variable 1 when it has an overflow row (rows in prow)
+    std::vector<uint32_t> ev;
+    std::vector<unsigned char> zovf;
 };
 
 template <typename R>
@@ -506,6 +515,16 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
                 if ((rc = upload_vec(g->prho, pr))) return rc;
             }
         }
+    } else if (g->zorder == 4) {
+        // scatter order: per-edge words, overflow positions and rows, the
+        // zeroed column table (entries past a variable's degree stay 0)
+        if ((rc = upload_vec(g->d_ev, fl.ev))) return rc;
+        if ((rc = upload_vec(g->d_pos, pos))) return rc;
+        if ((rc = upload_vec(g->prow, fl.prow))) return rc;
+        if ((rc = upload_vec(g->zovf, fl.zovf))) return rc;
+        const size_t pb = (size_t)std::max<int64_t>((int64_t)g->colw * g->nz + g->novf, 1) * sizeof(R);
+        CUDA_TRY(g->pvm.alloc(pb));
+        CUDA_TRY(cudaMemset(g->pvm.p, 0, pb));
     } else {
         if ((rc = upload_vec(g->chunks, fl.chunks))) return rc;
         if ((rc = upload_vec(g->slot_var, fl.slot_var))) return rc;
@@ -709,14 +728,17 @@ static int build_chunks(fga_graph *g, FastLayout &fl, int64_t items_per_chunk) {
 
 // Work lists of the fast z-update over rows `rowp`: low-degree rows one
 // thread each, others one warp each, hub rows split into kPiece pieces.
-static int build_zlists(fga_graph *g, const std::vector<int32_t> &rowp) {
+// Scatter order (overflow = true): only the overflow rows, each a warp item
+// or hub pieces (the columns are summed one thread per variable).
+static int build_zlists(fga_graph *g, const std::vector<int32_t> &rowp, bool overflow) {
     int rc;
     std::vector<int32_t> small, hub_np, hub_off;
     std::vector<int4> witems, med;
     int off = 0;
     for (int64_t b = 0; b < g->nz; ++b) {
         const int deg = rowp[b + 1] - rowp[b];
-        if (deg <= kSmallDeg) {
+        if (overflow && deg == 0) continue;
+        if (!overflow && deg <= kSmallDeg) {
             small.push_back((int32_t)b);
         } else if (deg <= kPiece) {
             med.push_back(make_int4((int)b, rowp[b], deg, -1));
@@ -910,6 +932,36 @@ static int try_hinge_plan(fga_graph *g, std::string &why) {
     return rc;
 }
 
+// Scatter order: the number of columns W (1..kColMax) for the degrees of
+// the scalar variables, the one that minimises the values phase Z reads
+// (W per variable) plus twice the overflow entries (each also costs a
+// position read and a warp item); returns the overflow entry count.
+static int64_t choose_columns(const std::vector<int32_t> &deg, int &W) {
+    std::vector<int64_t> cnt((size_t)kColMax + 1, 0);
+    int64_t big_n = 0, big_sum = 0;
+    for (int32_t d : deg) {
+        if (d <= kColMax) cnt[d]++;
+        else {
+            big_n++;
+            big_sum += d;
+        }
+    }
+    const int64_t nz = (int64_t)deg.size();
+    int64_t best = -1, best_ovf = 0;
+    W = 1;
+    for (int w = 1; w <= kColMax; ++w) {
+        int64_t ovf = big_sum - big_n * w;
+        for (int d = w + 1; d <= kColMax; ++d) ovf += cnt[d] * (d - w);
+        const int64_t cost = (int64_t)w * nz + 2 * ovf;
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_ovf = ovf;
+            W = w;
+        }
+    }
+    return best_ovf;
+}
+
 extern "C" int fga_finalize(fga_graph *g) {
     if (!g) return fail(FGA_EINVAL, "fga_finalize: NULL graph");
     if (g->finalized) return fail(FGA_ESTATE, "fga_finalize: graph already finalized");
@@ -983,6 +1035,33 @@ extern "C" int fga_finalize(fga_graph *g) {
     }
     if (zreq == 3 && g->precision != FGA_F32)
         return fail(FGA_EINVAL, "fga_finalize: FGA_OPT_ZORDER 3 (hinge bank) needs FGA_F32");
+    // 1a''. scatter order: per-variable columns when most edges fit in them
+    // (FP32 default over the chunked order for graphs of low-degree
+    // variables) or when asked
+    if (zreq == 4 || (zreq < 0 && g->zorder == 1)) {
+        std::vector<int32_t> deg((size_t)g->nz, 0);
+        for (const FactorBatch &b : g->batches)
+            for (int64_t f = 0; f < b.count; ++f)
+                for (int v = 0; v < b.nv; ++v) {
+                    const int64_t var = b.vars[f * b.nv + v];
+                    for (int d = 0; d < b.dims[v]; ++d) deg[(size_t)(g->voff[var] + d)]++;
+                }
+        int W = 1;
+        const int64_t ovf = choose_columns(deg, W);
+        const bool fits = g->nz < (int64_t)kEvVarMask && (int64_t)W * g->nz + ovf < (int64_t)UINT32_MAX;
+        if (zreq == 4 && !fits)
+            return fail(FGA_EINVAL, "fga_finalize: the scatter order (FGA_OPT_ZORDER 4) takes fewer than 2^28 "
+                                    "scalar variables and 2^32 column entries");
+        if (zreq == 4 || (fits && 4 * ovf <= g->ne && (int64_t)W * g->nz <= 2 * g->ne)) {
+            g->zorder = 4;
+            g->colw = W;
+            g->novf = ovf;
+        }
+    }
+    // the scatter order stores every bucket factor-major (consecutive work
+    // items touch consecutive components of a variable block)
+    if (g->zorder == 4)
+        for (Bucket &bk : g->buckets) bk.aos = true;
     const bool tile = g->zorder == 2;
     const bool hinge = g->zorder == 3;
     const int64_t tile_span = (int64_t)g->tile.U * kUnitEdges;
@@ -1079,12 +1158,44 @@ extern "C" int fga_finalize(fga_graph *g) {
         srho_d[b] += r;        // sequential, ascending creation order
         srho2_d[b] += r * r;
     }
-    // 4. fast z-order: chunks, their slots, and the variable-major partials
+    // 3a. scatter order: an edge of rank k (creation order) in its
+    // variable's row goes to column k while k < W, else to the variable's
+    // overflow row (its position there replaces pos)
     FastLayout fl;
+    if (g->zorder == 4) {
+        const int W = g->colw;
+        try {
+            fl.ev.assign((size_t)es, 0u);
+            fl.prow.assign((size_t)Z + 1, 0);
+            fl.zovf.assign((size_t)std::max<int64_t>(Z, 1), 0);
+        } catch (...) {
+            return fail(FGA_ENOMEM, "fga_finalize: out of host memory");
+        }
+        for (int64_t b = 0; b < Z; ++b) {
+            const int d = rowp[b + 1] - rowp[b];
+            fl.prow[b + 1] = fl.prow[b] + std::max(0, d - W);
+            fl.zovf[b] = d > W ? 1 : 0;
+        }
+        if ((int64_t)fl.prow[Z] != g->novf) return fail(FGA_EINVAL, "fga_finalize: scatter layout mismatch");
+        for (int64_t s = 0; s < es; ++s) {
+            if (g->s2c[s] < 0) continue;
+            const int32_t b = g->svar[s];
+            const int k = pos[s] - rowp[b];
+            if (k < W) {
+                fl.ev[s] = (uint32_t)b | ((uint32_t)k << kEvColShift);
+            } else {
+                fl.ev[s] = (uint32_t)b | (kEvOverflow << kEvColShift);
+                pos[s] = fl.prow[b] + (k - W);
+            }
+        }
+    }
+    // 4. fast z-order: chunks, their slots, and the variable-major partials
     int dev_sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device));
     g->blk = g->block ? g->block : 256;
-    g->smem = g->zorder == 1 ? chunk_smem((int)g->rsize()).total : canonical_z_smem((int)g->rsize());
+    g->smem = g->zorder == 1   ? chunk_smem((int)g->rsize()).total
+              : g->zorder == 4 ? 0
+                               : canonical_z_smem((int)g->rsize());
     // kernel variant: 1 = neither hinge / dynamics nor margin / equality
     // paths, 2 = margin / equality paths only, 3 = dynamics of at most 9
     // edges and elementwise paths, 0 = every path
@@ -1096,6 +1207,7 @@ extern "C" int fga_finalize(fga_graph *g) {
         me = me || bk.type == FGA_SVM_MARGIN || bk.type == FGA_EQUAL;
     }
     g->kind = (has_hinge || dyn_big || (dyn && me)) ? 0 : dyn ? 3 : me ? 2 : 1;
+    if (g->zorder == 4) g->kind |= kKindScatter;
     if (tile) {
         g->blk = g->tile.W * 32;
         g->smem = tile_smem_bytes(g->tile);
@@ -1132,7 +1244,9 @@ extern "C" int fga_finalize(fga_graph *g) {
         while (per < kChunkItems && count_chunks(per) > full) per += 2 * std::max<int64_t>(1, per / 128);
         per = std::min<int64_t>(kChunkItems, per);
         if ((rc = build_chunks(g, fl, per))) return rc;
-        if ((rc = build_zlists(g, fl.prow))) return rc;
+        if ((rc = build_zlists(g, fl.prow, false))) return rc;
+    } else if (g->zorder == 4) {
+        if ((rc = build_zlists(g, fl.prow, true))) return rc;
     }
     // 5. upload
     rc = g->precision == FGA_F32 ? finalize_typed<float>(g, pos, rowp, srho_d, srho2_d, fl)
@@ -1329,6 +1443,10 @@ static void fill_args(const fga_graph *g, SweepArgs<R> &a) {
     a.part = g->part.as<R>();
     a.prow = g->prow.as<int>();
     a.zorder = g->zorder;
+    a.ev = g->zorder == 4 ? g->d_ev.as<unsigned>() : nullptr;
+    a.ovf0 = (unsigned)((int64_t)g->colw * g->nz);
+    a.colw = g->colw;
+    a.zovf = g->zovf.as<unsigned char>();
     a.n_small = g->n_small;
     a.small_vars = g->small_vars.as<int>();
     a.n_witems = g->n_witems;
@@ -1847,7 +1965,11 @@ extern "C" int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n) {
     info[1] = g->blk;
     info[2] = g->smem;
     info[3] = g->bps;
-    info[4] = g->zorder == 1 ? g->nchunks : g->zorder == 2 ? g->tile.U : g->zorder == 3 ? g->hinge.G : 0;
+    info[4] = g->zorder == 1   ? g->nchunks
+              : g->zorder == 2 ? g->tile.U
+              : g->zorder == 3 ? g->hinge.G
+              : g->zorder == 4 ? g->colw
+                               : 0;
     info[5] = (int64_t)g->buckets.size();
     if (n >= 7) info[6] = g->zorder;
     return FGA_OK;

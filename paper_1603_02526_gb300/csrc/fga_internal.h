@@ -15,6 +15,18 @@ constexpr int kChunkSlots = 1024;   // fast z-order: distinct scalar variables p
 constexpr int kStagePairs = 128;    // fast z-order: disk pairs per bulk-copy stage
 constexpr int kChunkItems = 2048;   // fast z-order: work items per chunk (upper limit)
 constexpr int kLocalityBlock = 96;  // fast z-order: factors are sorted by (first, last) variable / this
+// Scatter z-order: per edge one word, its scalar variable | its column << 28;
+// columns 0..kColMax-1 hold a variable's first edges (in creation order),
+// column kEvOverflow marks an edge of the variable's overflow row.
+constexpr int kColMax = 15;
+// Kernel variant ("kind"): the factor types it is compiled for (bits 0-2,
+// see process_in_bucket) and the scatter order (kKindScatter).
+constexpr int kKindScatter = 8;
+inline __host__ __device__ constexpr int kind_types(int kind) { return kind & 7; }
+inline __host__ __device__ constexpr bool kind_scatter(int kind) { return (kind & kKindScatter) != 0; }
+constexpr unsigned kEvColShift = 28;
+constexpr unsigned kEvVarMask = (1u << kEvColShift) - 1u;
+constexpr unsigned kEvOverflow = 15u;
 
 // Shared-memory layout of one CTA in the fast z-order (byte offsets):
 // rho*m buffer (padded slot segments), z per slot, slot row starts, slot
@@ -147,11 +159,22 @@ struct SweepArgs {
     R *part;                      // per-slot partial sums, variable-major
     const int *prow;              // variable-major row pointers of part [nz + 1]
 
+    // scatter z-order (zorder 4): per edge its variable and column (ev,
+    // see kEvColShift), the edge's overflow position in pos when its column
+    // is kEvOverflow; pvm holds colw columns of nz values (column c of
+    // variable b at c * nz + b, zero past the variable's degree) and the
+    // overflow rows from ovf0 on (row pointers in prow); zovf[b] = 1 when
+    // variable b has an overflow row (its z is formed by the warp items)
+    const unsigned *ev;
+    unsigned ovf0;
+    int colw;
+    const unsigned char *zovf;
+
     // z-update work lists
-    int zorder;           // 0 canonical, 1 fast
+    int zorder;           // 0 canonical, 1 fast, 4 scatter
     int n_small;          // fast: variables reduced by one thread
     const int *small_vars;
-    int n_witems;         // fast: warp work items (var, start, len, hub or -1)
+    int n_witems;         // fast / scatter: warp work items (var, start, len, hub or -1)
     const int4 *witems;
     const int *hub_npieces;
     const int *hub_off;

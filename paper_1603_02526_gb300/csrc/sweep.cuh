@@ -311,21 +311,39 @@ __device__ __forceinline__ R edge_rho(const SweepArgs<R> &a, int e) {
     return a.rho_e ? a.rho_e[e] : a.rho_u;
 }
 
+// The z order an edge access is compiled for (the FAST template argument of
+// the functions below): canonical rows, fast-order chunks, scatter columns.
+enum EdgeOrder : int { EO_CANON = 0, EO_CHUNK = 1, EO_SCATTER = 2 };
+
+// Where the rho*m of edge e goes in pvm outside the fast order: its slot in
+// the variable-major rows (canonical), or its column or overflow slot
+// (scatter); returns the edge's scalar variable.
+template <typename R, int FAST>
+__device__ __forceinline__ int edge_dest(const SweepArgs<R> &a, int e, unsigned &dst) {
+    if constexpr (FAST == EO_SCATTER) {
+        const unsigned v = a.ev[e];
+        const unsigned c = v >> kEvColShift, b = v & kEvVarMask;
+        dst = c != kEvOverflow ? c * (unsigned)a.nz + b : a.ovf0 + (unsigned)a.pos[e];
+        return (int)b;
+    }
+    dst = (unsigned)a.pos[e];
+    return a.svar[e];
+}
+
 // z at the far end of edge e; `ix` receives what edge_put needs later.
-template <typename R, bool FAST>
+template <typename R, int FAST>
 __device__ __forceinline__ R edge_z(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, unsigned &ix) {
-    if (FAST) {
+    if constexpr (FAST == EO_CHUNK) {
         ix = a.lidx[e];
         return io.zl[ix & 0xffffu];
     }
-    ix = (unsigned)e;
-    return ldg_l2(io.zc + a.svar[e]);
+    return ldg_l2(io.zc + edge_dest<R, FAST>(a, e, ix));
 }
 
-template <typename R, bool FAST>
+template <typename R, int FAST>
 __device__ __forceinline__ void edge_put(const SweepArgs<R> &a, const EdgeIO<R> &io, unsigned ix, R p) {
-    if (FAST) io.pb[ix >> 16] = p;
-    else a.pvm[a.pos[ix]] = p;
+    if constexpr (FAST == EO_CHUNK) io.pb[ix >> 16] = p;
+    else a.pvm[ix] = p;
 }
 
 // Deferred u-update of the previous iteration (when MODE != F_PROX) and the
@@ -376,7 +394,7 @@ __device__ __forceinline__ void twa_mark(const SweepArgs<R> &a, const BucketDev<
 
 // One scalar edge, start of phase F: returns n; u holds the updated u
 // (already stored when MODE != F_PROX).
-template <typename R, int MODE, bool FAST>
+template <typename R, int MODE, int FAST>
 __device__ __forceinline__ R edge_pre(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, R &u, unsigned &ix,
                                       double &pri) {
     const R z = edge_z<R, FAST>(a, io, e, ix);
@@ -388,7 +406,7 @@ __device__ __forceinline__ R edge_pre(const SweepArgs<R> &a, const EdgeIO<R> &io
 }
 
 // One scalar edge, end of phase F: x, m = x + u, rho*m to the z-reduction.
-template <typename R, bool FAST>
+template <typename R, int FAST>
 __device__ __forceinline__ void edge_post(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, unsigned ix, R x, R u) {
     io.xout[e] = x;
     const R m = x + u;
@@ -426,7 +444,7 @@ template <> struct Vec2<double> { using T = double2; };
 // ---------------------------------------------------------------------------
 // per-type work items
 // ---------------------------------------------------------------------------
-template <typename R, int MODE, bool FAST>
+template <typename R, int MODE, int FAST>
 __device__ __forceinline__ void item_pack_pair(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                int f, double &pri) {
     using V = typename Vec2<R>::T;
@@ -435,18 +453,22 @@ __device__ __forceinline__ void item_pack_pair(const SweepArgs<R> &a, const Buck
     unsigned ix[6];
     load6<R, V>(a.u + e0, u);
     if (MODE != F_PROX) load6<R, V>(io.xin + e0, xo);
-    if (FAST) {
+    if constexpr (FAST == EO_CHUNK) {
         load6<unsigned, uint2>(a.lidx + e0, ix);
         #pragma unroll
         for (int k = 0; k < 6; ++k) z[k] = io.zl[ix[k] & 0xffffu];
-    } else {
-        int sv[6];
+    } else if constexpr (FAST == EO_CANON) {
+        int sv[6], ps[6];
         load6<int, int2>(a.svar + e0, sv);
+        load6<int, int2>(a.pos + e0, ps);
         #pragma unroll
         for (int k = 0; k < 6; ++k) {
             z[k] = ldg_l2(io.zc + sv[k]);
-            ix[k] = (unsigned)(e0 + k);
+            ix[k] = (unsigned)ps[k];
         }
+    } else {
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) z[k] = edge_z<R, FAST>(a, io, e0 + k, ix[k]);
     }
     if (a.rho_e) load6<R, V>(a.rho_e + e0, rho);
     else {
@@ -504,7 +526,7 @@ __device__ __forceinline__ void item_pack_pair_staged(const SweepArgs<R> &a, con
     for (int k = 0; k < 6; ++k) m[k] = x[k] + u[k];
     if (io.mout) store6<R, V>(io.mout + e0, m);
     #pragma unroll
-    for (int k = 0; k < 6; ++k) edge_put<R, true>(a, io, ix[k], rho[k] * m[k]);
+    for (int k = 0; k < 6; ++k) edge_put<R, EO_CHUNK>(a, io, ix[k], rho[k] * m[k]);
 }
 
 // Bounded wait on a stage barrier; false (and the grid's error word set)
@@ -520,7 +542,7 @@ static __device__ __forceinline__ bool stage_wait(unsigned long long *bar, unsig
     return false;
 }
 
-template <typename R, int MODE, bool FAST>
+template <typename R, int MODE, int FAST>
 __device__ __forceinline__ void item_pack_wall(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                int f, double &pri) {
     R n[3], u[3], rho[3];
@@ -545,7 +567,7 @@ __device__ __forceinline__ void item_pack_wall(const SweepArgs<R> &a, const Buck
 // two passes over the factor's edges (the first computes the margin in the
 // order of a serial loop, the second writes x).  Parameters factor-major:
 // p[f*(D+2) + j] = x_j, then y, c.
-template <typename R, int MODE, bool FAST>
+template <typename R, int MODE, int FAST>
 __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                int f, double &pri) {
     const int D = B.arity - 1;
@@ -591,11 +613,11 @@ __device__ __forceinline__ void item_svm_hinge(const SweepArgs<R> &a, const Buck
     }
 }
 
-// The same operator with one warp per factor (fast order): lane l owns the
+// The same operator with one warp per factor (fast and scatter orders): lane l owns the
 // edges j = l, l + 32, ...; the margin and the weight sum are reduced with a
 // fixed shuffle tree; one pass, the factor's edges and data point read
 // contiguously (factor-major storage).
-template <typename R, int MODE>
+template <typename R, int MODE, int FAST = EO_CHUNK>
 __device__ __forceinline__ void item_svm_hinge_warp(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                     int f, double &pri) {
     constexpr int JMAX = 4;   // up to 128 edges per factor kept in registers
@@ -611,7 +633,7 @@ __device__ __forceinline__ void item_svm_hinge_warp(const SweepArgs<R> &a, const
         const int j = lane + 32 * q;
         if (j > D) continue;
         const int e = e0 + j;
-        n[q] = edge_pre<R, MODE, true>(a, io, e, u[q], ix[q], pri);
+        n[q] = edge_pre<R, MODE, FAST>(a, io, e, u[q], ix[q], pri);
         rho[q] = edge_rho(a, e);
         xi[q] = j < D ? p[j] : R(1);
         dot += n[q] * xi[q];
@@ -637,7 +659,7 @@ __device__ __forceinline__ void item_svm_hinge_warp(const SweepArgs<R> &a, const
         const int j = lane + 32 * q;
         if (j > D) continue;
         const R x = n[q] + (gy * xi[q]) / rho[q];
-        edge_post<R, true>(a, io, e0 + j, ix[q], x, u[q]);
+        edge_post<R, FAST>(a, io, e0 + j, ix[q], x, u[q]);
     }
 }
 
@@ -648,7 +670,7 @@ __device__ __forceinline__ void item_svm_hinge_warp(const SweepArgs<R> &a, const
 // passes over the factor's edges (the first forms a.n and the weight sum in
 // the order of a serial loop, the second writes x).  Parameters
 // factor-major: p[f*(D+1) + j] = x_j, then y.
-template <typename R, int MODE, bool FAST>
+template <typename R, int MODE, int FAST>
 __device__ __forceinline__ void item_svm_margin(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                 int f, double &pri) {
     const int D = B.arity - 2;
@@ -677,11 +699,11 @@ __device__ __forceinline__ void item_svm_margin(const SweepArgs<R> &a, const Buc
     }
 }
 
-// The margin operator with one warp per factor (fast order): lane l owns
+// The margin operator with one warp per factor (fast and scatter orders): lane l owns
 // the edges j = l, l + 32, ...; a.n and the weight sum are reduced with a
 // fixed shuffle tree; one pass, the factor's edges and data point read
 // contiguously (factor-major storage).
-template <typename R, int MODE>
+template <typename R, int MODE, int FAST = EO_CHUNK>
 __device__ __forceinline__ void item_svm_margin_warp(const SweepArgs<R> &a, const BucketDev<R> &B,
                                                      const EdgeIO<R> &io, int f, double &pri) {
     constexpr int JMAX = 4;   // up to 128 edges per factor kept in registers
@@ -698,7 +720,7 @@ __device__ __forceinline__ void item_svm_margin_warp(const SweepArgs<R> &a, cons
         const int j = lane + 32 * q;
         if (j > D + 1) continue;
         const int e = e0 + j;
-        n[q] = edge_pre<R, MODE, true>(a, io, e, u[q], ix[q], pri);
+        n[q] = edge_pre<R, MODE, FAST>(a, io, e, u[q], ix[q], pri);
         rho[q] = edge_rho(a, e);
         av[q] = j < D ? y * p[j] : (j == D ? y : R(1));
         an += av[q] * n[q];
@@ -716,19 +738,21 @@ __device__ __forceinline__ void item_svm_margin_warp(const SweepArgs<R> &a, cons
     for (int q = 0; q < JMAX; ++q) {
         const int j = lane + 32 * q;
         if (j > D + 1) continue;
-        edge_post<R, true>(a, io, e0 + j, ix[q], n[q] + (lam * av[q]) / rho[q], u[q]);
+        edge_post<R, FAST>(a, io, e0 + j, ix[q], n[q] + (lam * av[q]) / rho[q], u[q]);
     }
 }
 
 // Appendix C equality of two copies v1, v2 in R^D: both become the
 // rho-weighted mean of the two messages, component by component.  One work
-// item per component pair, li = j * nf + f, edge-major storage (the pairs
-// of consecutive items sit side by side).
-template <typename R, int MODE, bool FAST>
+// item per component pair: li = j * nf + f with edge-major storage (the
+// pairs of consecutive items sit side by side), li = f * D + j with
+// factor-major storage (scatter order: consecutive items take consecutive
+// components of one copy).
+template <typename R, int MODE, int FAST>
 __device__ __forceinline__ void item_equal(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io, int li,
                                            double &pri) {
     const int D = B.arity >> 1;
-    const int j = li / B.nf, f = li - j * B.nf;
+    const int j = B.aos ? li % D : li / B.nf, f = B.aos ? li / D : li - j * B.nf;
     const int e1 = bedge(B, f, j), e2 = bedge(B, f, D + j);
     R u1, u2;
     unsigned i1, i2;
@@ -745,7 +769,7 @@ __device__ __forceinline__ void item_equal(const SweepArgs<R> &a, const BucketDe
 // {x' = A x + B u}, precomputed per distinct (A, B, rho).  AC = compile-time
 // arity (n kept in registers), or 0 for any arity (n re-formed from u and z
 // for each output row).
-template <typename R, int MODE, bool FAST, int AC>
+template <typename R, int MODE, int FAST, int AC>
 __device__ __forceinline__ void item_mpc_dyn(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                              int f, double &pri) {
     if constexpr (AC > 0) {
@@ -785,9 +809,11 @@ __device__ __forceinline__ void item_mpc_dyn(const SweepArgs<R> &a, const Bucket
     }
 }
 
-// Elementwise types: one work item per scalar edge, edge-major storage
-// (li = k * nf + f).
-template <typename R, int MODE, bool FAST>
+// Elementwise types: one work item per scalar edge, item li at storage
+// edge ebase + li: component k of factor f at li = k * nf + f (edge-major)
+// or li = f * arity + k (factor-major, scatter order).  Parameters SoA:
+// prm[j * nf + f]; per-component parameters at j = k.
+template <typename R, int MODE, int FAST>
 __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                  int li, double &pri) {
     const int e = B.ebase + li;
@@ -795,7 +821,8 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
     unsigned ix;
     const R n = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
     if (MODE == F_U_ONLY) return;
-    const int f = li % B.nf;
+    const int f = B.aos ? li / B.arity : li % B.nf;
+    const int pk = B.aos ? (li - f * B.arity) * B.nf + f : li;   // per-component parameter index
     const R rho = edge_rho(a, e);
     R x;
     switch (B.type) {
@@ -809,7 +836,7 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
         x = (rho * n) / (rho + B.prm[f]);
         break;
     case 7:  // MPC_QUAD: f = 1/2 q v^2, q per scalar component
-        x = (rho * n) / (B.prm[li] + rho);
+        x = (rho * n) / (B.prm[pk] + rho);
         break;
     case 8: {  // MPC_BOX
         const R lo = B.prm[f], hi = B.prm[B.nf + f];
@@ -824,7 +851,7 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
         break;
     }
     default:  // 9, FIX
-        x = B.prm[li];
+        x = B.prm[pk];
         break;
     }
     edge_post<R, FAST>(a, io, e, ix, x, u);
@@ -838,7 +865,7 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
 // 28-edge dynamics path the kernel needs fewer registers and fits 4 CTAs
 // per SM.  Each kernel is compiled without the paths its graphs lack, so
 // that their register demand does not limit it.
-template <typename R, int MODE, bool FAST, int KIND>
+template <typename R, int MODE, int FAST, int KIND>
 __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                   int li, double &pri) {
     switch (B.type) {
@@ -888,14 +915,36 @@ __device__ __forceinline__ void issue_pair_stage(const SweepArgs<R> &a, const Ed
 // rho*m lands in shared memory sorted by slot, and each slot's sum over the
 // chunk (edges in slot order) is written to the variable-major partial
 // array.  Both orders are deterministic.
-template <typename R, int MODE, int KIND>
+template <typename R, int MODE, int KIND_>
 __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, double &pri) {
+    constexpr int KIND = kind_types(KIND_);
+    if constexpr (kind_scatter(KIND_)) {
+        // scatter order: bucket after bucket over the whole grid, each
+        // edge's rho*m straight to its column (or overflow slot); hinge and
+        // margin factors one warp each, every other item one thread
+        const int gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+        const int wid = gtid >> 5, nw = stride >> 5;
+        for (int b = 0; b < a.nb; ++b) {
+            const BucketDev<R> &B = a.bk[b];
+            if (KIND == 0 && B.type == 4 && B.arity <= 128) {
+                for (int i = wid; i < B.nitems; i += nw)
+                    item_svm_hinge_warp<R, MODE, EO_SCATTER>(a, B, io, i, pri);
+            } else if ((KIND == 0 || KIND == 2) && B.type == 10 && B.arity >= 16 && B.arity <= 128) {
+                for (int i = wid; i < B.nitems; i += nw)
+                    item_svm_margin_warp<R, MODE, EO_SCATTER>(a, B, io, i, pri);
+            } else {
+                for (int i = gtid; i < B.nitems; i += stride)
+                    process_in_bucket<R, MODE, EO_SCATTER, KIND>(a, B, io, i, pri);
+            }
+        }
+        return;
+    }
     if (a.zorder == 0) {
         const int stride = gridDim.x * blockDim.x;
         for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < a.nitems_f; it += stride) {
             int b = 0;
             while (b + 1 < a.nb && it >= a.bk[b + 1].item0) ++b;
-            process_in_bucket<R, MODE, false, KIND>(a, a.bk[b], io, it - a.bk[b].item0, pri);
+            process_in_bucket<R, MODE, EO_CANON, KIND>(a, a.bk[b], io, it - a.bk[b].item0, pri);
             if (MODE != F_U_ONLY && a.wcls) twa_mark<R>(a, a.bk[b], io, it - a.bk[b].item0);
         }
         return;
@@ -973,7 +1022,7 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, dou
             for (int i = warp; i < ch.nitems; i += nwarps) item_svm_margin_warp<R, MODE>(a, B, io, f0 + i, pri);
         } else {
             for (int i = threadIdx.x; i < ch.nitems; i += blockDim.x)
-                process_in_bucket<R, MODE, true, KIND>(a, B, io, f0 + i, pri);
+                process_in_bucket<R, MODE, EO_CHUNK, KIND>(a, B, io, f0 + i, pri);
         }
         __syncthreads();
         if (MODE != F_U_ONLY) {
@@ -1028,7 +1077,7 @@ __device__ __forceinline__ R shard_start(const R *s_in, long long b) {
     return R(0);
 }
 
-template <typename R, bool CHK, bool SHARD = false>
+template <typename R, bool CHK, bool SHARD = false, bool SCAT = false>
 __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *zn, double &dual,
                                         const R *s_in = nullptr, R *s_out = nullptr) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1041,7 +1090,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         if constexpr (SHARD) s_out[b] = s_in ? s_in[b] + S : S;
         else z_store<R, CHK>(a, b, S, zo, zn, dual);
     };
-    if (!SHARD && a.zorder == 0 && a.wcls) {
+    if (!SCAT && !SHARD && a.zorder == 0 && a.wcls) {
         // canonical, three weights: per variable, in creation order, the
         // infinite-weight messages (m), the others (rho m) and among them
         // the standard ones; z from the first non-empty group
@@ -1076,7 +1125,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         }
         return;
     }
-    if (a.zorder == 0) {
+    if (!SCAT && a.zorder == 0) {
         // canonical.  Rows of at most kZShort values: one thread per
         // variable over the whole grid, its values added one by one in
         // creation order straight from the variable-major array.
@@ -1137,10 +1186,28 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         }
         return;
     }
-    // fast: sums of the chunk partials, row by row (variable-major)
-    const R *src = a.part;
+    // scatter order: a variable's columns, added in column (= creation)
+    // order; the loads of all columns are issued before the additions
+    constexpr bool scat = SCAT;
+    auto colsum = [&](int b) {
+        R v[kColMax];
+        #pragma unroll
+        for (int c = 0; c < kColMax; ++c) v[c] = c < a.colw ? ldg_l2(a.pvm + (size_t)c * a.nz + b) : R(0);
+        R S = R(0);
+        #pragma unroll
+        for (int c = 0; c < kColMax; ++c)
+            if (c < a.colw) S += v[c];
+        return S;
+    };
+    if constexpr (scat) {
+        for (long long b = gtid; b < a.nz; b += gstride)
+            if (!a.zovf[b]) finish_sum((int)b, colsum((int)b));
+    }
+    // fast: sums of the chunk partials, row by row (variable-major); scatter:
+    // the overflow rows, the columns added first
+    const R *src = scat ? a.pvm + a.ovf0 : a.part;
     const int *row = a.prow;
-    // low-degree variables one thread each ...
+    // low-degree variables one thread each (fast order; none in scatter) ...
     for (long long i = gtid; i < a.n_small; i += gstride) {
         const int b = a.small_vars[i];
         R S = R(0);
@@ -1158,7 +1225,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
         if (wi.w < 0) {
-            if (lane == 0) finish_sum(wi.x, S);
+            if (lane == 0) finish_sum(wi.x, scat ? colsum(wi.x) + S : S);
             continue;
         }
         const int h = wi.w;
@@ -1179,7 +1246,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
             for (int o = 16; o > 0; o >>= 1) T += __shfl_xor_sync(0xffffffffu, T, o);
             if (lane == 0) {
                 a.hub_ticket[h] = 0u;
-                finish_sum(wi.x, T);
+                finish_sum(wi.x, scat ? colsum(wi.x) + T : T);
             }
         }
     }
@@ -1254,7 +1321,9 @@ __device__ __forceinline__ EdgeIO<R> make_io(const SweepArgs<R> &a, int xp, int 
 // the persistent kernel: a whole call in one launch
 // ---------------------------------------------------------------------------
 template <typename R, int KIND>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 && (KIND == 1 || KIND == 3)) ? 4 : 3) k_sweep_persistent(const SweepArgs<R> a) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && (kind_types(KIND) == 1 || kind_types(KIND) == 3)) ? 4 : 3)
+    k_sweep_persistent(const SweepArgs<R> a) {
+    constexpr bool SCAT = kind_scatter(KIND);
     unsigned int gen = 0;
     const unsigned int G = gridDim.x;
     bool skip = (a.skip_block == (int)blockIdx.x);
@@ -1283,8 +1352,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && (KIND == 1 || KIND == 
         xp ^= 1;
         const bool chkz = ((a.k0 + it) % a.check_every == 0) || it == a.K;
         double dual = 0.0;
-        if (chkz) phase_z<R, true>(a, a.z[zp], a.z[zp ^ 1], dual);
-        else phase_z<R, false>(a, a.z[zp], a.z[zp ^ 1], dual);
+        if (chkz) phase_z<R, true, false, SCAT>(a, a.z[zp], a.z[zp ^ 1], dual);
+        else phase_z<R, false, false, SCAT>(a, a.z[zp], a.z[zp ^ 1], dual);
         if (chkz) {
             const double s = block_sum(dual);
             if (threadIdx.x == 0) a.res_dual[(long long)(it & 1) * a.gmax + blockIdx.x] = s;
@@ -1320,12 +1389,12 @@ __global__ void __launch_bounds__(256) k_phase_f(const SweepArgs<R> a, int xp, i
     }
 }
 
-template <typename R>
+template <typename R, bool SCAT>
 __global__ void __launch_bounds__(256) k_phase_z(const SweepArgs<R> a, int zp, long long it, int chk) {
     if (*(volatile int *)&a.ctl->done) return;
     double dual = 0.0;
-    if (chk) phase_z<R, true>(a, a.z[zp], a.z[zp ^ 1], dual);
-    else phase_z<R, false>(a, a.z[zp], a.z[zp ^ 1], dual);
+    if (chk) phase_z<R, true, false, SCAT>(a, a.z[zp], a.z[zp ^ 1], dual);
+    else phase_z<R, false, false, SCAT>(a, a.z[zp], a.z[zp ^ 1], dual);
     if (chk) {
         const double s = block_sum(dual);
         if (threadIdx.x == 0) a.res_dual[(long long)(it & 1) * a.gmax + blockIdx.x] = s;

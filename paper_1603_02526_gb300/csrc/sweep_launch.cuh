@@ -31,18 +31,30 @@ static cudaError_t allow_smem_k(int smem) {
 
 template <typename R>
 static cudaError_t allow_smem(int smem, int kind) {
-    return kind == 1   ? allow_smem_k<R, 1>(smem)
-           : kind == 2 ? allow_smem_k<R, 2>(smem)
-           : kind == 3 ? allow_smem_k<R, 3>(smem)
-                       : allow_smem_k<R, 0>(smem);
+    switch (kind) {
+    case 1: return allow_smem_k<R, 1>(smem);
+    case 2: return allow_smem_k<R, 2>(smem);
+    case 3: return allow_smem_k<R, 3>(smem);
+    case kKindScatter + 0: return allow_smem_k<R, kKindScatter + 0>(smem);
+    case kKindScatter + 1: return allow_smem_k<R, kKindScatter + 1>(smem);
+    case kKindScatter + 2: return allow_smem_k<R, kKindScatter + 2>(smem);
+    case kKindScatter + 3: return allow_smem_k<R, kKindScatter + 3>(smem);
+    default: return allow_smem_k<R, 0>(smem);
+    }
 }
 
 template <typename R>
 static const void *persistent_fn(int kind) {
-    return kind == 1   ? (const void *)k_sweep_persistent<R, 1>
-           : kind == 2 ? (const void *)k_sweep_persistent<R, 2>
-           : kind == 3 ? (const void *)k_sweep_persistent<R, 3>
-                       : (const void *)k_sweep_persistent<R, 0>;
+    switch (kind) {
+    case 1: return (const void *)k_sweep_persistent<R, 1>;
+    case 2: return (const void *)k_sweep_persistent<R, 2>;
+    case 3: return (const void *)k_sweep_persistent<R, 3>;
+    case kKindScatter + 0: return (const void *)k_sweep_persistent<R, kKindScatter + 0>;
+    case kKindScatter + 1: return (const void *)k_sweep_persistent<R, kKindScatter + 1>;
+    case kKindScatter + 2: return (const void *)k_sweep_persistent<R, kKindScatter + 2>;
+    case kKindScatter + 3: return (const void *)k_sweep_persistent<R, kKindScatter + 3>;
+    default: return (const void *)k_sweep_persistent<R, 0>;
+    }
 }
 
 template <typename R>
@@ -70,17 +82,24 @@ cudaError_t sweep_phase_f(const SweepArgs<R> &a, int mode, int xp, int zp, int g
                           cudaStream_t s) {
     cudaError_t e = allow_smem<R>(smem, kind);
     if (e != cudaSuccess) return e;
-    if (kind == 1) phase_f_k<R, 1>(a, mode, xp, zp, grid, block, smem, s);
-    else if (kind == 2) phase_f_k<R, 2>(a, mode, xp, zp, grid, block, smem, s);
-    else if (kind == 3) phase_f_k<R, 3>(a, mode, xp, zp, grid, block, smem, s);
-    else phase_f_k<R, 0>(a, mode, xp, zp, grid, block, smem, s);
+    switch (kind) {
+    case 1: phase_f_k<R, 1>(a, mode, xp, zp, grid, block, smem, s); break;
+    case 2: phase_f_k<R, 2>(a, mode, xp, zp, grid, block, smem, s); break;
+    case 3: phase_f_k<R, 3>(a, mode, xp, zp, grid, block, smem, s); break;
+    case kKindScatter + 0: phase_f_k<R, kKindScatter + 0>(a, mode, xp, zp, grid, block, smem, s); break;
+    case kKindScatter + 1: phase_f_k<R, kKindScatter + 1>(a, mode, xp, zp, grid, block, smem, s); break;
+    case kKindScatter + 2: phase_f_k<R, kKindScatter + 2>(a, mode, xp, zp, grid, block, smem, s); break;
+    case kKindScatter + 3: phase_f_k<R, kKindScatter + 3>(a, mode, xp, zp, grid, block, smem, s); break;
+    default: phase_f_k<R, 0>(a, mode, xp, zp, grid, block, smem, s); break;
+    }
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t sweep_phase_z(const SweepArgs<R> &a, int zp, long long it, int chk, int grid, int block,
                           cudaStream_t s) {
-    k_phase_z<R><<<grid, block, a.zorder == 0 ? canonical_z_smem((int)sizeof(R)) : 0, s>>>(a, zp, it, chk);
+    if (a.zorder == 4) k_phase_z<R, true><<<grid, block, 0, s>>>(a, zp, it, chk);
+    else k_phase_z<R, false><<<grid, block, a.zorder == 0 ? canonical_z_smem((int)sizeof(R)) : 0, s>>>(a, zp, it, chk);
     return cudaGetLastError();
 }
 

@@ -79,7 +79,7 @@ def test_validation_errors(lib):
     assert lib.fga_set_rho_alpha(g, 2.0, 1.0) == 0
     # options: bad values
     assert lib.fga_set_option(g, 2, 100) == FGA_EINVAL
-    assert lib.fga_set_option(g, 0, 4) == FGA_EINVAL
+    assert lib.fga_set_option(g, 0, 5) == FGA_EINVAL
     assert lib.fga_set_option(g, 0, -1) == FGA_EINVAL
     assert lib.fga_set_option(g, 0, 1) == 0
     # calls that need a finalized / initialised graph

@@ -6,7 +6,9 @@ FP64 runs use the canonical z order and must match the oracle to 1e-9
 relative per message (floor 1e-3 of the array's scale): the z sums are the
 oracle's, but the dynamics operator is applied here as a precomputed
 projection matrix and in the oracle by a Cholesky solve per call, which
-round differently (a few ulps per iteration, not amplified).  FP32 runs use the fast order.  Tolerance: one iteration rounds each message
+round differently (a few ulps per iteration, not amplified).  FP32 runs
+use the chunked fast order here (the scatter order, the FP32 default for
+this graph, has its own tests with the same bounds).  Tolerance: one iteration rounds each message
 by a few FP32 ulps of the variables' scale S (the dynamics operator is a
 9-term dot product: at most about 9 * 2^-24 * S = 5.4e-7 S); the method on
 this convex problem does not amplify earlier errors (each iteration is a
@@ -47,11 +49,11 @@ def test_horizon_f64(fused):
 
 
 @pytest.mark.parametrize("K", [1, 37, 500])
-def test_horizon_f32_fast_order(K):
+def test_horizon_f32_chunked_order(K):
     """FP32 fast order, 300 iterations, every message within the bound of
     the module docstring (300 iterations: 1.6e-4 S)."""
     p = inputs.mpc_horizon_problem(K)
-    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1})
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1, _lib.FGA_OPT_ZORDER: 1})
     g.fga_iterate(300)
     o = oracle_from_problem(p)
     o.iterate(300)
@@ -70,7 +72,7 @@ def test_horizon_full_size_f64_and_f32():
     g.fga_iterate(20)
     assert_messages_match(g, o, 1e-9)
     del g
-    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1})
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1, _lib.FGA_OPT_ZORDER: 1})
     g.fga_iterate(20)
     assert_messages_close_scaled(g, o, 20 * F32_PER_ITER)
 
@@ -102,8 +104,9 @@ def test_horizon_converges_to_lqr():
     np.testing.assert_allclose(us, np.array(ul), atol=1e-6)
 
 
-def test_horizon_full_size_f32_stop_rule():
-    """K = 10^5 in FP32 to residual 1e-5 (checked every 10; 1e-4 is met
+@pytest.mark.parametrize("zorder", [1, 4])
+def test_horizon_full_size_f32_stop_rule(zorder):
+    """K = 10^5 in FP32 (chunked and scatter orders) to residual 1e-5 (checked every 10; 1e-4 is met
     after about 10 iterations, the RMS running over 1.4M edges of which most
     stay near zero): the stop is
     reported with both residuals at or below the tolerance, the primal
@@ -113,7 +116,7 @@ def test_horizon_full_size_f32_stop_rule():
     <= (1 + |A| + |B|) r_pri, about 2.4 r_pri)."""
     K = 100000
     p = inputs.mpc_horizon_problem(K)
-    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1})
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1, _lib.FGA_OPT_ZORDER: zorder})
     r = g.fga_iterate(50000, 1e-5, 1e-5, check_every=10)
     assert r["status"] == 0 and r["iters"] % 10 == 0 and r["iters"] > 100
     assert r["r_pri"] <= 1e-5 and r["r_dual"] <= 1e-5

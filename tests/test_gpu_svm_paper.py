@@ -5,8 +5,9 @@ oracle, through the C-ABI.
 
 FP64 runs use the canonical z order; the margin, slack and equality
 operators take the same operations in the same order as the oracle's, so
-every message must equal the oracle's bit for bit.  FP32 runs use the fast
-order.  Tolerance: one iteration rounds a message by a few FP32 ulps of the
+every message must equal the oracle's bit for bit.  FP32 runs use the
+chunked fast order here (the scatter order, the FP32 default for this graph,
+has its own tests with the same bound).  Tolerance: one iteration rounds a message by a few FP32 ulps of the
 variables' scale S, the largest term being the margin's dot product over
 D + 2 edges with data values of magnitude up to about 4: about
 4 (D + 2) 2^-24 S; the method on this convex problem does not amplify
@@ -56,11 +57,11 @@ def test_svm_paper_f64_bit_exact(fused):
 
 
 @pytest.mark.parametrize("npts,d", [(1, 2), (37, 5), (500, 3)])
-def test_svm_paper_f32_fast_order(npts, d):
+def test_svm_paper_f32_chunked_order(npts, d):
     """FP32 fast order, 300 iterations, every message within the module
     docstring's bound; N = 1 has no equality factor."""
     p = inputs.svm_paper_problem(npts, d, seed=3200 + npts, C=1.0)
-    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1})
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1, _lib.FGA_OPT_ZORDER: 1})
     g.fga_iterate(300)
     o = oracle_from_problem(p)
     o.iterate(300)
@@ -79,7 +80,7 @@ def test_svm_paper_full_size():
     assert np.array_equal(g.fga_read_z(), o.z())
     _edges_equal(g, o)
     del g
-    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1})
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 1, _lib.FGA_OPT_ZORDER: 1})
     g.fga_iterate(3)
     assert_messages_close_scaled(g, o, _f32_bound(64, 3))
 
