@@ -37,6 +37,10 @@
  *     sqrt(sum_e rho_e^2 (z_b - z_b_prev)^2 / |E|), evaluated after the
  *     n-update of every check_every-th iteration; stop at the first checked
  *     iteration where both are <= their tolerances.
+ *   - User-supplied operators (og_register_prox): the paper's addNode
+ *     takes each factor's proximal operator as a function pointer
+ *     (Sec. III); the x-update calls it with the factor's messages, weights
+ *     and parameters in creation order.
  *   - Prox formulas: Appendix A (packing), B (MPC), C (SVM), re-derived
  *     where the printed form has sign or term errors; see each function.
  */
@@ -64,6 +68,17 @@ enum {
 };
 
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ESTATE = -4, OR_ENONFINITE = -6 };
+
+/* User-supplied operators.  The paper's addNode receives each factor's
+ * proximal operator as a function pointer (Sec. III); og_register_prox does
+ * the same here.  fn(arity, n, rho, params, x, ctx) must write
+ * x = Prox_{f,rho}(n) (Eq. PO) for one factor: n and rho hold the factor's
+ * arity scalar edges in creation order (its variables in the order given,
+ * each variable's components in order), params its np parameters.  Types are
+ * numbered from OT_USER0 in registration order, per graph. */
+typedef void (*og_prox_fn)(int32_t arity, const double *n, const double *rho, const double *params, double *x,
+                           void *ctx);
+enum { OT_USER0 = 64, OG_MAX_USER = 16 };
 
 typedef struct {
     int32_t type;
@@ -105,6 +120,11 @@ typedef struct og_graph {
      * (each x-update gives each edge a weight class, see twa_classes) */
     int weights;
     int8_t *cls;         /* [ne] weight class of each edge's last message     */
+    /* user-supplied operators, type OT_USER0 + k */
+    int32_t nuser;
+    og_prox_fn ufn[OG_MAX_USER];
+    void *uctx[OG_MAX_USER];
+    int32_t uarity[OG_MAX_USER], unp[OG_MAX_USER];
 } og_graph;
 
 /* Weight classes of a message (three-weight reading, see og_set_weights). */
@@ -202,6 +222,28 @@ static int expected_params(int32_t type, int32_t nv, const int32_t *dims, int32_
     }
 }
 
+/* Registers a user-supplied operator for factors of `arity` scalar edges and
+ * `np` parameters each; returns its type number (OT_USER0 + k) or -1. */
+int32_t og_register_prox(og_graph *g, og_prox_fn fn, void *ctx, int32_t arity, int32_t np)
+{
+    if (g->finalized || !fn || arity < 1 || np < 0 || g->nuser == OG_MAX_USER) return -1;
+    const int32_t k = g->nuser++;
+    g->ufn[k] = fn;
+    g->uctx[k] = ctx;
+    g->uarity[k] = arity;
+    g->unp[k] = np;
+    return OT_USER0 + k;
+}
+
+/* Parameters of a user type for a factor of `arity` scalar edges (-1 if the
+ * type is not registered or the arity differs from the registered one). */
+static int user_params(const og_graph *g, int32_t type, int32_t arity)
+{
+    const int32_t k = type - OT_USER0;
+    if (k < 0 || k >= g->nuser || g->uarity[k] != arity) return -1;
+    return g->unp[k];
+}
+
 /* Adds `count` factors of one type.  vars: count*nv variable ids; params:
  * count*np values.  Edges are numbered in call order.  Returns the first
  * factor id or -1. */
@@ -219,7 +261,8 @@ int64_t og_add_factors(og_graph *g, int32_t type, int64_t count, int32_t nv,
             dims[k] = g->vdim[v];
             arity += dims[k];
         }
-        if (expected_params(type, nv, dims, arity) != np) return -1;
+        const int want = type >= OT_USER0 ? user_params(g, type, arity) : expected_params(type, nv, dims, arity);
+        if (want != np) return -1;
         if (grow((void **)&g->fac, &g->cap_fac, g->nfac + 1, sizeof(ofactor))) return -1;
         if (grow((void **)&g->fvars, &g->cap_fvars, g->nfvars + nv, sizeof(int64_t))) return -1;
         if (grow((void **)&g->params, &g->cap_params, g->nparams + np, sizeof(double))) return -1;
@@ -632,6 +675,12 @@ int og_prox(int32_t type, int32_t nv, const int32_t *dims, const double *params,
 
 static int factor_prox(og_graph *g, const ofactor *f)
 {
+    if (f->type >= OT_USER0) {
+        /* the user's operator, through its function pointer */
+        const int32_t k = f->type - OT_USER0;
+        g->ufn[k](f->arity, g->n + f->edge0, g->rho + f->edge0, g->params + f->par0, g->x + f->edge0, g->uctx[k]);
+        return OR_OK;
+    }
     int32_t dims[64];
     for (int32_t k = 0; k < f->nv; ++k) dims[k] = g->vdim[g->fvars[f->var0 + k]];
     return og_prox(f->type, f->nv, dims, g->params + f->par0, g->rho + f->edge0,

@@ -37,6 +37,7 @@ T_FIX = 9
 T_SVM_MARGIN = 10
 T_SVM_SLACK = 11
 T_EQUAL = 12
+T_USER0 = 64   # first type number of user-supplied operators (og_register_prox)
 
 EDGE_X, EDGE_M, EDGE_U, EDGE_N = 0, 1, 2, 3
 
@@ -122,7 +123,14 @@ def _declare(lib):
     lib.og_get_edge_var.argtypes = [P, lp]
     lib.og_prox.argtypes = [i32, i32, ip, dp, dp, dp, dp]
     lib.og_set_weights.argtypes = [P, i32]
+    lib.og_register_prox.argtypes = [P, PROX_FN, P, i32, i32]
+    lib.og_register_prox.restype = i32
     return lib
+
+
+# og_prox_fn: (arity, n, rho, params, x, ctx), see og_register_prox
+PROX_FN = ctypes.CFUNCTYPE(None, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
 def _dp(a):
@@ -155,6 +163,7 @@ class OracleGraph:
         self._lib = _load()
         self._g = self._lib.og_new()
         self.finalized = False
+        self._callbacks = []   # user operators: kept alive as long as the graph
 
     def __del__(self):
         try:
@@ -169,6 +178,26 @@ class OracleGraph:
         if r < 0:
             raise ValueError("oracle: bad variables")
         return r
+
+    def register_prox(self, fn, arity, n_params):
+        """Registers a user-supplied proximal operator (the paper's addNode
+        takes it as a function pointer, Sec. III): fn(n, rho, params) returns
+        x = Prox_{f,rho}(n) for one factor, all FP64 arrays (n and rho of
+        length `arity` in creation order, params of length `n_params`).
+        Returns the new type number (T_USER0, T_USER0 + 1, ...)."""
+        def call(arity_c, n, rho, prm, x, ctx):
+            nn = np.ctypeslib.as_array(n, shape=(arity_c,)).copy()
+            rr = np.ctypeslib.as_array(rho, shape=(arity_c,)).copy()
+            pp = (np.ctypeslib.as_array(prm, shape=(n_params,)).copy() if n_params
+                  else np.zeros(0))
+            np.ctypeslib.as_array(x, shape=(arity_c,))[:] = np.asarray(fn(nn, rr, pp), dtype=np.float64)
+
+        cb = PROX_FN(call)
+        t = self._lib.og_register_prox(self._g, cb, None, int(arity), int(n_params))
+        if t < 0:
+            raise ValueError("oracle: operator not registered")
+        self._callbacks.append(cb)
+        return t
 
     def add_factors(self, ftype, var_ids, params=None):
         """var_ids: (count, nv) ids; params: (count, np), or (np,) shared by all."""

@@ -9,6 +9,7 @@ from oracle import oracle as orc
 from tests import test_oracle_alg as alg
 from tests import test_oracle_prox as prox
 from tests import test_oracle_twa as twa
+from tests import test_oracle_user as usr
 
 # (name, exact source text, replacement, pins that must catch it)
 MUTANTS = [
@@ -63,6 +64,14 @@ MUTANTS = [
      "g->cls[e] == OW_STD ? g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]]) : 0.0",
      "g->u[e] + g->alpha[e] * (g->x[e] - g->z[g->ez[e]])",
      [(twa.test_inactive_box_by_hand, {}), (twa.test_infinite_weight_decides_z, {})]),
+    ("user operator given the first factor's parameters",
+     "g->params + f->par0, g->x + f->edge0, g->uctx[k]", "g->params, g->x + f->edge0, g->uctx[k]",
+     [(usr.test_operator_sees_its_messages_in_creation_order, {})]
+     + [(usr.test_user_lasso_converges_to_the_closed_form, dict(seed=s)) for s in (1, 2, 3)]),
+    ("user operator given the first edges' rho",
+     "g->ufn[k](f->arity, g->n + f->edge0, g->rho + f->edge0,", "g->ufn[k](f->arity, g->n + f->edge0, g->rho,",
+     [(usr.test_operator_sees_its_messages_in_creation_order, {}),
+      (usr.test_user_operators_restating_builtins_match_bit_for_bit, {})]),
 ]
 
 
