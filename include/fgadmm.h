@@ -88,6 +88,9 @@ extern "C" {
 #define FGA_EQUAL 12          /* (v1:D, v2:D) ; 0 ; indicator of v1 = v2
                                  (Appendix C, equality of two copies)         */
 #define FGA_NUM_TYPES 13
+#define FGA_USER_TYPE0 64     /* first type number returned by
+                                 fga_register_prox (user-supplied operators,
+                                 numbered in registration order per graph)   */
 
 /* ---- edge arrays for readout ------------------------------------------- */
 #define FGA_EDGE_X 0
@@ -185,6 +188,36 @@ int fga_add_variables(fga_graph *g, int64_t count, int32_t dim, int64_t *first_v
 int fga_add_factors(fga_graph *g, int32_t type, int64_t count, int32_t n_vars_per_factor,
                     const int64_t *var_ids, const double *params, int32_t params_per_factor,
                     int32_t params_shared, int64_t *first_factor_id);
+
+/* Registers a user-supplied proximal operator as a new factor type (the
+ * paper's addNode takes the operator of a factor as a function pointer,
+ * Sec. III; a GPU cannot call host code, so here it is CUDA source).
+ *   cuda_source: NUL-terminated CUDA C++ that defines a function template
+ *     template <typename R>
+ *     void function_name(int arity, const R *n, const R *rho, const R *params, R *x);
+ *   which must write x = argmin_s f(s) + sum_k rho_k/2 (s_k - n_k)^2
+ *   (Eq. PO) for one factor: n, rho and x hold the factor's `arity` scalar
+ *   edges in creation order (its variables in the order given to
+ *   fga_add_factors, each variable's components in order; x holds n on
+ *   entry), params its params_per_factor values (R = float for FGA_F32
+ *   graphs, double for FGA_F64).  Functions need no __device__ mark; the
+ *   CUDA math functions are available; no headers are included.
+ *   arity: 1..64 scalar edges per factor; params_per_factor: 0..4096.
+ * The source is compiled at once for the graph's device with NVRTC (FP64
+ * graphs without multiply-add contraction, so that an operator written
+ * the same way as a host implementation gives the same bits; IEEE division
+ * and square root in both precisions).  *type_out gets the type number
+ * (FGA_USER_TYPE0 + k) to pass to fga_add_factors; every factor of that type
+ * must have `arity` scalar edges and params_per_factor parameters.
+ * Before fga_finalize.  Errors: FGA_EINVAL with the compiler's log in
+ * fga_last_error() when the source does not compile or the name is not a C
+ * identifier; FGA_ECUDA when NVRTC (libnvrtc.so.13) cannot be opened.
+ * A graph with user types runs in the canonical or scatter z-order
+ * (FGA_OPT_ZORDER 0 or 4, the library's choice by default), with fixed
+ * weights, one launch per update phase whatever fga_iter_opts.fused says
+ * (each user type has its own x-update kernel), and not as a shard. */
+int fga_register_prox(fga_graph *g, const char *cuda_source, const char *function_name, int32_t arity,
+                      int32_t params_per_factor, int32_t *type_out);
 
 /* Uniform rho > 0 and alpha > 0 on every edge (default 1, 1).  Before
  * fga_finalize. */

@@ -29,6 +29,7 @@ FGA_F32 = 0
 FGA_F64 = 1
 FGA_EDGE_X, FGA_EDGE_M, FGA_EDGE_U, FGA_EDGE_N = 0, 1, 2, 3
 FGA_OPT_ZORDER, FGA_OPT_STORE_M, FGA_OPT_BLOCK, FGA_OPT_WEIGHTS = 0, 1, 2, 3
+FGA_USER_TYPE0 = 64
 
 
 class FgaError(RuntimeError):
@@ -73,6 +74,7 @@ def _declare(lib):
         "fga_set_option": [P, i32, i64],
         "fga_add_variables": [P, i64, i32, pi64],
         "fga_add_factors": [P, i32, i64, i32, P, P, i32, i32, pi64],
+        "fga_register_prox": [P, ctypes.c_char_p, ctypes.c_char_p, i32, i32, ctypes.POINTER(ctypes.c_int32)],
         "fga_set_rho_alpha": [P, dbl, dbl],
         "fga_set_edge_rho_alpha": [P, P, P],
         "fga_finalize": [P],

@@ -47,6 +47,7 @@ def _units():
         ("fga_hinge.cpp", None),
         ("fga_batch.cpp", None),
         ("fga_mlp.cpp", None),
+        ("fga_user.cpp", None),
     ]
     return [(s, f) for s, f in units if os.path.exists(os.path.join(CSRC, s))]
 
@@ -92,7 +93,7 @@ def build(force=False, verbose=False):
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("libfgadmm build failed:\n" + msg)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    link = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs
+    link = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-ldl"]
     if verbose:
         print(" ".join(link), file=sys.stderr)
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)

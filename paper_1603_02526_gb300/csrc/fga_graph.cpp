@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <limits>
@@ -19,6 +20,7 @@
 #include "fga_host.h"
 #include "tile_internal.h"
 #include "hinge_internal.h"
+#include "user_internal.h"
 
 using namespace fga;
 
@@ -105,6 +107,14 @@ struct Bucket {
     int64_t ebase = 0, item0 = 0, nitems = 0;
     bool per_edge = false;
     bool aos = false;      // factor-major storage of the bucket's edges
+    int prm_buf = -1;      // its parameters in bucket_bufs
+};
+
+// A bucket of a user-supplied operator: per edge (factor-major) its scalar
+// variable and the slot of its rho m in the z-reduction's input.
+struct UserBucket {
+    int bucket = 0, user = 0;
+    DevBuf var, dst;
 };
 
 struct fga_graph {
@@ -166,6 +176,10 @@ struct fga_graph {
     int weights = 0;
     DevBuf wcls, pwcls, prho;
     DevBuf shard_res;   // per-CTA dual partials of the z-step (fixed grid: equal on every rank)
+    // user-supplied operators (fga_register_prox) and their buckets
+    std::vector<UserProg> users;
+    std::vector<std::unique_ptr<UserBucket>> ubk;
+    bool has_user() const { return !ubk.empty(); }
 
     // state
     int64_t iters_done = 0;
@@ -297,7 +311,9 @@ extern "C" int fga_add_factors(fga_graph *g, int32_t type, int64_t count, int32_
                                int32_t params_shared, int64_t *first_factor_id) {
     if (!g) return fail(FGA_EINVAL, "fga_add_factors: NULL graph");
     if (g->finalized) return fail(FGA_ESTATE, "fga_add_factors: graph already finalized");
-    if (type < 0 || type >= FGA_NUM_TYPES) return fail(FGA_EINVAL, "fga_add_factors: unknown type %d", type);
+    const bool user = type >= kUserType0;
+    if (type < 0 || (type >= FGA_NUM_TYPES && !user) || (user && type - kUserType0 >= (int)g->users.size()))
+        return fail(FGA_EINVAL, "fga_add_factors: unknown type %d", type);
     if (count < 0 || n_vars_per_factor < 1 || n_vars_per_factor > 64)
         return fail(FGA_EINVAL, "fga_add_factors: count %lld, %d variables per factor", (long long)count,
                     n_vars_per_factor);
@@ -333,7 +349,9 @@ extern "C" int fga_add_factors(fga_graph *g, int32_t type, int64_t count, int32_
                 return fail(FGA_EINVAL, "fga_add_factors: factors of one call must have the same variable shape");
         }
     }
-    const int want = expected_params(type, b.dims, b.arity);
+    const int want = !user ? expected_params(type, b.dims, b.arity)
+                     : b.arity == g->users[type - kUserType0].arity ? g->users[type - kUserType0].np
+                                                                    : -1;
     if (want < 0) return fail(FGA_EINVAL, "fga_add_factors: variable shape does not fit factor type %d", type);
     if (want != params_per_factor)
         return fail(FGA_EINVAL, "fga_add_factors: type %d takes %d parameters, got %d", type, want, params_per_factor);
@@ -373,6 +391,38 @@ extern "C" int fga_add_factors(fga_graph *g, int32_t type, int64_t count, int32_
         return fail(FGA_ENOMEM, "fga_add_factors: out of host memory");
     }
     if (first_factor_id) *first_factor_id = first;
+    return FGA_OK;
+}
+
+extern "C" int fga_register_prox(fga_graph *g, const char *cuda_source, const char *function_name, int32_t arity,
+                                 int32_t params_per_factor, int32_t *type_out) {
+    if (!g || !cuda_source || !function_name || !type_out) return fail(FGA_EINVAL, "fga_register_prox: NULL argument");
+    if (g->finalized) return fail(FGA_ESTATE, "fga_register_prox: graph already finalized");
+    if (arity < 1 || arity > kUserMaxArity)
+        return fail(FGA_EINVAL, "fga_register_prox: arity %d outside [1, %d]", arity, kUserMaxArity);
+    if (params_per_factor < 0 || params_per_factor > kUserMaxParams)
+        return fail(FGA_EINVAL, "fga_register_prox: %d parameters per factor (at most %d)", params_per_factor,
+                    kUserMaxParams);
+    if ((int)g->users.size() == kMaxUserTypes)
+        return fail(FGA_EINVAL, "fga_register_prox: more than %d user operators", kMaxUserTypes);
+    int rc = set_device(g);
+    if (rc) return rc;
+    UserProg p;
+    std::string log;
+    if (!user_compile(cuda_source, function_name, arity, params_per_factor, g->precision == FGA_F64, p, log)) {
+        if (log.size() > 1500) log.resize(1500);
+        const bool env = log.rfind("NVRTC (", 0) == 0 || log.rfind("no CUDA", 0) == 0 ||
+                         log.rfind("cudaLibrary", 0) == 0;
+        t_last_error = "fga_register_prox: " + log;
+        return env ? FGA_ECUDA : FGA_EINVAL;
+    }
+    try {
+        g->users.push_back(p);
+    } catch (...) {
+        user_release(p);
+        return fail(FGA_ENOMEM, "fga_register_prox: out of host memory");
+    }
+    *type_out = kUserType0 + (int)g->users.size() - 1;
     return FGA_OK;
 }
 
@@ -556,6 +606,7 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
 
     // per-bucket parameters (SoA) and MPC projection matrices
     g->bucket_bufs.clear();
+    g->ubk.clear();
     for (auto &bk : g->buckets) {
         const int64_t nf = (int64_t)bk.members.size();
         std::vector<R> prm((size_t)bk.np * nf);
@@ -564,12 +615,37 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
             const double *p = b.param(bk.members[f].second);
             // hinge and margin parameters factor-major (a factor's data
             // point read contiguously); every other type edge-major
-            const bool fmaj = bk.type == FGA_SVM_HINGE || bk.type == FGA_SVM_MARGIN;
+            const bool fmaj = bk.type == FGA_SVM_HINGE || bk.type == FGA_SVM_MARGIN || bk.type >= kUserType0;
             for (int j = 0; j < bk.np; ++j) prm[fmaj ? (size_t)f * bk.np + j : (size_t)j * nf + f] = (R)p[j];
         }
         auto pb = std::make_unique<DevBuf>();
         if ((rc = upload_vec(*pb, prm))) return rc;
+        bk.prm_buf = (int)g->bucket_bufs.size();
         g->bucket_bufs.push_back(std::move(pb));
+        if (bk.type >= kUserType0) {
+            // per edge of the bucket: its scalar variable and where its rho m
+            // goes (the canonical rows, or the scatter columns / overflow)
+            auto ub = std::make_unique<UserBucket>();
+            ub->bucket = (int)(&bk - g->buckets.data());
+            ub->user = bk.type - kUserType0;
+            const int64_t n = nf * bk.arity;
+            std::vector<int32_t> var((size_t)std::max<int64_t>(n, 1), 0);
+            std::vector<uint32_t> dst((size_t)std::max<int64_t>(n, 1), 0u);
+            for (int64_t l = 0; l < n; ++l) {
+                const int64_t st = bk.ebase + l;
+                var[l] = g->svar[st];
+                if (g->zorder == 4) {
+                    const uint32_t ev = fl.ev[st], c = ev >> kEvColShift, b = ev & kEvVarMask;
+                    dst[l] = c != kEvOverflow ? c * (uint32_t)g->nz + b
+                                              : (uint32_t)((int64_t)g->colw * g->nz) + (uint32_t)pos[st];
+                } else {
+                    dst[l] = (uint32_t)pos[st];
+                }
+            }
+            if ((rc = upload_vec(ub->var, var))) return rc;
+            if ((rc = upload_vec(ub->dst, dst))) return rc;
+            g->ubk.push_back(std::move(ub));
+        }
         if (bk.type == FGA_MPC_DYN) {
             const int nx = bk.dims[0], nu = bk.dims[1], n = bk.arity;
             std::map<std::vector<double>, int> seen;
@@ -973,6 +1049,11 @@ extern "C" int fga_finalize(fga_graph *g) {
         g->zorder = 0;
     }
     const int zreq = g->zorder;   // -1: library choice
+    bool user = false;
+    for (const FactorBatch &b : g->batches) user = user || b.type >= kUserType0;
+    if (user && (g->weights || (zreq >= 1 && zreq <= 3)))
+        return fail(FGA_EINVAL, "fga_finalize: user operators run with fixed weights in the canonical (0) or "
+                                "scatter (4) z-order");
     if (zreq == 2 && g->precision != FGA_F32)
         return fail(FGA_EINVAL, "fga_finalize: FGA_OPT_ZORDER 2 (disk tiles) needs FGA_F32");
     if (g->zorder < 0) g->zorder = g->precision == FGA_F64 ? 0 : 1;
@@ -1009,14 +1090,14 @@ extern "C" int fga_finalize(fga_graph *g) {
             nb.arity = b.arity;
             nb.per_edge = is_per_edge(b.type);
             nb.aos = b.type == FGA_PACK_PAIR || b.type == FGA_PACK_WALL || b.type == FGA_MPC_DYN ||
-                     b.type == FGA_SVM_HINGE || b.type == FGA_SVM_MARGIN;
+                     b.type == FGA_SVM_HINGE || b.type == FGA_SVM_MARGIN || b.type >= kUserType0;
             g->buckets.push_back(nb);
             found = (int)g->buckets.size() - 1;
         }
         for (int64_t f = 0; f < b.count; ++f) g->buckets[found].members.emplace_back(bi, f);
     }
     // 1a. disk-tile order when the graph suits it (FP32 default) or when asked
-    if (g->precision == FGA_F32 && (zreq < 0 || zreq == 2)) {
+    if (g->precision == FGA_F32 && !user && (zreq < 0 || zreq == 2)) {
         std::string why;
         const int r = try_tile_plan(g, why);
         if (r < 0) return r;
@@ -1025,7 +1106,7 @@ extern "C" int fga_finalize(fga_graph *g) {
             return fail(FGA_EINVAL, "fga_finalize: the disk-tile order does not apply: %s", why.c_str());
     }
     // 1a'. hinge bank for a linear SVM (FP32 default when it qualifies)
-    if (g->precision == FGA_F32 && g->zorder != 2 && (zreq < 0 || zreq == 3)) {
+    if (g->precision == FGA_F32 && !user && g->zorder != 2 && (zreq < 0 || zreq == 3)) {
         std::string why;
         const int r = try_hinge_plan(g, why);
         if (r < 0) return r;
@@ -1058,6 +1139,9 @@ extern "C" int fga_finalize(fga_graph *g) {
             g->novf = ovf;
         }
     }
+    // user operators: the canonical order when the scatter order does not
+    // apply (their kernels write each edge's rho m to one slot)
+    if (user && g->zorder == 1) g->zorder = 0;
     // the scatter order stores every bucket factor-major (consecutive work
     // items touch consecutive components of a variable block)
     if (g->zorder == 4)
@@ -1661,6 +1745,36 @@ static int iterate_hinge(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
     return FGA_OK;
 }
 
+// The x-update of every bucket of a user operator, in phase-F mode `mode`,
+// after the built-in types' phase F of the same iteration (same stream).
+template <typename R>
+static int user_xsteps(fga_graph *g, const SweepArgs<R> &a, int mode, int xp, int zp, cudaStream_t s) {
+    for (const auto &ub : g->ubk) {
+        const Bucket &bk = g->buckets[ub->bucket];
+        UserLaunch L;
+        L.mode = mode;
+        L.nf = (int)bk.members.size();
+        L.ebase = (int)bk.ebase;
+        L.var = ub->var.as<int>();
+        L.dst = ub->dst.as<unsigned>();
+        L.zc = a.z[zp];
+        L.xin = a.x[xp];
+        L.xout = a.x[xp ^ 1];
+        L.u = a.u;
+        L.mout = a.m[xp ^ 1];
+        L.pvm = a.pvm;
+        L.rho_e = a.rho_e;
+        L.rho_u = g->rho_u;
+        L.alpha_e = a.alpha_e;
+        L.alpha_u = g->alpha_u;
+        L.prm = g->bucket_bufs[bk.prm_buf]->p;
+        L.res_pri = a.res_pri;
+        L.done = reinterpret_cast<const int *>(reinterpret_cast<const char *>(a.ctl) + offsetof(Ctl, done));
+        CUDA_TRY(user_launch(g->users[ub->user], g->precision == FGA_F64, L, g->grid, g->blk, s));
+    }
+    return FGA_OK;
+}
+
 template <typename R>
 static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
     SweepArgs<R> a;
@@ -1679,15 +1793,19 @@ static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
     CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(Barrier), s));
     if (g->n_hubs) CUDA_TRY(cudaMemsetAsync(g->hub_ticket.p, 0, g->hub_ticket.bytes, s));
     CUDA_TRY(cudaEventRecord(g->ev0, s));
-    if (o.fused) {
+    int rc;
+    if (o.fused && !g->has_user()) {
         CUDA_TRY(sweep_persistent<R>(a, g->grid, g->blk, g->smem, g->kind, s));
     } else {
+        // one launch per phase (and the graph's user operators run their
+        // own kernels between phase F and the check)
         int xp = g->xpar, zp = g->zpar;
         for (long long it = 1; it <= a.K; ++it) {
             const bool pend = it > 1;
             const bool chk = pend && ((a.k0 + it - 1) % a.check_every == 0);
             const int mode = !pend ? F_PROX : chk ? F_U_PROX_CHK : F_U_PROX;
             CUDA_TRY(sweep_phase_f<R>(a, mode, xp, zp, g->grid, g->blk, g->smem, g->kind, s));
+            if ((rc = user_xsteps<R>(g, a, mode, xp, zp, s))) return rc;
             if (chk) CUDA_TRY(sweep_check<R>(a, it - 1, xp, zp, 0, g->grid, s));
             xp ^= 1;
             const bool chkz = ((a.k0 + it) % a.check_every == 0) || it == a.K;
@@ -1696,6 +1814,7 @@ static int iterate_typed(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
         }
         if (a.K > 0) {
             CUDA_TRY(sweep_phase_f<R>(a, F_U_ONLY, xp, zp, g->grid, g->blk, g->smem, g->kind, s));
+            if ((rc = user_xsteps<R>(g, a, F_U_ONLY, xp, zp, s))) return rc;
             CUDA_TRY(sweep_check<R>(a, a.K, xp, zp, 1, g->grid, s));
         }
     }
@@ -1742,8 +1861,9 @@ extern "C" int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_res
     if (!g->finalized || !g->initialized) return fail(FGA_ESTATE, "fga_iterate: call fga_finalize and fga_init first");
     if (opts->max_iters < 0 || opts->check_every < 1 || opts->tol_pri < 0 || opts->tol_dual < 0)
         return fail(FGA_EINVAL, "fga_iterate: bad options");
-    if (opts->fault_skip_block >= 0 && !opts->fused)
-        return fail(FGA_EINVAL, "fga_iterate: fault_skip_block needs the fused kernel");
+    if (opts->fault_skip_block >= 0 && (!opts->fused || g->has_user()))
+        return fail(FGA_EINVAL, "fga_iterate: fault_skip_block needs the fused kernel (graphs with user operators "
+                                "run one launch per phase)");
     if (g->shard) return fail(FGA_ESTATE, "fga_iterate: the graph is a shard (use fga_shard_xstep / zstep)");
     if ((g->zorder == 2 || g->zorder == 3) && !opts->fused)
         return fail(FGA_EINVAL, "fga_iterate: the disk-tile and hinge-bank orders run as one persistent launch "
@@ -1816,6 +1936,7 @@ extern "C" int fga_shard_begin(fga_graph *g, const double *srho_total, const dou
         return fail(FGA_EINVAL, "fga_shard_begin: shards run the canonical or the fast z-order (FGA_OPT_ZORDER 0 "
                                 "or 1), not the disk-tile or hinge-bank kernels");
     if (g->weights) return fail(FGA_EINVAL, "fga_shard_begin: shards run fixed weights (FGA_OPT_WEIGHTS 0)");
+    if (g->has_user()) return fail(FGA_EINVAL, "fga_shard_begin: shards run the built-in factor types only");
     for (int64_t b = 0; b < g->nz; ++b)
         if (!std::isfinite(srho_total[b]) || srho_total[b] < 0.0 || !std::isfinite(srho2_total[b]))
             return fail(FGA_EINVAL, "fga_shard_begin: bad graph-wide rho sum at variable %lld", (long long)b);
@@ -2052,6 +2173,10 @@ extern "C" int fga_destroy(fga_graph *g) {
         cudaStreamSynchronize(g->stream);
         if (g->ev0) cudaEventDestroy(g->ev0);
         if (g->ev1) cudaEventDestroy(g->ev1);
+    }
+    if (!g->users.empty()) {
+        cudaSetDevice(g->device);
+        for (UserProg &p : g->users) user_release(p);
     }
     delete g;
     return FGA_OK;

@@ -8,6 +8,7 @@
 namespace fga {
 
 constexpr int kMaxBuckets = 24;     // distinct (type, variable-shape) groups
+constexpr int kUserType0 = 64;      // first type number of a user-supplied operator (FGA_USER_TYPE0)
 constexpr int kPiece = 2048;        // hub variables are reduced in pieces of this many edges
 constexpr int kSmallDeg = 16;       // fast z-order: thread per variable up to this degree
 constexpr int kChunkEdges = 6912;   // fast z-order: scalar edges per chunk (shared-memory buffer)

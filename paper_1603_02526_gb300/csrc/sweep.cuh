@@ -868,6 +868,8 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
 template <typename R, int MODE, int FAST, int KIND>
 __device__ __forceinline__ void process_in_bucket(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
                                                   int li, double &pri) {
+    // user-supplied operators run their own kernels (run-time compiled)
+    if (B.type >= kUserType0) return;
     switch (B.type) {
     case 0: item_pack_pair<R, MODE, FAST>(a, B, io, li, pri); break;
     case 1: item_pack_wall<R, MODE, FAST>(a, B, io, li, pri); break;
@@ -926,6 +928,7 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, dou
         const int wid = gtid >> 5, nw = stride >> 5;
         for (int b = 0; b < a.nb; ++b) {
             const BucketDev<R> &B = a.bk[b];
+            if (B.type >= kUserType0) continue;
             if (KIND == 0 && B.type == 4 && B.arity <= 128) {
                 for (int i = wid; i < B.nitems; i += nw)
                     item_svm_hinge_warp<R, MODE, EO_SCATTER>(a, B, io, i, pri);

@@ -82,6 +82,15 @@ class FactorGraph:
                                         ctypes.byref(first)), "fga_add_factors")
         return first.value
 
+    def fga_register_prox(self, cuda_source, function_name, arity, params_per_factor):
+        """Compiles a user-supplied proximal operator (CUDA source of a
+        function template, see include/fgadmm.h) and returns its type number
+        for fga_add_factors."""
+        t = ctypes.c_int32()
+        check(self._lib.fga_register_prox(self._g, cuda_source.encode(), function_name.encode(), int(arity),
+                                          int(params_per_factor), ctypes.byref(t)), "fga_register_prox")
+        return t.value
+
     def fga_set_rho_alpha(self, rho, alpha):
         check(self._lib.fga_set_rho_alpha(self._g, float(rho), float(alpha)), "fga_set_rho_alpha")
 

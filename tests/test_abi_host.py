@@ -202,3 +202,22 @@ def test_horizon_create_validation(lib):
                                   1.0, 1.0, 0, None) == FGA_EINVAL
     assert lib.fga_horizon_init(None) == FGA_EINVAL
     assert lib.fga_horizon_destroy(None) == 0
+
+
+def test_register_prox_argument_checks(lib):
+    """Host-side checks of fga_register_prox and of user type numbers (the
+    compilation itself needs the GPU and is covered by the GPU tests)."""
+    from paper_1603_02526_gb300._lib import FGA_EINVAL, FGA_USER_TYPE0
+    g = _new(lib)
+    t = ctypes.c_int32()
+    assert lib.fga_register_prox(g, None, b"f", 1, 0, ctypes.byref(t)) == FGA_EINVAL
+    assert lib.fga_register_prox(g, b"src", None, 1, 0, ctypes.byref(t)) == FGA_EINVAL
+    assert lib.fga_register_prox(g, b"src", b"f", 0, 0, ctypes.byref(t)) == FGA_EINVAL
+    assert lib.fga_register_prox(g, b"src", b"f", 65, 0, ctypes.byref(t)) == FGA_EINVAL
+    assert lib.fga_register_prox(g, b"src", b"f", 1, -1, ctypes.byref(t)) == FGA_EINVAL
+    assert lib.fga_add_variables(g, 1, 1, None) == 0
+    one = np.array([[0]], dtype=np.int64)
+    # no operator registered: user type numbers are unknown types
+    assert lib.fga_add_factors(g, FGA_USER_TYPE0, 1, 1, ctypes.c_void_p(one.ctypes.data), None, 0, 0,
+                               None) == FGA_EINVAL
+    assert lib.fga_destroy(g) == 0
