@@ -70,13 +70,16 @@ enum FMode : int { F_PROX = 0, F_U_PROX = 1, F_U_ONLY = 2, F_U_PROX_CHK = 3 };
 
 inline __host__ __device__ constexpr bool fmode_checks(int mode) { return mode == F_U_PROX_CHK || mode == F_U_ONLY; }
 
-// Grid-wide barrier state (device memory, zeroed before every launch).
+// Grid-wide barrier state (device memory, zeroed before every launch):
+// count and gen together are the 64-bit arrival counter of the persistent
+// sweep's barrier (8-byte aligned at the start of the buffer).
 struct Barrier {
     unsigned int count;
     unsigned int gen;
     int error;
     int pad;
 };
+static_assert(sizeof(unsigned int) * 2 == sizeof(unsigned long long), "count and gen form one 64-bit counter");
 
 // Per-call control block written by the device.
 struct Ctl {

@@ -36,23 +36,8 @@ struct PassMode {
 // G x (iterations so far).  Bounded by timeout_ns and a spin count; on
 // expiry the CTA sets the error word and every CTA leaves.
 // ---------------------------------------------------------------------------
-static __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-// Fire-and-forget integer addition at L2 (no value returned to the thread).
-static __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-static __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-static __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
+// (the 64-bit release addition, relaxed addition and relaxed / acquire
+// loads are in sweep.cuh)
 
 // Count of contributions in the difference of two count-and-sum words
 // (kTileCountUnit per contribution, the sum in the low bits).

@@ -43,22 +43,6 @@ static __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-static __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-static __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-static __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v) {
-    unsigned int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
 // ---- cp.async (global -> shared, one element, zero when !valid) -------------
 template <typename R>
 static __device__ __forceinline__ void cp_async_zfill(R *dst, const R *src, bool valid) {
@@ -115,42 +99,63 @@ static __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Grid-wide barrier with a time limit.  One thread per CTA arrives on a
-// counter; the last arrival resets the counter and bumps the generation.
-// Every wait is bounded by timeout_ns (globaltimer) and by a spin count; on
-// expiry the CTA records FGA_ETIMEOUT in the barrier's error word and
-// returns false, and every other CTA stops waiting as soon as it sees the
-// error word.  The caller then leaves the kernel.  `skip` suppresses this
-// CTA's arrival (fault-injection test of the time limit).
+static __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Fire-and-forget integer addition at L2 (no value returned to the thread).
+static __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+static __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+static __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier with a time limit.  The barrier's first eight bytes
+// (count and gen, zeroed before each launch) are one 64-bit counter that
+// only grows: thread 0 of each CTA arrives with a fire-and-forget release
+// addition and waits, polling with relaxed loads, until the counter reaches
+// nblk x (barriers passed so far, `gen` + 1); one acquire load then orders
+// the CTA's later reads (through bar.sync) after every CTA's writes.  No
+// arrival returns a value and no last arrival has to release the others,
+// which makes a barrier of several hundred CTAs cheaper than a counter that
+// is reset each time.  Every wait is bounded by timeout_ns (globaltimer) and
+// by a spin count; on expiry the CTA records FGA_ETIMEOUT in the barrier's
+// error word and returns false, and every other CTA stops waiting as soon as
+// it sees the error word.  The caller then leaves the kernel.  `skip`
+// suppresses this CTA's arrival (fault-injection test of the time limit).
 static __device__ __noinline__ bool grid_barrier(Barrier *b, unsigned int nblk, unsigned int &gen,
                                           long long timeout_ns, bool skip) {
     __shared__ int s_err;
     __syncthreads();
     if (threadIdx.x == 0) {
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(&b->count);
+        const unsigned long long target = (unsigned long long)nblk * ((unsigned long long)gen + 1ull);
         int err = 0;
-        if (!skip) {
-            __threadfence();
-            unsigned int prev = atom_add_acq_rel(&b->count, 1u);
-            if (prev == nblk - 1) {
-                atomicExch(&b->count, 0u);
-                __threadfence();
-                st_release_u32(&b->gen, gen + 1);
-            }
-        }
-        const unsigned long long t0 = global_ns();
-        const unsigned long long lim = (unsigned long long)timeout_ns;
-        unsigned int spins = 0;
-        while (ld_acquire_u32(&b->gen) == gen) {
-            ++spins;
-            if ((spins & 63u) == 0u) {
-                if (*(volatile int *)&b->error) { err = 1; break; }
-                if (global_ns() - t0 > lim || spins > (1u << 30)) {
-                    atomicExch(&b->error, kETimeout);
-                    err = 1;
-                    break;
+        if (!skip) red_release_add_u64(cnt, 1ull);
+        if (ld_relaxed_u64(cnt) < target) {
+            const unsigned long long t0 = global_ns();
+            const unsigned long long lim = (unsigned long long)timeout_ns;
+            unsigned int spins = 0;
+            while (ld_relaxed_u64(cnt) < target) {
+                ++spins;
+                if ((spins & 63u) == 0u) {
+                    if (*(volatile int *)&b->error) { err = 1; break; }
+                    if (global_ns() - t0 > lim || spins > (1u << 30)) {
+                        atomicExch(&b->error, kETimeout);
+                        err = 1;
+                        break;
+                    }
                 }
             }
         }
+        (void)ld_acquire_u64(cnt);
         if (!err && *(volatile int *)&b->error) err = 1;
         gen += 1;
         s_err = err;
