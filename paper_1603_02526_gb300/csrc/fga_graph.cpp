@@ -1143,9 +1143,11 @@ extern "C" int fga_finalize(fga_graph *g) {
     // apply (their kernels write each edge's rho m to one slot)
     if (user && g->zorder == 1) g->zorder = 0;
     // the scatter order stores every bucket factor-major (consecutive work
-    // items touch consecutive components of a variable block)
+    // items touch consecutive components of a variable block), except the
+    // dynamics factors, one thread each: edge-major, so that a warp's loads
+    // and stores of its factors' k-th edges are contiguous
     if (g->zorder == 4)
-        for (Bucket &bk : g->buckets) bk.aos = true;
+        for (Bucket &bk : g->buckets) bk.aos = bk.type != FGA_MPC_DYN;
     const bool tile = g->zorder == 2;
     const bool hinge = g->zorder == 3;
     const int64_t tile_span = (int64_t)g->tile.U * kUnitEdges;
