@@ -410,6 +410,28 @@ __device__ __forceinline__ R edge_pre(const SweepArgs<R> &a, const EdgeIO<R> &io
     return n;
 }
 
+// The same in two halves, so that an item issues the loads of several of
+// its edges before the first store (a store to u may alias a later load as
+// far as the compiler knows, so edge_pre in a loop over edges makes every
+// edge's loads wait for the previous edge's store): edge_load reads z at
+// the far end, u and the previous x; edge_update runs the deferred u-update
+// and the n-update and stores u.  The arithmetic is edge_pre's.
+template <typename R, int MODE, int FAST>
+__device__ __forceinline__ void edge_load(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, R &z, R &u, R &xo,
+                                          unsigned &ix) {
+    z = edge_z<R, FAST>(a, io, e, ix);
+    u = a.u[e];
+    xo = MODE != F_PROX ? io.xin[e] : R(0);
+}
+
+template <typename R, int MODE>
+__device__ __forceinline__ R edge_update(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, R z, R xo, R &u,
+                                         double &pri) {
+    const R n = update_un<R, MODE>(a, io, e, z, xo, u, pri);
+    if (MODE != F_PROX) a.u[e] = u;
+    return n;
+}
+
 // One scalar edge, end of phase F: x, m = x + u, rho*m to the z-reduction.
 template <typename R, int FAST>
 __device__ __forceinline__ void edge_post(const SweepArgs<R> &a, const EdgeIO<R> &io, int e, unsigned ix, R x, R u) {
@@ -780,8 +802,19 @@ __device__ __forceinline__ void item_mpc_dyn(const SweepArgs<R> &a, const Bucket
     if constexpr (AC > 0) {
         R n[AC], u[AC];
         unsigned ix[AC];
+        // the loads of CH edges at a time before their updates (CH divides
+        // AC; small groups keep the register demand within the kernel's)
+        constexpr int CH = AC % 4 == 0 ? 4 : AC % 3 == 0 ? 3 : 1;
         #pragma unroll
-        for (int k = 0; k < AC; ++k) n[k] = edge_pre<R, MODE, FAST>(a, io, bedge(B, f, k), u[k], ix[k], pri);
+        for (int k0 = 0; k0 < AC; k0 += CH) {
+            R z[CH], xo[CH];
+            #pragma unroll
+            for (int t = 0; t < CH; ++t)
+                edge_load<R, MODE, FAST>(a, io, bedge(B, f, k0 + t), z[t], u[k0 + t], xo[t], ix[k0 + t]);
+            #pragma unroll
+            for (int t = 0; t < CH; ++t)
+                n[k0 + t] = edge_update<R, MODE>(a, io, bedge(B, f, k0 + t), z[t], xo[t], u[k0 + t], pri);
+        }
         if (MODE == F_U_ONLY) return;
         const R *P = B.pmat + (long long)B.pidx[f] * AC * AC;
         #pragma unroll 2
