@@ -1240,7 +1240,57 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
             if (c < a.colw) S += v[c];
         return S;
     };
-    if constexpr (scat) {
+    if constexpr (scat && !SHARD) {
+        // NB variables per thread: every load of the NB (overflow flags,
+        // columns, old z, rho sums) before their stores; the same additions
+        // in the same order as colsum and z_store
+        constexpr int NB = 4;
+        for (long long b0 = gtid; b0 < a.nz; b0 += NB * gstride) {
+            int bb[NB];
+            bool ok[NB];
+            #pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const long long b = b0 + q * gstride;
+                bb[q] = (int)b;
+                ok[q] = b < a.nz && !a.zovf[b];
+            }
+            R S[NB];
+            #pragma unroll
+            for (int q = 0; q < NB; ++q) S[q] = R(0);
+            for (int c0 = 0; c0 < a.colw; c0 += 4) {
+                R v[NB][4];
+                #pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    #pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        v[q][t] = (ok[q] && c0 + t < a.colw) ? ldg_l2(a.pvm + (size_t)(c0 + t) * a.nz + bb[q]) : R(0);
+                }
+                #pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    #pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (c0 + t < a.colw) S[q] += v[q][t];
+                }
+            }
+            R zold[NB], sr[NB];
+            #pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                zold[q] = ok[q] ? zo[bb[q]] : R(0);
+                sr[q] = ok[q] ? a.srho[bb[q]] : R(0);
+            }
+            #pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (!ok[q]) continue;
+                R znew = zold[q];
+                if (sr[q] > R(0)) znew = S[q] / sr[q];   // a variable without edges keeps z
+                zn[bb[q]] = znew;
+                if constexpr (CHK) {
+                    const double dz = (double)znew - (double)zold[q];
+                    dual += a.srho2[bb[q]] * dz * dz;
+                }
+            }
+        }
+    } else if constexpr (scat) {
         for (long long b = gtid; b < a.nz; b += gstride)
             if (!a.zovf[b]) finish_sum((int)b, colsum((int)b));
     }
