@@ -792,6 +792,38 @@ __device__ __forceinline__ void item_equal(const SweepArgs<R> &a, const BucketDe
     edge_post<R, FAST>(a, io, e2, i2, v, u2);
 }
 
+// NB equality items of one thread, li = i0 + q * step: the loads of all of
+// them first (as items_elementwise).
+template <typename R, int MODE, int FAST, int NB>
+__device__ __forceinline__ void items_equal(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io, int i0,
+                                            int step, double &pri) {
+    const int D = B.arity >> 1;
+    R z[NB][2], u[NB][2], xo[NB][2];
+    unsigned ix[NB][2];
+    int e[NB][2];
+    #pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const int li = i0 + q * step;
+        if (li >= B.nitems) continue;
+        const int j = B.aos ? li % D : li / B.nf, f = B.aos ? li / D : li - j * B.nf;
+        e[q][0] = bedge(B, f, j);
+        e[q][1] = bedge(B, f, D + j);
+        #pragma unroll
+        for (int k = 0; k < 2; ++k) edge_load<R, MODE, FAST>(a, io, e[q][k], z[q][k], u[q][k], xo[q][k], ix[q][k]);
+    }
+    #pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        if (i0 + q * step >= B.nitems) break;
+        const R n1 = edge_update<R, MODE>(a, io, e[q][0], z[q][0], xo[q][0], u[q][0], pri);
+        const R n2 = edge_update<R, MODE>(a, io, e[q][1], z[q][1], xo[q][1], u[q][1], pri);
+        if (MODE == F_U_ONLY) continue;
+        const R r1 = edge_rho(a, e[q][0]), r2 = edge_rho(a, e[q][1]);
+        const R v = (r1 * n1 + r2 * n2) / (r1 + r2);
+        edge_post<R, FAST>(a, io, e[q][0], ix[q][0], v, u[q][0]);
+        edge_post<R, FAST>(a, io, e[q][1], ix[q][1], v, u[q][1]);
+    }
+}
+
 // Appendix B dynamics: v = P n with P the rho-weighted projector onto
 // {x' = A x + B u}, precomputed per distinct (A, B, rho).  AC = compile-time
 // arity (n kept in registers), or 0 for any arity (n re-formed from u and z
@@ -851,17 +883,10 @@ __device__ __forceinline__ void item_mpc_dyn(const SweepArgs<R> &a, const Bucket
 // edge ebase + li: component k of factor f at li = k * nf + f (edge-major)
 // or li = f * arity + k (factor-major, scatter order).  Parameters SoA:
 // prm[j * nf + f]; per-component parameters at j = k.
-template <typename R, int MODE, int FAST>
-__device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
-                                                 int li, double &pri) {
-    const int e = B.ebase + li;
-    R u;
-    unsigned ix;
-    const R n = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
-    if (MODE == F_U_ONLY) return;
+template <typename R>
+__device__ __forceinline__ R elementwise_x(const BucketDev<R> &B, int li, R n, R rho) {
     const int f = B.aos ? li / B.arity : li % B.nf;
     const int pk = B.aos ? (li - f * B.arity) * B.nf + f : li;   // per-component parameter index
-    const R rho = edge_rho(a, e);
     R x;
     switch (B.type) {
     case 2:  // PACK_RADIUS_LIN: f = -w r
@@ -892,7 +917,43 @@ __device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const Bu
         x = B.prm[pk];
         break;
     }
-    edge_post<R, FAST>(a, io, e, ix, x, u);
+    return x;
+}
+
+template <typename R, int MODE, int FAST>
+__device__ __forceinline__ void item_elementwise(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
+                                                 int li, double &pri) {
+    const int e = B.ebase + li;
+    R u;
+    unsigned ix;
+    const R n = edge_pre<R, MODE, FAST>(a, io, e, u, ix, pri);
+    if (MODE == F_U_ONLY) return;
+    edge_post<R, FAST>(a, io, e, ix, elementwise_x(B, li, n, edge_rho(a, e)), u);
+}
+
+// NB elementwise items of one thread, li = i0 + q * step (q < NB, those
+// below B.nitems): the loads of all NB items first, then their updates and
+// operators in order (the same arithmetic, item by item, as NB calls of
+// item_elementwise).
+template <typename R, int MODE, int FAST, int NB>
+__device__ __forceinline__ void items_elementwise(const SweepArgs<R> &a, const BucketDev<R> &B, const EdgeIO<R> &io,
+                                                  int i0, int step, double &pri) {
+    R z[NB], u[NB], xo[NB];
+    unsigned ix[NB];
+    #pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const int li = i0 + q * step;
+        if (li < B.nitems) edge_load<R, MODE, FAST>(a, io, B.ebase + li, z[q], u[q], xo[q], ix[q]);
+    }
+    #pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const int li = i0 + q * step;
+        if (li >= B.nitems) break;
+        const int e = B.ebase + li;
+        const R n = edge_update<R, MODE>(a, io, e, z[q], xo[q], u[q], pri);
+        if (MODE == F_U_ONLY) continue;
+        edge_post<R, FAST>(a, io, e, ix[q], elementwise_x(B, li, n, edge_rho(a, e)), u[q]);
+    }
 }
 
 // KIND 0: every factor type; KIND 1: graphs without hinge, dynamics, margin
@@ -955,7 +1016,12 @@ __device__ __forceinline__ void issue_pair_stage(const SweepArgs<R> &a, const Ed
 // rho*m lands in shared memory sorted by slot, and each slot's sum over the
 // chunk (edges in slot order) is written to the variable-major partial
 // array.  Both orders are deterministic.
-template <typename R, int MODE, int KIND_>
+// BATCH (the one-launch-per-phase kernels): elementwise and equality
+// items of the scatter order with the loads of two items (two edges) in
+// flight together; the persistent kernel, compiled for three or four
+// resident CTAs per SM, keeps one item at a time (the batches' extra
+// registers would spill there).
+template <typename R, int MODE, int KIND_, bool BATCH = false>
 __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, double &pri) {
     constexpr int KIND = kind_types(KIND_);
     if constexpr (kind_scatter(KIND_)) {
@@ -973,6 +1039,14 @@ __device__ __forceinline__ void phase_f(const SweepArgs<R> &a, EdgeIO<R> io, dou
             } else if ((KIND == 0 || KIND == 2) && B.type == 10 && B.arity >= 16 && B.arity <= 128) {
                 for (int i = wid; i < B.nitems; i += nw)
                     item_svm_margin_warp<R, MODE, EO_SCATTER>(a, B, io, i, pri);
+            } else if (BATCH && B.per_edge) {
+                // elementwise buckets: two items per thread with their loads
+                // in flight together (the same items, in the same order, as
+                // one at a time)
+                for (int i = gtid; i < B.nitems; i += 2 * stride)
+                    items_elementwise<R, MODE, EO_SCATTER, 2>(a, B, io, i, stride, pri);
+            } else if (BATCH && KIND != 1 && B.type == 12) {
+                for (int i = gtid; i < B.nitems; i += stride) items_equal<R, MODE, EO_SCATTER, 1>(a, B, io, i, stride, pri);
             } else {
                 for (int i = gtid; i < B.nitems; i += stride)
                     process_in_bucket<R, MODE, EO_SCATTER, KIND>(a, B, io, i, pri);
@@ -1473,7 +1547,7 @@ __global__ void __launch_bounds__(256) k_phase_f(const SweepArgs<R> a, int xp, i
     if (*(volatile int *)&a.ctl->done) return;
     const EdgeIO<R> io = make_io(a, xp, zp);
     double pri = 0.0;
-    phase_f<R, MODE, KIND>(a, io, pri);
+    phase_f<R, MODE, KIND, true>(a, io, pri);
     if constexpr (fmode_checks(MODE)) {
         const double s = block_sum(pri);
         if (threadIdx.x == 0) a.res_pri[blockIdx.x] = s;
