@@ -487,7 +487,8 @@ def run_extras(log=None):
     # same 100k x 64 data and on the paper's d = 2
     sp = {"workload": "soft-margin SVM in the paper's form: margin (w_i, b, xi_i), minimal-error (weight C = 1000, "
                       "the hinge form's c / lam), split norm |w_i|^2 / 2N and the equality chain w_i = w_{i+1}; "
-                      "rho 1, FP32 fast z order; device time of 100 fused iterations",
+                      "rho 1, FP32, the library's default z order (scatter); device time of 100 iterations, fused "
+                      "(one persistent launch) and per_phase (one launch per update phase)",
           "kernel": "k_sweep_persistent<float>"}
     for npts, dd in ((100000, 64), (100000, 2)):
         p = inputs.svm_paper_problem(npts, dd, seed=3000, C=1000.0)
@@ -495,9 +496,18 @@ def run_extras(log=None):
         g.fga_iterate(20, check_every=20)
         g.fga_init(p.z0)
         r = g.fga_iterate(100, check_every=100)
-        sp["%dx%d" % (npts, dd)] = {"scalar_edges": p.num_edges, "ms_100_iters": r["ms"],
+        g.fga_init(p.z0)
+        g.fga_iterate(20, check_every=20, fused=False)
+        g.fga_init(p.z0)
+        ru = g.fga_iterate(100, check_every=100, fused=False)
+        sp["%dx%d" % (npts, dd)] = {"scalar_edges": p.num_edges, "zorder": g.fga_launch_info()["zorder"],
+                                    "ms_100_iters": r["ms"],
                                     "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3),
-                                    "frac_of_hbm": 20 * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak}
+                                    "frac_of_hbm": 20 * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak,
+                                    "per_phase": {"ms_100_iters": ru["ms"],
+                                                  "edge_updates_per_s": p.num_edges * 100 / (ru["ms"] * 1e-3),
+                                                  "frac_of_hbm": 20 * p.num_edges * 100 / (ru["ms"] * 1e-3) / 1e9
+                                                  / peak}}
         del g
     sp["peak_kind"] = peak_kind
     out["svm_paper_form"] = sp
@@ -554,8 +564,9 @@ def run_extras(log=None):
     # the K = 10^5 solve to RMS residual 1e-5 (1e-4 is met after about 10
     # iterations: the RMS runs over 1.4M edges, most of them near zero)
     hz = {"workload": "inverted-pendulum MPC, one instance as one factor graph (FIX, DYN, stage and terminal "
-                      "QUAD; 14 scalar edges per step), rho 1, z0 = 0; FP32 fast z order and FP64 canonical "
-                      "order; per K: device time of 100 fused iterations",
+                      "QUAD; 14 scalar edges per step), rho 1, z0 = 0; FP32 in the library's default z order "
+                      "(scatter) and FP64 canonical order; per K: device time of 100 fused iterations (per_phase: "
+                      "one launch per update phase)",
           "kernel": "k_sweep_persistent<float> / <double>; f32_grid: k_horizon (one step per thread, "
                     "messages in registers, one grid barrier per iteration)", "per_K": {}}
     for K in (200, 1000, 10000, 50000, 100000):
@@ -569,6 +580,14 @@ def run_extras(log=None):
             bpe = 20 if prec == "f32" else 40
             row[prec] = {"ms_100_iters": r["ms"], "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3),
                          "frac_of_hbm": bpe * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak}
+            if prec == "f32" and K >= 10000:
+                g.fga_init(p.z0)
+                g.fga_iterate(20, check_every=20, fused=False)
+                g.fga_init(p.z0)
+                ru = g.fga_iterate(100, check_every=100, fused=False)
+                row[prec]["per_phase"] = {"ms_100_iters": ru["ms"],
+                                          "edge_updates_per_s": p.num_edges * 100 / (ru["ms"] * 1e-3),
+                                          "frac_of_hbm": bpe * p.num_edges * 100 / (ru["ms"] * 1e-3) / 1e9 / peak}
             if K == 100000 and prec == "f32":
                 g.fga_init(p.z0)
                 r = g.fga_iterate(50000, 1e-5, 1e-5, check_every=10)
