@@ -732,9 +732,10 @@ def run_profile(args):
     if args.zorder is not None:
         opts[_lib.FGA_OPT_ZORDER] = args.zorder
     g = graph_from_problem(p, "f32", options=opts)
-    g.fga_iterate(args.profile_iters, check_every=args.profile_iters)
+    fused = not args.profile_per_phase
+    g.fga_iterate(args.profile_iters, check_every=args.profile_iters, fused=fused)
     g.fga_init(p.z0)
-    r = g.fga_iterate(args.profile_iters, check_every=args.profile_iters)
+    r = g.fga_iterate(args.profile_iters, check_every=args.profile_iters, fused=fused)
     torch.cuda.synchronize()
     print("profile run: %d iterations, %.3f ms, %.3e edge-updates/s" % (
         r["iters"], r["ms"], p.num_edges * r["iters"] / (r["ms"] * 1e-3)))
@@ -758,6 +759,9 @@ def main():
                     choices=["packing", "svm", "mpc_horizon", "mpc_horizon_grid", "svm_paper", "mpc_one",
                              "mpc_batch", "mlp_forward"])
     ap.add_argument("--profile-threads", type=int, default=256, help="CTA size of the mpc_one profiling run")
+    ap.add_argument("--profile-per-phase", action="store_true",
+                    help="profiling run of a graph workload: one launch per update phase instead of the persistent "
+                         "kernel")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one warm-up and one timed solve of this many iterations, no JSON")
     args = ap.parse_args()
