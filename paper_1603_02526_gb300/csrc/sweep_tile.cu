@@ -243,11 +243,17 @@ static __device__ __forceinline__ void tile_unit_a1(const TileArgs &a, const Pas
             #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const float xo = __fadd_rn(no[k], dl[k]);
-                const float uo = __fadd_rn(__fsub_rn(zp[k], z[k]), dl[k]);
                 const float d = __fsub_rn(xo, z[k]);
                 sq = __fmaf_rn(d, d, sq);
-                a.xout[ubase + (c * 6 + k) * 32] = xo;
-                a.u[ubase + (c * 6 + k) * 32] = uo;
+                // x and u of the pairs are stored by the call's last pass and
+                // by a check that also saves (its dsave then no longer holds
+                // the displacements of it-2); any other check that stops the
+                // call stores them afterwards (tile_store_a1), so that checks
+                // that go on write nothing but the displacements
+                if (MODE == T_FINAL || SAVE) {
+                    a.xout[ubase + (c * 6 + k) * 32] = xo;
+                    a.u[ubase + (c * 6 + k) * 32] = __fadd_rn(__fsub_rn(zp[k], z[k]), dl[k]);
+                }
             }
             // the pair's squared differences in FP32, the sum over pairs in
             // FP64 (the FP64 pipe is narrow on this part)
@@ -293,6 +299,53 @@ static __device__ __forceinline__ void tile_unit_a1(const TileArgs &a, const Pas
         col[c][2] = -pt;
     }
     if (MODE != T_FINAL) stage_unit(lane, ar0, ar1, ar2, col, stg_w);
+}
+
+// ---------------------------------------------------------------------------
+// alpha = 1, after a check that stops the call: the stored state of
+// iteration it-1 (x and u of the unit's pair edges), from the displacements
+// of iteration it-1 (dres, written by the check pass), those of it-2 (dsave,
+// or the stored u when it-2 was the call's start: RELOAD) and the pass's z
+// tables -- the same operations on the same operands as a check pass that
+// stores them (so the same bits).
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ void tile_store_a1(const TileArgs &a, bool reload, int unit, int lane, int rs,
+                                                     const unsigned (&csp)[4], const float4 *z4, const float4 *zp4,
+                                                     const float4 *yp4) {
+    const size_t ubase = (size_t)a.pair_ebase + (size_t)unit * kUnitEdges + lane;
+    const size_t dbase = (size_t)unit * (kUnitEdges / 2) + lane;
+    const float4 zr = z4[rs], zpr = zp4[rs];
+    const float4 ypr = reload ? make_float4(0.f, 0.f, 0.f, 0.f) : yp4[rs];
+    #pragma unroll 2
+    for (int c = 0; c < 8; ++c) {
+        const unsigned slot = col_slot(csp, c);
+        const float4 zc = z4[slot], zpc = zp4[slot];
+        const float z[6] = {zr.x, zr.y, zr.z, zc.x, zc.y, zc.z};
+        const float zp[6] = {zpr.x, zpr.y, zpr.z, zpc.x, zpc.y, zpc.z};
+        float no[6];
+        if (reload) {
+            #pragma unroll
+            for (int k = 0; k < 6; ++k) no[k] = __fsub_rn(zp[k], a.u[ubase + (c * 6 + k) * 32]);
+        } else {
+            const float4 ypc = yp4[slot];
+            const float pa = a.dsave[dbase + (c * 3) * 32], pb = a.dsave[dbase + (c * 3 + 1) * 32],
+                        pt = a.dsave[dbase + (c * 3 + 2) * 32];
+            no[0] = __fadd_rn(ypr.x, pa);
+            no[1] = __fadd_rn(ypr.y, pb);
+            no[2] = __fadd_rn(ypr.z, pt);
+            no[3] = __fsub_rn(ypc.x, pa);
+            no[4] = __fsub_rn(ypc.y, pb);
+            no[5] = __fadd_rn(ypc.z, pt);
+        }
+        const float da = a.dres[dbase + (c * 3) * 32], db = a.dres[dbase + (c * 3 + 1) * 32],
+                    dt = a.dres[dbase + (c * 3 + 2) * 32];
+        const float dl[6] = {-da, -db, -dt, da, db, -dt};
+        #pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            a.xout[ubase + (c * 6 + k) * 32] = __fadd_rn(no[k], dl[k]);
+            a.u[ubase + (c * 6 + k) * 32] = __fadd_rn(__fsub_rn(zp[k], z[k]), dl[k]);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -763,6 +816,9 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
             c.status = finite ? 0 : kENonFinite;
             c.stop = !finite || s_dec[1] != 0;
             if (c.stop || fin) {
+                // a check that stops the call stores its state now (alpha = 1;
+                // a check that also saved has stored it in the pass)
+                if (A1 && !fin && !pm.save && has_unit) tile_store_a1(a, pm.reload, unit, lane, rs, csp, z4, zp4, yp4);
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
                     Ctl *ctl = a.ctl;
                     ctl->iters = it - 1;
