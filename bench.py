@@ -449,21 +449,23 @@ def run_extras(log=None):
                     "algorithmic_gbs": f64_bytes / (r["ms"] * 1e-3) / 1e9,
                     "frac_of_hbm": f64_bytes / (r["ms"] * 1e-3) / 1e9 / peak, "peak_kind": peak_kind}
         del g
-    # packing above the disk-tile limit (about 1,050 disks on 152 SMs):
-    # N = 2000 (about 12M scalar edges) through the chunked fast order, the
-    # time of 100 iterations
+    # packing with more disk tiles than warps per SM: N = 2000 (about 12M
+    # scalar edges), the time of 100 iterations in the library's default
+    # order (the disk tiles, several units per warp) and in the chunked order
     p = inputs.packing_problem(2000, seed=SEED)
-    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 0})
-    g.fga_iterate(20, check_every=20)
-    g.fga_init(p.z0)
-    r = g.fga_iterate(100, check_every=100)
-    out["packing_n2000_f32"] = {"workload": "circle packing N=2000, FP32, 100 iterations (above the disk-tile limit: "
-                                            "the chunked fast z order)", "scalar_edges": p.num_edges,
-                                "zorder": g.fga_launch_info()["zorder"], "ms_100_iters": r["ms"],
-                                "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3),
-                                "frac_of_hbm": 20 * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak,
-                                "kernel": "k_sweep_persistent<float, 1>", "peak_kind": peak_kind}
-    del g
+    row = {"workload": "circle packing N=2000, FP32, 100 iterations: the library's default order (disk tiles, each "
+                       "warp taking several units in turn) and the chunked fast order",
+           "scalar_edges": p.num_edges, "peak_kind": peak_kind}
+    for name, opts in (("default", {_lib.FGA_OPT_STORE_M: 0}), ("chunked", {_lib.FGA_OPT_ZORDER: 1})):
+        g = graph_from_problem(p, "f32", options=opts)
+        g.fga_iterate(20, check_every=20)
+        g.fga_init(p.z0)
+        r = g.fga_iterate(100, check_every=100)
+        row[name] = {"zorder": g.fga_launch_info()["zorder"], "ms_100_iters": r["ms"],
+                     "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3),
+                     "frac_of_hbm": 20 * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak}
+        del g
+    out["packing_n2000_f32"] = row
     # SVM
     p = inputs.svm_problem(100000, 64, seed=3000)
     g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 0})

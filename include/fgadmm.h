@@ -142,7 +142,9 @@ extern "C" {
 #define FGA_OPT_STORE_M 1     /* 1 = keep m per edge so FGA_EDGE_M can be read
                                  back (default 1 for FGA_F64, 0 for FGA_F32)  */
 #define FGA_OPT_BLOCK 2       /* threads per CTA of the sweep (0 = library
-                                 choice; 64..256, multiple of 32)            */
+                                 choice; 64..256, multiple of 32); in the
+                                 disk-tile order, the most threads per CTA
+                                 (a CTA's units beyond its warps take turns) */
 #define FGA_OPT_WEIGHTS 3     /* 0 = rho fixed per edge (Algorithm 2 as
                                  printed); 1 = three weights: each x-update
                                  gives every edge a weight class -- infinite

@@ -159,7 +159,7 @@ struct fga_graph {
     // disk-tile order (zorder 2): the plan and its device copies
     TilePlan tile;
     DevBuf t_cta, t_rowslot, t_colslot, t_mask, t_sv, t_zden, t_cptr, t_clist, t_loc, t_part, t_res, t_dsave;
-    DevBuf t_dres, t_zprev, t_lres;
+    DevBuf t_dres, t_zprev, t_lres, t_dlive;
     // hinge bank (zorder 3)
     HingePlan hinge;
     HingeInput hin;
@@ -545,6 +545,7 @@ static int finalize_typed(fga_graph *g, const std::vector<int32_t> &pos, const s
         CUDA_TRY(cudaMemset(g->t_part.p, 0, g->t_part.bytes));
         CUDA_TRY(g->t_dsave.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
         CUDA_TRY(g->t_dres.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
+        if (T.W > T.warps) CUDA_TRY(g->t_dlive.alloc((size_t)T.U * (kUnitEdges / 2) * sizeof(float)));
         CUDA_TRY(g->t_lres.alloc((size_t)std::max<size_t>(T.loc.size(), 1) * sizeof(float)));
         CUDA_TRY(g->t_zprev.alloc((size_t)std::max<int64_t>(g->nz, 1) * sizeof(float)));
     } else if (g->zorder == 0) {
@@ -912,6 +913,7 @@ static int try_tile_plan(fga_graph *g, std::string &why) {
     }
     CUDA_TRY(cudaDeviceGetAttribute(&in.sms, cudaDevAttrMultiProcessorCount, g->device));
     in.wmax = tile_max_warps();
+    if (g->block) in.wmax = std::min(in.wmax, g->block / 32);   // FGA_OPT_BLOCK caps the warps per CTA
     int rc;
     try {
         rc = tile_plan(in, g->tile, why);
@@ -1295,7 +1297,7 @@ extern "C" int fga_finalize(fga_graph *g) {
     g->kind = (has_hinge || dyn_big || (dyn && me)) ? 0 : dyn ? 3 : me ? 2 : 1;
     if (g->zorder == 4) g->kind |= kKindScatter;
     if (tile) {
-        g->blk = g->tile.W * 32;
+        g->blk = g->tile.warps * 32;
         g->smem = tile_smem_bytes(g->tile);
     }
     if (hinge) {
@@ -1575,6 +1577,7 @@ static void fill_tile_args(const fga_graph *g, TileArgs &a) {
     a.u = g->u.as<float>();
     a.dsave = g->t_dsave.as<float>();
     a.dres = g->t_dres.as<float>();
+    a.dlive = T.W > T.warps ? g->t_dlive.as<float>() : nullptr;
     a.lres = g->t_lres.as<float>();
     a.zpin = g->t_zprev.as<float>();
     a.zpout = g->t_zprev.as<float>();

@@ -2,7 +2,8 @@
 //
 // Input: the disk pairs, walls and radius rewards of a packing graph.
 // Output: the units (32 row disks x 8 column disks of the pair matrix) in
-// row-major order, their assignment to CTAs (one unit per warp), each CTA's
+// row-major order, their assignment to CTAs (one unit per warp, or several
+// per warp on larger graphs), each CTA's
 // z table (slots = disks it touches), the staging positions of every
 // contribution to a slot variable and the order they are summed in, and
 // the CTA that owns each variable (writes its z, adds its dual residual and
@@ -116,10 +117,12 @@ int tile_plan(const TileInput &in, TilePlan &P, std::string &why) {
     P.pair_pos.resize((size_t)npairs);
     for (int64_t p = 0; p < npairs; ++p) P.pair_pos[p] = rank[tmp_pos[p] / 256] * 256 + tmp_pos[p] % 256;
 
-    // 3. launch shape: one unit per warp, as few warps per CTA as fit the SMs
+    // 3. launch shape: as few units per CTA as fit the SMs, one warp each up
+    // to the kernel's warps per CTA; beyond that each warp takes several in
+    // turn (their state then lives in device memory between passes)
     const int64_t W = (U + in.sms - 1) / in.sms;
-    if (W > in.wmax) {
-        why = "more units than the resident warps can hold";
+    if (W > kTileMaxUnitsMulti) {
+        why = "more units per CTA than the tables of one CTA can hold";
         return 1;
     }
     if (U * (int64_t)kUnitEdges > (int64_t)INT32_MAX / 2) {
@@ -130,6 +133,7 @@ int tile_plan(const TileInput &in, TilePlan &P, std::string &why) {
     P.U = (int)U;
     P.W = (int)W;
     P.G = G;
+    P.warps = (int)std::min<int64_t>(W, in.wmax);
 
     // 4. per CTA: slots (disks) of its units
     P.rowslot.assign((size_t)U * kTileRows, 0);

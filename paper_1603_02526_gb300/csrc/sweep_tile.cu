@@ -595,18 +595,90 @@ struct PairState<false> {
     float u[8][6];
 };
 
-template <bool GEN, bool A1>
+// A unit's lane descriptors: the z-table slot of the lane's row disk, the
+// mask of its pairs, and the slots of its register slots' column disks.
+static __device__ __forceinline__ void unit_desc(const TileArgs &a, int unit, int lane, int &rs, unsigned &msk,
+                                                 unsigned (&csp)[4]) {
+    rs = a.rowslot[unit * 32 + lane];
+    msk = a.mask[unit * 32 + lane];
+    const int mp = (lane >> 2) & 7;
+    #pragma unroll
+    for (int j = 0; j < 4; ++j)
+        csp[j] = (unsigned)a.colslot[unit * 8 + ((2 * j) ^ mp)] | ((unsigned)a.colslot[unit * 8 + ((2 * j + 1) ^ mp)] << 16);
+}
+
+// Several units per warp (MULTI): a unit's pair state lives in device
+// memory between passes (alpha = 1: its displacements in dlive; any alpha:
+// its u in the edge array) and is loaded into registers for the unit's turn.
+template <bool A1>
+static __device__ __forceinline__ void state_load(const TileArgs &a, int unit, int lane, PairState<A1> &ps) {
+    if constexpr (A1) {
+        const size_t dbase = (size_t)unit * (kUnitEdges / 2) + lane;
+        #pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            #pragma unroll
+            for (int k = 0; k < 3; ++k) ps.D[c][k] = a.dlive[dbase + (c * 3 + k) * 32];
+        }
+    } else {
+        const size_t ubase = (size_t)a.pair_ebase + (size_t)unit * kUnitEdges + lane;
+        #pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            #pragma unroll
+            for (int k = 0; k < 6; ++k) ps.u[c][k] = a.u[ubase + (c * 6 + k) * 32];
+        }
+    }
+}
+template <bool A1>
+static __device__ __forceinline__ void state_store(const TileArgs &a, int unit, int lane, const PairState<A1> &ps) {
+    if constexpr (A1) {
+        const size_t dbase = (size_t)unit * (kUnitEdges / 2) + lane;
+        #pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            #pragma unroll
+            for (int k = 0; k < 3; ++k) a.dlive[dbase + (c * 3 + k) * 32] = ps.D[c][k];
+        }
+    } else {
+        const size_t ubase = (size_t)a.pair_ebase + (size_t)unit * kUnitEdges + lane;
+        #pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            #pragma unroll
+            for (int k = 0; k < 6; ++k) a.u[ubase + (c * 6 + k) * 32] = ps.u[c][k];
+        }
+    }
+}
+
+template <bool GEN, bool A1, bool MULTI>
 static __device__ __forceinline__ void tile_pass(const TileArgs &a, const PassMode pm, const TileCta &C, const TileLocal *loc, float *uloc,
                                                  bool has_unit, int unit, int lane, int rs, unsigned msk,
                                                  const unsigned (&csp)[4], PairState<A1> &ps, const float4 *z4,
                                                  const float4 *zp4, const float4 *y4, const float4 *yp4, float *stg,
                                                  double &pri) {
-    float *stg_w = stg + (threadIdx.x >> 5) * kUnitStage;
-    if (has_unit) {
-        if constexpr (A1)
-            tile_unit_a1<GEN>(a, pm, unit, lane, rs, msk, csp, ps.D, z4, zp4, y4, yp4, stg_w, pri);
-        else
-            tile_unit_u<GEN>(a, pm, unit, lane, rs, msk, csp, ps.u, z4, zp4, stg_w, pri);
+    if constexpr (MULTI) {
+        // the warp's units in turn: unit w, w + warps, ... of the CTA
+        const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int MODE = GEN ? pm.mode : (int)T_MID;
+        for (int lu = warp; lu < C.nunit; lu += nw) {
+            const int un = C.unit0 + lu;
+            int rs_u;
+            unsigned msk_u, csp_u[4];
+            unit_desc(a, un, lane, rs_u, msk_u, csp_u);
+            PairState<A1> pu;
+            state_load<A1>(a, un, lane, pu);
+            float *stg_w = stg + lu * kUnitStage;
+            if constexpr (A1)
+                tile_unit_a1<GEN>(a, pm, un, lane, rs_u, msk_u, csp_u, pu.D, z4, zp4, y4, yp4, stg_w, pri);
+            else
+                tile_unit_u<GEN>(a, pm, un, lane, rs_u, msk_u, csp_u, pu.u, z4, zp4, stg_w, pri);
+            if (MODE != T_FINAL) state_store<A1>(a, un, lane, pu);
+        }
+    } else {
+        float *stg_w = stg + (threadIdx.x >> 5) * kUnitStage;
+        if (has_unit) {
+            if constexpr (A1)
+                tile_unit_a1<GEN>(a, pm, unit, lane, rs, msk, csp, ps.D, z4, zp4, y4, yp4, stg_w, pri);
+            else
+                tile_unit_u<GEN>(a, pm, unit, lane, rs, msk, csp, ps.u, z4, zp4, stg_w, pri);
+        }
     }
     tile_locals<GEN, A1>(a, pm, C, loc, uloc, lane, z4, zp4, y4, yp4, stg, pri);
 }
@@ -615,7 +687,9 @@ static __device__ __forceinline__ void tile_pass(const TileArgs &a, const PassMo
 // the kernel: iterations 1..K of one call, then the deferred update of
 // iteration K (with its residual check), in one cooperative launch
 // ---------------------------------------------------------------------------
-template <bool A1>
+// MULTI: more units than warps in a CTA (larger graphs): each warp takes
+// its units in turn, their state in device memory between passes.
+template <bool A1, bool MULTI>
 __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const TileArgs a) {
     extern __shared__ __align__(16) unsigned char tsm[];
     const TileSmem L = tile_smem_layout(a.smax, a.svmax, a.locmax, a.clmax, a.stgmax);
@@ -646,22 +720,23 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
 
     const TileCta C = a.cta[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool has_unit = warp < C.nunit;
+    const bool has_unit = !MULTI && warp < C.nunit;
     const int unit = C.unit0 + warp;
     int rs = 0;
     unsigned msk = 0u;
     unsigned csp[4] = {0u, 0u, 0u, 0u};
     PairState<A1> ps;
-    if (has_unit) {
-        rs = a.rowslot[unit * 32 + lane];
-        msk = a.mask[unit * 32 + lane];
-        const int mp = (lane >> 2) & 7;
-        #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            csp[j] = (unsigned)a.colslot[unit * 8 + ((2 * j) ^ mp)] |
-                     ((unsigned)a.colslot[unit * 8 + ((2 * j + 1) ^ mp)] << 16);
-    }
-    if constexpr (A1) {
+    if (has_unit) unit_desc(a, unit, lane, rs, msk, csp);
+    if constexpr (MULTI) {
+        // a call that resumes the previous one takes up its displacements
+        if constexpr (A1) {
+            for (int lu = warp; lu < C.nunit; lu += (int)(blockDim.x >> 5)) {
+                const size_t dbase = (size_t)(C.unit0 + lu) * (kUnitEdges / 2) + lane;
+                for (int j = 0; j < 24; ++j)
+                    a.dlive[dbase + j * 32] = a.resume ? a.dres[dbase + j * 32] : 0.f;
+            }
+        }
+    } else if constexpr (A1) {
         // a call that resumes the previous one takes up its displacements
         const size_t dbase = (size_t)unit * (kUnitEdges / 2) + lane;
         #pragma unroll
@@ -743,9 +818,11 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
         pm.save = save;
         pm.it = it;
         if (pm.mode == T_MID && !pm.save)
-            tile_pass<false, A1>(a, pm, C, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg, pri);
+            tile_pass<false, A1, MULTI>(a, pm, C, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg,
+                                        pri);
         else
-            tile_pass<true, A1>(a, pm, C, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg, pri);
+            tile_pass<true, A1, MULTI>(a, pm, C, loc, uloc, has_unit, unit, lane, rs, msk, csp, ps, z4, zp4, y4, yp4, stg,
+                                       pri);
         __syncthreads();
         if (!fin) {
             // one partial per (CTA, variable): staged contributions in list
@@ -818,7 +895,18 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
             if (c.stop || fin) {
                 // a check that stops the call stores its state now (alpha = 1;
                 // a check that also saved has stored it in the pass)
-                if (A1 && !fin && !pm.save && has_unit) tile_store_a1(a, pm.reload, unit, lane, rs, csp, z4, zp4, yp4);
+                if (A1 && !fin && !pm.save) {
+                    if constexpr (MULTI) {
+                        for (int lu = warp; lu < C.nunit; lu += (int)(blockDim.x >> 5)) {
+                            int rs_u;
+                            unsigned msk_u, csp_u[4];
+                            unit_desc(a, C.unit0 + lu, lane, rs_u, msk_u, csp_u);
+                            tile_store_a1(a, pm.reload, C.unit0 + lu, lane, rs_u, csp_u, z4, zp4, yp4);
+                        }
+                    } else if (has_unit) {
+                        tile_store_a1(a, pm.reload, unit, lane, rs, csp, z4, zp4, yp4);
+                    }
+                }
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
                     Ctl *ctl = a.ctl;
                     ctl->iters = it - 1;
@@ -905,16 +993,19 @@ cudaError_t tile_floor_launch(const TileArgs &a, long long iters, int mode, int 
     return cudaLaunchCooperativeKernel(fn, dim3(a.G), dim3(block), args, (size_t)smem, s);
 }
 
-static const void *tile_kernel(bool a1) {
-    return a1 ? (const void *)k_tile_sweep<true> : (const void *)k_tile_sweep<false>;
+static const void *tile_kernel(bool a1, bool multi) {
+    if (multi) return a1 ? (const void *)k_tile_sweep<true, true> : (const void *)k_tile_sweep<false, true>;
+    return a1 ? (const void *)k_tile_sweep<true, false> : (const void *)k_tile_sweep<false, false>;
 }
 
 int tile_max_warps() {
     int w = kTileMaxWarps;
     for (bool a1 : {true, false}) {
-        cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, tile_kernel(a1)) != cudaSuccess) return 0;
-        if (fa.maxThreadsPerBlock / 32 < w) w = fa.maxThreadsPerBlock / 32;
+        for (bool multi : {false, true}) {
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, tile_kernel(a1, multi)) != cudaSuccess) return 0;
+            if (fa.maxThreadsPerBlock / 32 < w) w = fa.maxThreadsPerBlock / 32;
+        }
     }
     return w;
 }
@@ -924,7 +1015,7 @@ int tile_smem_bytes(const TilePlan &P) {
 }
 
 cudaError_t tile_sweep_launch(const TileArgs &a, int block, int smem, cudaStream_t s) {
-    const void *fn = tile_kernel(a.alpha == 1.0f);
+    const void *fn = tile_kernel(a.alpha == 1.0f, a.dlive != nullptr);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};

@@ -26,7 +26,8 @@ constexpr int kTileRows = 32;                               // disks per row blo
 constexpr int kTileCols = 8;                                // disks per column group
 constexpr int kUnitEdges = kTileRows * kTileCols * 6;       // storage slots of one unit
 constexpr int kUnitStage = 3 * kTileRows + 3 * kTileCols;   // staged partial sums of one unit
-constexpr int kTileMaxWarps = 16;                           // units (warps) per CTA, at most
+constexpr int kTileMaxWarps = 16;                           // warps per CTA, at most
+constexpr int kTileMaxUnitsMulti = 256;                     // units per CTA, at most (several per warp)
 constexpr int kTileMaxHolders = 255;                        // CTAs holding one variable, at most
 // Per-CTA partial sums are added into one 64-bit word per variable: the
 // count of contributions in the top 8 bits (2^56 per contribution, modulo
@@ -143,6 +144,9 @@ struct TileArgs {
     float *u;                        // per edge (storage order)
     float *dsave;                    // alpha = 1: [U][24][32] displacements kept for the next check
     float *dres;                     // alpha = 1: [U][24][32] displacements of the stored state
+    float *dlive;                    // more units than warps per CTA: [U][24][32] the live
+                                     // displacements (alpha = 1) between a unit's turns; null when
+                                     // every unit has its own warp (state in registers)
     float *lres;                     // alpha = 1: per wall / reward, its displacement parameter
                                      // of the stored state
     const float *zpin;               // alpha = 1: z before the stored state (resume)
@@ -188,6 +192,8 @@ struct TileInput {
 
 struct TilePlan {
     int U = 0, W = 0, G = 0, smax = 0, stgmax = 0, svmax = 0, locmax = 0, clmax = 0;
+    int warps = 0;                      // warps per CTA: W when W <= the kernel's warps, else that
+                                        // maximum (each warp then takes several units in turn)
     int ptot = 0;                       // accumulators per buffer (scalar variables)
     std::vector<int32_t> pair_pos;      // per disk pair (bucket order): unit * 256 + slot * 32 + lane
     std::vector<TileCta> cta;

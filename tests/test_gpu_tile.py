@@ -155,6 +155,57 @@ def test_tile_resume_after_stop_and_alpha():
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("alpha", [1.0, 0.7])
+def test_tile_several_units_per_warp_bit_exact(alpha):
+    """More units than warps in a CTA: with FGA_OPT_BLOCK 64 two warps take
+    each CTA's fourteen units of N = 1000 in turn, their pair state in device
+    memory between passes.  The same CTAs hold the same units, so every
+    operator, staged value and fixed-point sum is the same, and the iterates
+    equal those of one unit per warp bit for bit (the FP64 residual sums to
+    rounding: a thread's partial now spans several units): through checks every 7
+    iterations, then a solve stopping at its tolerance, then a resumed call
+    (the u form for alpha 0.7)."""
+    p = inputs.packing_problem(1000)
+    p.alpha = alpha
+    a = _tile(p)
+    b = graph_from_problem(p, "f32", options={_lib.FGA_OPT_BLOCK: 64})
+    ia, ib = a.fga_launch_info(), b.fga_launch_info()
+    assert ib["zorder"] == 2 and ib["block"] == 64 and ia["block"] > 64 and ia["grid"] == ib["grid"]
+    for ce in (7, 10):
+        ra = a.fga_iterate(60, 1e-3, 1e-3, check_every=ce)
+        rb = b.fga_iterate(60, 1e-3, 1e-3, check_every=ce)
+        # the residual partials are grouped by thread, and a thread now holds
+        # several units: the FP64 sums agree to rounding, the iterates exactly
+        assert (ra["iters"], ra["status"]) == (rb["iters"], rb["status"])
+        np.testing.assert_allclose([rb["r_pri"], rb["r_dual"]], [ra["r_pri"], ra["r_dual"]], rtol=1e-12)
+        assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+        for x, y in zip(_edges(a), _edges(b)):
+            assert np.array_equal(x, y)
+
+
+def test_tile_n2000_several_units_per_warp():
+    """N = 2000 (12M scalar edges): more units per CTA than warps, the disk
+    tiles with their state in device memory between passes.  After 10
+    iterations z agrees with the chunked order and with the FP64 oracle to
+    1e-4 of the variables' scale."""
+    p = inputs.packing_problem(2000)
+    g = _tile(p)
+    info = g.fga_launch_info()
+    assert info["chunks"] > info["grid"] * (info["block"] // 32)
+    r = g.fga_iterate(10)
+    assert r["iters"] == 10 and r["status"] == 0
+    b = graph_from_problem(p, "f32", options={_lib.FGA_OPT_ZORDER: 1})
+    b.fga_iterate(10)
+    o = oracle_from_problem(p)
+    o.iterate(10)
+    S = float(np.max(np.abs(o.z())))
+    zg = g.fga_read_z()
+    e_ch = np.max(np.abs(zg - b.fga_read_z()))
+    e_or = np.max(np.abs(zg - o.z()))
+    print("N=2000 tiles: max |dz| vs chunked %.3e S, vs oracle %.3e S" % (e_ch / S, e_or / S))
+    assert e_ch <= 1e-4 * S and e_or <= 1e-4 * S
+
+
 @pytest.mark.parametrize("ce", [1, 7])
 def test_tile_stop_rule_state(ce):
     """A call that stops at the first checked iteration meeting the
