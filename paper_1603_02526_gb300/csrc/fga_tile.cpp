@@ -307,6 +307,10 @@ int tile_plan(const TileInput &in, TilePlan &P, std::string &why) {
         d.z = 0;
         d.w = k == 0 ? (int)0x80000000u : 0;
     }
+    if (stgmax > 65535) {
+        why = "a CTA stages more than 2^16 values";
+        return 1;
+    }
     P.ptot = (int)std::max<int64_t>(in.nz, 1);
     P.smax = smax;
     P.stgmax = stgmax;

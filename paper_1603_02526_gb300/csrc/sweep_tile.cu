@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     float *uloc = reinterpret_cast<float *>(tsm + L.uloc);
     float *zden = reinterpret_cast<float *>(tsm + L.zden);
     int *cptr = reinterpret_cast<int *>(tsm + L.cptr);
-    int *clist = reinterpret_cast<int *>(tsm + L.clist);
+    unsigned short *clist = reinterpret_cast<unsigned short *>(tsm + L.clist);   // positions < 2^16
     float *stg = reinterpret_cast<float *>(tsm + L.stg);
     unsigned long long *pv = reinterpret_cast<unsigned long long *>(tsm + L.pv);
     float *zt = reinterpret_cast<float *>(z4);
@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
     }
     for (int i = threadIdx.x; i <= C.nsv; i += blockDim.x) cptr[i] = a.cptr[C.sv0 + i] - cbase;
     const int ncl = a.cptr[C.sv0 + C.nsv] - cbase;
-    for (int j = threadIdx.x; j < ncl; j += blockDim.x) clist[j] = a.clist[cbase + j];
+    for (int j = threadIdx.x; j < ncl; j += blockDim.x) clist[j] = (unsigned short)a.clist[cbase + j];
     for (int i = threadIdx.x; i < C.nloc; i += blockDim.x) {
         const TileLocal l = a.loc[C.loc0 + i];
         loc[i] = l;
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(kTileMaxWarps * 32, 1) k_tile_sweep(const Tile
                 for (int j = cptr[i]; j < j1; j += 8) {
                     int idx[8];
                     #pragma unroll
-                    for (int t = 0; t < 8; ++t) idx[t] = j + t < j1 ? clist[j + t] : -1;
+                    for (int t = 0; t < 8; ++t) idx[t] = j + t < j1 ? (int)clist[j + t] : -1;
                     float v[8];
                     #pragma unroll
                     for (int t = 0; t < 8; ++t) v[t] = idx[t] >= 0 ? stg[idx[t]] : 0.f;

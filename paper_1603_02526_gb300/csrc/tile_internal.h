@@ -113,8 +113,8 @@ inline __host__ __device__ TileSmem tile_smem_layout(int smax, int svmax, int lo
     o = tile_align16(o + svmax * 4);
     L.cptr = o;
     o = tile_align16(o + (svmax + 1) * 4);
-    L.clist = o;
-    o = tile_align16(o + clmax * 4);
+    L.clist = o;   // 16-bit staging positions (the planner keeps the staging area below 2^16 values)
+    o = tile_align16(o + clmax * 2);
     L.stg = o;
     o = tile_align16(o + stgmax * 4);
     L.pv = o;   // per slot-var and word: the value seen the last time
