@@ -729,7 +729,7 @@ def run_profile(args):
     elif args.profile_workload == "svm_paper":
         p = inputs.svm_paper_problem(100000, 64, seed=3000, C=1000.0)
     else:
-        p = inputs.packing_problem(N_DISKS, seed=SEED)
+        p = inputs.packing_problem(args.profile_n or N_DISKS, seed=SEED)
     opts = {_lib.FGA_OPT_STORE_M: 0}
     if args.zorder is not None:
         opts[_lib.FGA_OPT_ZORDER] = args.zorder
@@ -761,6 +761,8 @@ def main():
                     choices=["packing", "svm", "mpc_horizon", "mpc_horizon_grid", "svm_paper", "mpc_one",
                              "mpc_batch", "mlp_forward"])
     ap.add_argument("--profile-threads", type=int, default=256, help="CTA size of the mpc_one profiling run")
+    ap.add_argument("--profile-n", type=int, default=0,
+                    help="profiling run of the packing workload: number of disks (default 1000)")
     ap.add_argument("--profile-per-phase", action="store_true",
                     help="profiling run of a graph workload: one launch per update phase instead of the persistent "
                          "kernel")
