@@ -483,6 +483,15 @@ def run_extras(log=None):
                   "algorithmic_bytes_per_iter": svm_bytes,
                   "algorithmic_gbs": svm_bytes * r["iters"] / (r["ms"] * 1e-3) / 1e9,
                   "frac_of_hbm": svm_bytes * r["iters"] / (r["ms"] * 1e-3) / 1e9 / peak, "peak_kind": peak_kind}
+    if g.fga_launch_info()["zorder"] == 3:
+        # the hinge bank's latency floor on its own grid: the count-and-sum
+        # exchange every pass, plus the grid barrier every 10th (the checks)
+        g.fga_latency_floor(200, 1)
+        fl = float(np.median([g.fga_latency_floor(1000, 1) for _ in range(3)])) * 1e3 / 1000
+        br = float(np.median([g.fga_latency_floor(1000, 0) for _ in range(3)])) * 1e3 / 1000
+        us = r["ms"] * 1e3 / r["iters"]
+        out["svm"].update({"us_per_iter": us, "floor_us": fl, "barrier_us": br,
+                           "frac_of_latency_floor": (fl + br / 10) / us})
     del g
     # the SVM in the paper's own form (a copy of w per point, chained by
     # equality factors): time of 100 iterations on the general path, on the

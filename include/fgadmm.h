@@ -290,12 +290,14 @@ int fga_iterate(fga_graph *g, const fga_iter_opts *opts, fga_iter_result *result
  * n >= 7 info[6] the z-order in use (FGA_OPT_ZORDER values).  n >= 6. */
 int fga_launch_info(const fga_graph *g, int64_t *info, int32_t n);
 
-/* Latency floor of the disk-tile order (FGA_OPT_ZORDER 2) on this graph's
- * grid: device time of `iters` passes that do everything an unchecked pass
- * does except the operators -- mode 1: each CTA adds one count-and-sum
- * contribution (value zero) per variable it holds and polls its variables'
- * words until every holder's contribution is in (the z exchange); mode 0:
- * the grid-wide barrier alone (which checked passes add).  A measurement of
+/* Latency floor of the disk-tile and hinge-bank orders (FGA_OPT_ZORDER 2
+ * and 3) on this graph's grid: device time of `iters` passes that do
+ * everything an unchecked pass does except the operators -- mode 1: each CTA
+ * adds one count-and-sum contribution (value zero) per variable it holds
+ * (every variable, in the hinge bank) and polls its variables' words until
+ * every holder's contribution is in (the z exchange); mode 0: the grid-wide
+ * barrier alone (which checked passes add).  FGA_EINVAL for other orders, and
+ * for a graph not finalized.  A measurement of
  * the hardware's floor under a pass (the paper reports where an
  * iteration's time goes, Sec. V-A); the graph's variables and messages are
  * not changed.  *ms: device time (CUDA events). */

@@ -1655,11 +1655,9 @@ static int iterate_tile(fga_graph *g, const fga_iter_opts &o, fga_iter_result &r
     return FGA_OK;
 }
 
-// Hinge bank: one cooperative launch for the whole call (FP32, alpha = 1).
-static int iterate_hinge(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
+static void fill_hinge_args(const fga_graph *g, HingeArgs &a) {
     const HingePlan &H = g->hinge;
     const HingeInput &in = g->hin;
-    HingeArgs a;
     std::memset(&a, 0, sizeof a);
     a.G = H.G;
     a.N = (int)in.N;
@@ -1697,6 +1695,12 @@ static int iterate_hinge(fga_graph *g, const fga_iter_opts &o, fga_iter_result &
     a.E = g->ne;
     a.ctl = g->ctl.as<Ctl>();
     a.sync = g->bar.as<TileSync>();
+}
+
+// Hinge bank: one cooperative launch for the whole call (FP32, alpha = 1).
+static int iterate_hinge(fga_graph *g, const fga_iter_opts &o, fga_iter_result &res) {
+    HingeArgs a;
+    fill_hinge_args(g, a);
     a.k0 = g->iters_done;
     a.K = o.max_iters;
     a.check_every = o.check_every;
@@ -2062,17 +2066,27 @@ extern "C" int fga_shard_stop_rule(const double *pri_parts, int32_t n_shards, do
 extern "C" int fga_latency_floor(fga_graph *g, int64_t iters, int32_t mode, float *ms) {
     if (!g || !ms || iters < 1 || (mode != 0 && mode != 1)) return fail(FGA_EINVAL, "fga_latency_floor: bad argument");
     if (!g->finalized) return fail(FGA_ESTATE, "fga_latency_floor: call fga_finalize first");
-    if (g->zorder != 2) return fail(FGA_EINVAL, "fga_latency_floor: the disk-tile order only");
+    if (g->zorder != 2 && g->zorder != 3)
+        return fail(FGA_EINVAL, "fga_latency_floor: the disk-tile and hinge-bank orders only");
     int rc = set_device(g);
     if (rc) return rc;
-    TileArgs a;
-    fill_tile_args(g, a);
-    a.timeout_ns = 2000000000LL;
     cudaStream_t s = g->stream;
     CUDA_TRY(cudaMemsetAsync(g->bar.p, 0, sizeof(TileSync), s));
-    CUDA_TRY(cudaMemsetAsync(g->t_part.p, 0, g->t_part.bytes, s));   // the next solve zeroes them again
-    CUDA_TRY(cudaEventRecord(g->ev0, s));
-    CUDA_TRY(tile_floor_launch(a, iters, mode, g->blk, g->smem, s));
+    if (g->zorder == 2) {
+        TileArgs a;
+        fill_tile_args(g, a);
+        a.timeout_ns = 2000000000LL;
+        CUDA_TRY(cudaMemsetAsync(g->t_part.p, 0, g->t_part.bytes, s));   // the next solve zeroes them again
+        CUDA_TRY(cudaEventRecord(g->ev0, s));
+        CUDA_TRY(tile_floor_launch(a, iters, mode, g->blk, g->smem, s));
+    } else {
+        HingeArgs a;
+        fill_hinge_args(g, a);
+        a.timeout_ns = 2000000000LL;
+        CUDA_TRY(cudaMemsetAsync(g->h_acc.p, 0, g->h_acc.bytes, s));   // the next solve zeroes them again
+        CUDA_TRY(cudaEventRecord(g->ev0, s));
+        CUDA_TRY(hinge_floor_launch(a, iters, mode, s));
+    }
     CUDA_TRY(cudaEventRecord(g->ev1, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     float t = 0.f;

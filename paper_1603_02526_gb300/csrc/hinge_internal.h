@@ -95,5 +95,8 @@ int hinge_plan(const HingeInput &in, HingePlan &P, std::string &why);
 int hinge_smem_bytes(int rows_max);
 
 cudaError_t hinge_sweep_launch(const HingeArgs &a, int smem, cudaStream_t s);
+// The latency floor of a pass on the same grid (mode 0: barrier; 1: the
+// count-and-sum exchange), `iters` passes.
+cudaError_t hinge_floor_launch(const HingeArgs &a, long long iters, int mode, cudaStream_t s);
 
 }  // namespace fga

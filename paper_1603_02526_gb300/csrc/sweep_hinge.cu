@@ -458,6 +458,61 @@ __global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_sweep(const Hinge
     }
 }
 
+// ---------------------------------------------------------------------------
+// Latency floor of one pass on the same grid (a measurement, not part of a
+// solve).  MODE 0: the grid-wide barrier alone (what a checked pass adds).
+// MODE 1: what an unchecked pass does besides the operators -- every CTA
+// adds one contribution (count, value 0) to each of the D + 1 variables'
+// words, then polls the words until every CTA's contribution of the pass is
+// in.  Needs the words zeroed before the launch.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kHingeWarps * 32, 1) k_hinge_floor(const HingeArgs a, long long iters) {
+    __shared__ unsigned long long s_pv[2 * 80];
+    __shared__ int s_ok;
+    const int NV = a.D + 1;
+    for (int j = threadIdx.x; j < 2 * 80; j += blockDim.x) s_pv[j] = 0ull;
+    __syncthreads();
+    const unsigned long long G = (unsigned long long)a.G;
+    for (long long it = 1; it <= iters; ++it) {
+        if (MODE == 1) {
+            const int par = (int)(it & 1);
+            if (threadIdx.x == 0) s_ok = 1;
+            __syncthreads();
+            if (threadIdx.x < NV) {
+                const int j = threadIdx.x;
+                unsigned long long *w = a.acc + (size_t)par * NV * kHingeAccStride + (size_t)j * kHingeAccStride;
+                red_add_u64(w, kTileCountUnit);
+                const unsigned long long p = s_pv[par * 80 + j];
+                unsigned long long v = ld_relaxed_u64(w);
+                const unsigned long long t0 = global_ns();
+                unsigned int spins = 0;
+                while (tile_count(v - p) != (unsigned)G) {
+                    if ((++spins & 63u) == 0u &&
+                        (*(volatile int *)&a.sync->error || global_ns() - t0 > (unsigned long long)a.timeout_ns ||
+                         spins > (1u << 30))) {
+                        atomicCAS(&a.sync->error, 0, kETimeout);
+                        s_ok = 0;
+                        break;
+                    }
+                    v = ld_relaxed_u64(w);
+                }
+                s_pv[par * 80 + j] = v;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+        } else if (!tile_barrier(a.sync, G * (unsigned long long)it, a.timeout_ns, false)) {
+            return;
+        }
+    }
+}
+
+cudaError_t hinge_floor_launch(const HingeArgs &a, long long iters, int mode, cudaStream_t s) {
+    const void *fn = mode == 0 ? (const void *)k_hinge_floor<0> : (const void *)k_hinge_floor<1>;
+    void *args[] = {(void *)&a, (void *)&iters};
+    return cudaLaunchCooperativeKernel(fn, dim3(a.G), dim3(kHingeWarps * 32), args, 0, s);
+}
+
 cudaError_t hinge_sweep_launch(const HingeArgs &a, int smem, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute((const void *)k_hinge_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

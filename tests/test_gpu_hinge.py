@@ -160,3 +160,27 @@ def test_hinge_rejections():
     g = _hinge(p)
     with pytest.raises(_lib.FgaError):
         g.fga_iterate(10, fused=False)
+
+
+def test_hinge_latency_floor_leaves_the_solve_unchanged():
+    """The operator-free floor (both modes) runs on the hinge bank's own
+    grid and count-and-sum words: positive device times, and a solve split
+    around floor calls bit-equal to one without them (the words are zeroed
+    again); other orders and modes are refused."""
+    p = inputs.svm_problem(5000, 64, seed=3400)
+    a = _hinge(p)
+    a.fga_iterate(200, check_every=10)
+    b = _hinge(p)
+    b.fga_iterate(100, check_every=10)
+    ms1 = b.fga_latency_floor(500, 1)
+    ms0 = b.fga_latency_floor(500, 0)
+    assert ms1 > 0 and ms0 > 0
+    b.fga_iterate(100, check_every=10)
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+    for x, y in zip(_edges(a), _edges(b)):
+        assert np.array_equal(x, y)
+    c = graph_from_problem(p, "f32", options={_lib.FGA_OPT_ZORDER: 1})
+    with pytest.raises(_lib.FgaError):
+        c.fga_latency_floor(10, 1)
+    with pytest.raises(_lib.FgaError):
+        b.fga_latency_floor(10, 2)

@@ -280,3 +280,21 @@ def test_tile_rejections():
     g = _tile(p)
     with pytest.raises(_lib.FgaError):
         g.fga_iterate(10, fused=False)
+
+
+def test_tile_latency_floor_leaves_the_solve_unchanged():
+    """The operator-free floor (both modes) on the disk-tile grid: positive
+    device times, and a solve split around floor calls bit-equal to one
+    without them (the count-and-sum words are zeroed again)."""
+    p = inputs.packing_problem(200)
+    a = _tile(p)
+    a.fga_iterate(200, check_every=10)
+    b = _tile(p)
+    b.fga_iterate(100, check_every=10)
+    ms1 = b.fga_latency_floor(500, 1)
+    ms0 = b.fga_latency_floor(500, 0)
+    assert ms1 > 0 and ms0 > 0
+    b.fga_iterate(100, check_every=10)
+    assert np.array_equal(a.fga_read_z(), b.fga_read_z())
+    for x, y in zip(_edges(a), _edges(b)):
+        assert np.array_equal(x, y)
