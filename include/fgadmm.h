@@ -108,8 +108,10 @@ extern "C" {
                                  radius rewards), FP32, one rho and one
                                  alpha, m not kept -- a warp holds 32 x 8
                                  disk pairs' state in registers, x is
-                                 recomputed from u and the previous z, one
-                                 grid-wide barrier per iteration; fused
+                                 recomputed from u and the previous z, the
+                                 CTAs' per-variable sums exchanged through
+                                 count-and-sum words (a grid-wide barrier
+                                 on checked iterations only); fused
                                  launches only; 3 = hinge bank: a linear
                                  soft-margin SVM only (Sec. V-C: hinge
                                  factors on one shared (w, b), dim(w) <= 64,
@@ -117,8 +119,8 @@ extern "C" {
                                  alpha = 1, m not kept -- each CTA keeps its
                                  slice of the data rows in shared memory and
                                  one value of state per hinge factor in
-                                 registers, one grid-wide barrier per
-                                 iteration; fused launches only; 4 =
+                                 registers, the sums exchanged as in 2;
+                                 fused launches only; 4 =
                                  scatter: each edge's rho*m goes straight to
                                  a per-variable column (the variable's k-th
                                  edge in creation order to column k < W, W

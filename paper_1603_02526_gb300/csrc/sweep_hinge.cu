@@ -19,9 +19,11 @@
 // row is read once per iteration (two 16-byte loads per lane) and the dot
 // product needs three shuffles.  The groups' sums are combined per warp
 // (two shuffles), per CTA (in shared memory, fixed warp order) and across
-// CTAs in the fixed-point accumulators (exact, order-free); one grid
-// barrier per iteration.  Checks form x, u and the FP64 residual sums from
-// the same quantities and store the state.
+// CTAs in the fixed-point accumulators (exact, order-free), each word
+// carrying a count of the contributions it holds: a CTA starts its next
+// pass once every word counts all CTAs, and only checked passes add a grid
+// barrier.  Checks form x, u and the FP64 residual sums from the same
+// quantities and store the state.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -1,7 +1,8 @@
 """GPU parity of the hinge-bank sweep (FGA_OPT_ZORDER 3: a linear
 soft-margin SVM in FP32 with alpha = 1, one scalar of state per hinge
-factor, the data rows in shared memory, one grid barrier per iteration)
-against the FP64 oracle and against the chunked order, through the C-ABI.
+factor, the data rows in shared memory, the z exchange through
+count-and-sum words, a grid barrier on checked passes only) against the
+FP64 oracle and against the chunked order, through the C-ABI.
 
 FP32 rule: z and the edge messages are compared on the scale S of the
 variables; a hinge whose margin sits at a rounding-level distance from 1

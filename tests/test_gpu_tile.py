@@ -1,6 +1,7 @@
 """GPU parity of the disk-tile sweep (FGA_OPT_ZORDER 2: FP32 circle packing,
-disk-pair state in registers, x recomputed, one grid barrier per
-iteration) against the FP64 oracle and against the chunked fast order,
+disk-pair state in registers, x recomputed, the z exchange through
+count-and-sum words, a grid barrier on checked passes only) against the
+FP64 oracle and against the chunked fast order,
 through the C-ABI.
 
 FP32 rule (as for the chunked order): z and the edge messages are compared
