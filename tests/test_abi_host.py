@@ -86,6 +86,13 @@ def test_validation_errors(lib):
     out = np.zeros(6)
     assert lib.fga_read_z(g, P(out.ctypes.data), 6) == FGA_ESTATE
     assert lib.fga_init(g, None, None) == FGA_ESTATE
+    # the latency floor: arguments first, then a finalized graph
+    ms = ctypes.c_float()
+    assert lib.fga_latency_floor(None, 10, 1, ctypes.byref(ms)) == FGA_EINVAL
+    assert lib.fga_latency_floor(g, 0, 1, ctypes.byref(ms)) == FGA_EINVAL
+    assert lib.fga_latency_floor(g, 10, 2, ctypes.byref(ms)) == FGA_EINVAL
+    assert lib.fga_latency_floor(g, 10, 1, None) == FGA_EINVAL
+    assert lib.fga_latency_floor(g, 10, 1, ctypes.byref(ms)) == FGA_ESTATE
     e, z, f, v = (ctypes.c_int64() for _ in range(4))
     assert lib.fga_graph_info(g, ctypes.byref(e), ctypes.byref(z), ctypes.byref(f), ctypes.byref(v)) == 0
     assert (e.value, z.value, f.value, v.value) == (6, 6, 1, 4)
