@@ -466,6 +466,20 @@ def run_extras(log=None):
                      "frac_of_hbm": 20 * p.num_edges * 100 / (r["ms"] * 1e-3) / 1e9 / peak}
         del g
     out["packing_n2000_f32"] = row
+    # the paper's area objective -r^2/2 (its prox needs rho > 1; rho 25) on
+    # the N = 1000 graph: 2000 iterations in the library's default order
+    p = inputs.packing_problem(1000, seed=SEED, reward="quad", rho=25.0)
+    g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 0})
+    g.fga_iterate(20, check_every=20)
+    g.fga_init(p.z0)
+    r = g.fga_iterate(ITERS, check_every=ITERS)
+    out["packing_area_f32"] = {"workload": "circle packing N=1000 with the area reward -r^2/2, rho 25, FP32, "
+                                           "%d iterations, the library's default order" % ITERS,
+                               "scalar_edges": p.num_edges, "zorder": g.fga_launch_info()["zorder"],
+                               "iters": r["iters"], "status": r["status"], "ms": r["ms"],
+                               "us_per_iter": r["ms"] * 1e3 / r["iters"],
+                               "edge_updates_per_s": p.num_edges * r["iters"] / (r["ms"] * 1e-3)}
+    del g
     # SVM
     p = inputs.svm_problem(100000, 64, seed=3000)
     g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 0})

@@ -4,7 +4,8 @@ A plain NumPy restatement, in single precision, of the iteration of Sec. II
 (x = Prox(n) per factor, m = x + u, z = sum rho m / sum rho, u += alpha (x - z),
 n = z - u) with the Appendix A operators as the FP64 oracle reads them (the
 no-collision operator with the radii moved down, walls with unit inward
-normals, the linear radius reward x = n + w / rho).  Every value is rounded
+normals, the linear radius reward x = n + w / rho, the area reward
+x = rho n / (rho - 1) written as n + n / (rho - 1)).  Every value is rounded
 to FP32 after each operation (NumPy float32 arithmetic); z sums each
 variable's terms one by one in creation order in FP32.  Uniform rho and
 alpha only.
@@ -30,9 +31,10 @@ class PackingFP32:
         blocks = {b.ftype: b for b in p.factor_blocks}
         pair = blocks.get(inputs.PACK_PAIR)
         wall = blocks[inputs.PACK_WALL]
-        rew = blocks[inputs.PACK_RADIUS_LIN]
+        self.area = inputs.PACK_RADIUS_QUAD in blocks
+        rew = blocks[inputs.PACK_RADIUS_QUAD if self.area else inputs.PACK_RADIUS_LIN]
         if len(p.factor_blocks) != (3 if pair is not None else 2):
-            raise ValueError("packing graphs only (pairs, walls, linear rewards)")
+            raise ValueError("packing graphs only (pairs, walls, one kind of radius reward)")
         self.rho = f32(p.rho)
         self.alpha = f32(p.alpha)
         dims = p.var_dims()
@@ -54,7 +56,7 @@ class PackingFP32:
         self.nwall = wall.var_ids.shape[0]
         self.wQ = wall.params[:, 0:2].astype(f32)
         self.wV = wall.params[:, 2:4].astype(f32)
-        self.w = rew.params[:, 0].astype(f32)
+        self.w = None if self.area else rew.params[:, 0].astype(f32)
         self.e_wall = 6 * self.npair
         self.e_rew = self.e_wall + 3 * self.nwall
         self.z = p.z0.astype(f32)
@@ -100,7 +102,11 @@ class PackingFP32:
         lam = np.where(h < 0, -h * f32(0.5), f32(0))   # one rho, |Q| = 1
         o = np.stack([q[:, 0] + lam * qx, q[:, 1] + lam * qy, q[:, 2] - lam], 1)
         x[self.e_wall:self.e_rew] = o.ravel()
-        x[self.e_rew:] = n[self.e_rew:] + self.w / self.rho
+        if self.area:
+            q = n[self.e_rew:]
+            x[self.e_rew:] = q + q * f32(1.0 / (float(self.rho) - 1.0))
+        else:
+            x[self.e_rew:] = n[self.e_rew:] + self.w / self.rho
 
     def iterate(self, k=1):
         for _ in range(k):

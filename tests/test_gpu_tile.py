@@ -299,3 +299,31 @@ def test_tile_latency_floor_leaves_the_solve_unchanged():
     assert np.array_equal(a.fga_read_z(), b.fga_read_z())
     for x, y in zip(_edges(a), _edges(b)):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("iters", [3, 10])
+def test_tile_n1000_area_reward_against_oracle(iters):
+    """The paper's area reward -r^2/2 on the N = 1000 graph (rho 25, the
+    prox needs rho > 1), under the same bounds as the linear reward's
+    benchmark graph: z and the edge messages at the 99.9th percentile and
+    at the maximum within 2x the FP32 emulation's own distance from the
+    FP64 oracle; residuals to 1e-3 relative."""
+    from tests.fp32_emulation import PackingFP32
+    p = inputs.packing_problem(1000, reward="quad", rho=25.0)
+    g = _tile(p)
+    r = g.fga_iterate(iters)
+    assert r["iters"] == iters
+    o = oracle_from_problem(p)
+    ro = o.iterate(iters)
+    em = PackingFP32(p, sums="exact")
+    em.iterate(iters)
+    S = float(np.max(np.abs(o.z())))
+    ez = np.abs(g.fga_read_z() - o.z()).max()
+    assert ez <= 2 * np.abs(em.z - o.z()).max(), (ez / S, np.abs(em.z - o.z()).max() / S)
+    for got, w, ref in zip(_edges(g), (EDGE_X, EDGE_U, EDGE_N), (em.x, em.u, em.n)):
+        err = np.abs(got - o.edge(w))
+        eref = np.abs(ref.astype(np.float64) - o.edge(w))
+        for q in (99.9, 100):
+            assert np.percentile(err, q) <= 2 * np.percentile(eref, q), (w, q, np.percentile(err, q) / S,
+                                                                            np.percentile(eref, q) / S)
+    np.testing.assert_allclose([r["r_pri"], r["r_dual"]], [ro["r_pri"], ro["r_dual"]], rtol=1e-3)
