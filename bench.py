@@ -30,6 +30,20 @@ sys.path.insert(0, ROOT)
 
 N_DISKS = 1000
 ITERS = 2000
+# user operators of the user-operator extra: 1/2 q v^2 per component and the
+# box [p0, p1] (the library's own quadratic-cost and box types, restated)
+USER_QUAD0 = r"""
+template <typename R>
+void quad0(int d, const R *n, const R *rho, const R *p, R *x) {
+    for (int k = 0; k < d; ++k) x[k] = (rho[k] * n[k]) / (p[k] + rho[k]);
+}
+"""
+USER_BOX = r"""
+template <typename R>
+void box(int d, const R *n, const R *rho, const R *p, R *x) {
+    for (int k = 0; k < d; ++k) x[k] = fmin(fmax(n[k], p[0]), p[1]);
+}
+"""
 SEED = 1000 * 1 + 0       # config index x 1000 + replicate
 BYTES_PER_EDGE_ITER = 20  # algorithmic: read u, read m|x, write u, write m|x, read m (FP32)
 METRIC = "edge-updates/s"
@@ -480,6 +494,56 @@ def run_extras(log=None):
                                "us_per_iter": r["ms"] * 1e3 / r["iters"],
                                "edge_updates_per_s": p.num_edges * r["iters"] / (r["ms"] * 1e-3)}
     del g
+    # three weights (zero / standard / infinite weight classes set by each
+    # x-update): the N = 1000 packing in FP64, canonical order, 100
+    # iterations with and without them
+    p = inputs.packing_problem(1000, seed=SEED)
+    tw = {"workload": "circle packing N=1000, FP64, canonical z order, 100 iterations: standard ADMM and the "
+                      "three-weight mode (FGA_OPT_WEIGHTS 1)", "scalar_edges": p.num_edges}
+    for name, opts in (("standard", {_lib.FGA_OPT_ZORDER: 0}), ("three_weights", {_lib.FGA_OPT_WEIGHTS: 1})):
+        g = graph_from_problem(p, "f64", options=opts)
+        g.fga_iterate(5, check_every=5)
+        g.fga_init(p.z0)
+        r = g.fga_iterate(100, check_every=100)
+        tw[name] = {"zorder": g.fga_launch_info()["zorder"], "ms_100_iters": r["ms"],
+                    "edge_updates_per_s": p.num_edges * 100 / (r["ms"] * 1e-3)}
+        del g
+    out["three_weights"] = tw
+    # user-supplied operators (CUDA source compiled at run time): a chain of
+    # 100,000 three-dimensional blocks, each with a quadratic cost and a box,
+    # neighbours equal; the cost and the box as user operators against the
+    # library's own types, FP32, one launch per phase
+    from paper_1603_02526_gb300.graph import FactorGraph
+    T, dd = 100000, 3
+    rng = np.random.default_rng(SEED + 7)
+    qv = rng.uniform(0.1, 10.0, (T, dd))
+    z0 = rng.normal(0.0, 1.0, T * dd)
+    ids = np.arange(T, dtype=np.int64)[:, None]
+    us = {"workload": "chain of 100,000 blocks in R^3: quadratic cost and box [-0.4, 0.6] per block, equality "
+                      "between neighbours; FP32, 100 iterations, one launch per phase; the cost and the box as "
+                      "user operators (fga_register_prox) and as the library's own types"}
+    for name in ("user", "builtin"):
+        g = FactorGraph("f32", 0)
+        g.fga_add_variables(T, dd)
+        if name == "user":
+            tq = g.fga_register_prox(USER_QUAD0, "quad0", dd, dd)
+            tb = g.fga_register_prox(USER_BOX, "box", dd, 2)
+        else:
+            tq, tb = inputs.MPC_QUAD, inputs.MPC_BOX
+        g.fga_add_factors(tq, ids, qv)
+        g.fga_add_factors(tb, ids, np.broadcast_to(np.array([-0.4, 0.6]), (T, 2)))
+        g.fga_add_factors(inputs.EQUAL, np.stack([np.arange(T - 1), np.arange(1, T)], axis=1))
+        g.fga_finalize()
+        g.fga_init(z0)
+        g.fga_iterate(20, check_every=20, fused=False)
+        g.fga_init(z0)
+        r = g.fga_iterate(100, check_every=100, fused=False)
+        E = g.num_edges
+        us[name] = {"zorder": g.fga_launch_info()["zorder"], "ms_100_iters": r["ms"],
+                    "edge_updates_per_s": E * 100 / (r["ms"] * 1e-3)}
+        us["scalar_edges"] = E
+        del g
+    out["user_operators"] = us
     # SVM
     p = inputs.svm_problem(100000, 64, seed=3000)
     g = graph_from_problem(p, "f32", options={_lib.FGA_OPT_STORE_M: 0})

@@ -1211,9 +1211,7 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
         // the standard ones; z from the first non-empty group
         for (long long b = gtid; b < a.nz; b += gstride) {
             R S = R(0), Rr = R(0), Ss = R(0), Rs = R(0), Si = R(0), Ni = R(0);
-            for (int k = a.row[b]; k < a.row[b + 1]; ++k) {
-                const R v = ldg_l2(a.pvm + k);
-                const int c = a.pwcls[k];
+            auto add = [&](int k, R v, int c) {
                 if (c == 2) {
                     Si += v;
                     Ni += R(1);
@@ -1226,7 +1224,23 @@ __device__ __forceinline__ void phase_z(const SweepArgs<R> &a, const R *zo, R *z
                         Rs += r;
                     }
                 }
+            };
+            const int k1 = a.row[b + 1];
+            int k = a.row[b];
+            // eight messages and classes loaded together, then added one by
+            // one in creation order (the same sums as one at a time)
+            for (; k + 8 <= k1; k += 8) {
+                R v[8];
+                int c[8];
+                #pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    v[t] = ldg_l2(a.pvm + k + t);
+                    c[t] = a.pwcls[k + t];
+                }
+                #pragma unroll
+                for (int t = 0; t < 8; ++t) add(k + t, v[t], c[t]);
             }
+            for (; k < k1; ++k) add(k, ldg_l2(a.pvm + k), a.pwcls[k]);
             const R zold = zo[b];
             R znew = zold;
             if (Ni > R(0)) znew = Si / Ni;
