@@ -16,6 +16,9 @@ MUTANTS = [
     ("radius reward sign",
      "x[0] = n[0] + p[0] / rho[0];", "x[0] = n[0] - p[0] / rho[0];",
      [(prox.test_radius_rewards, dict(rho=r)) for r in (0.5, 1.0, 3.0)]),
+    ("area reward with rho + 1 in the denominator",
+     "x[0] = (rho[0] * n[0]) / (rho[0] - 1.0);", "x[0] = (rho[0] * n[0]) / (rho[0] + 1.0);",
+     [(prox.test_radius_rewards, dict(rho=3.0))]),
     ("wall weights swapped",
      "double wc = 1.0 / rho[0], wr = 1.0 / rho[2];", "double wc = 1.0 / rho[2], wr = 1.0 / rho[0];",
      [(prox.test_pack_wall_matches_bruteforce, dict(seed=s)) for s in range(10)]),
