@@ -19,6 +19,21 @@ MUTANTS = [
     ("area reward with rho + 1 in the denominator",
      "x[0] = (rho[0] * n[0]) / (rho[0] - 1.0);", "x[0] = (rho[0] * n[0]) / (rho[0] + 1.0);",
      [(prox.test_radius_rewards, dict(rho=3.0))]),
+    ("disk pair: radii moved up",
+     "x[2] = n[2] - tr1;", "x[2] = n[2] + tr1;",
+     [(prox.test_pack_pair_matches_bruteforce, dict(seed=s)) for s in range(4)]),
+    ("disk pair: shares by rho instead of 1 / rho",
+     "double wc1 = 1.0 / rho[0], wr1 = 1.0 / rho[2];", "double wc1 = rho[0], wr1 = rho[2];",
+     [(prox.test_pack_pair_matches_bruteforce, dict(seed=s)) for s in range(4)]),
+    ("L2 factor: lambda subtracted",
+     "x[j] = (rho[j] * n[j]) / (rho[j] + p[0]);", "x[j] = (rho[j] * n[j]) / (rho[j] - p[0]);",
+     [(prox.test_svm_l2_and_quad, dict(lam=l)) for l in (1.0, 5.0)]),
+    ("quadratic cost: q in the numerator",
+     "x[j] = (rho[j] * n[j]) / (p[j] + rho[j]);", "x[j] = (p[j] * n[j]) / (p[j] + rho[j]);",
+     [(prox.test_svm_l2_and_quad, dict(lam=1.0))]),
+    ("box: upper violations clamped to the lower bound",
+     "if (v > hi) v = hi;", "if (v > hi) v = lo;",
+     [(prox.test_box_and_fix, {})]),
     ("wall weights swapped",
      "double wc = 1.0 / rho[0], wr = 1.0 / rho[2];", "double wc = 1.0 / rho[2], wr = 1.0 / rho[0];",
      [(prox.test_pack_wall_matches_bruteforce, dict(seed=s)) for s in range(10)]),
