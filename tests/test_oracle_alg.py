@@ -413,7 +413,13 @@ def test_two_factor_weighted_rho_and_alpha_by_hand():
       1/2 + 1/2 (4 - 57/16)) = (-69/32, 23/32);  n = (183/32, 91/32).
     Every value is a dyadic rational, so FP64 holds it exactly.  An
     unweighted mean would give z = 2 after iteration 1, and alpha taken as 1
-    would give u = (-3, 1)."""
+    would give u = (-3, 1).
+
+    Residuals (RMS over the two edges): iteration 1, x - z = (-3, 1) and
+    rho (z - z_prev) = (3, 9), so r_pri = sqrt(10 / 2) and r_dual =
+    sqrt(90 / 2); iteration 2, x - z = (-21/16, 7/16) and rho (z - z_prev) =
+    (9/16, 27/16), so r_pri = sqrt(490 / 512) and r_dual = sqrt(810 / 512).
+    Without rho in the dual residual it would be sqrt(9) after iteration 1."""
     g = OracleGraph()
     g.add_variables(1, 1)
     g.add_factors(inputs.MPC_QUAD, [[0]], [[1.0]])
@@ -421,11 +427,13 @@ def test_two_factor_weighted_rho_and_alpha_by_hand():
     g.finalize(np.array([1.0, 3.0]), np.array([0.5, 0.5]))
     g.init(np.array([0.0]))
     want = [
-        dict(x=[0.0, 4.0], m=[0.0, 4.0], z=[3.0], u=[-1.5, 0.5], n=[4.5, 2.5]),
-        dict(x=[2.25, 4.0], m=[0.75, 4.5], z=[57 / 16], u=[-69 / 32, 23 / 32], n=[183 / 32, 91 / 32]),
+        dict(x=[0.0, 4.0], m=[0.0, 4.0], z=[3.0], u=[-1.5, 0.5], n=[4.5, 2.5], r=(10 / 2, 90 / 2)),
+        dict(x=[2.25, 4.0], m=[0.75, 4.5], z=[57 / 16], u=[-69 / 32, 23 / 32], n=[183 / 32, 91 / 32],
+             r=(490 / 512, 810 / 512)),
     ]
     for w in want:
-        g.iterate(1)
+        r = g.iterate(1)
+        np.testing.assert_allclose([r["r_pri"], r["r_dual"]], np.sqrt(w["r"]), rtol=1e-15)
         assert list(g.edge(EDGE_X)) == w["x"]
         assert list(g.edge(EDGE_M)) == w["m"]
         assert list(g.z()) == w["z"]

@@ -34,6 +34,12 @@ MUTANTS = [
     ("box: upper violations clamped to the lower bound",
      "if (v > hi) v = hi;", "if (v > hi) v = lo;",
      [(prox.test_box_and_fix, {})]),
+    ("dual residual without rho",
+     "double s = g->rho[e] * (g->z[b] - g->zprev[b]);", "double s = (g->z[b] - g->zprev[b]);",
+     [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {})]),
+    ("primal residual against the previous z",
+     "double r = g->x[e] - g->z[b];", "double r = g->x[e] - g->zprev[b];",
+     [(alg.test_residual_definition_and_stop_rule, {}), (alg.test_two_factor_weighted_rho_and_alpha_by_hand, {})]),
     ("wall weights swapped",
      "double wc = 1.0 / rho[0], wr = 1.0 / rho[2];", "double wc = 1.0 / rho[2], wr = 1.0 / rho[0];",
      [(prox.test_pack_wall_matches_bruteforce, dict(seed=s)) for s in range(10)]),
