@@ -40,6 +40,14 @@ MUTANTS = [
     ("primal residual against the previous z",
      "double r = g->x[e] - g->z[b];", "double r = g->x[e] - g->zprev[b];",
      [(alg.test_residual_definition_and_stop_rule, {}), (alg.test_two_factor_weighted_rho_and_alpha_by_hand, {})]),
+    ("m-update with u subtracted",
+     "for (int64_t e = 0; e < E; ++e) g->m[e] = g->x[e] + g->u[e];",
+     "for (int64_t e = 0; e < E; ++e) g->m[e] = g->x[e] - g->u[e];",
+     [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {}), (alg.test_alg1_equals_alg2_scalar_consensus, {})]),
+    ("n-update with u added",
+     "for (int64_t e = 0; e < E; ++e) g->n[e] = g->z[g->ez[e]] - g->u[e];",
+     "for (int64_t e = 0; e < E; ++e) g->n[e] = g->z[g->ez[e]] + g->u[e];",
+     [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {}), (alg.test_residual_definition_and_stop_rule, {})]),
     ("wall weights swapped",
      "double wc = 1.0 / rho[0], wr = 1.0 / rho[2];", "double wc = 1.0 / rho[2], wr = 1.0 / rho[0];",
      [(prox.test_pack_wall_matches_bruteforce, dict(seed=s)) for s in range(10)]),
