@@ -48,6 +48,12 @@ MUTANTS = [
      "for (int64_t e = 0; e < E; ++e) g->n[e] = g->z[g->ez[e]] - g->u[e];",
      "for (int64_t e = 0; e < E; ++e) g->n[e] = g->z[g->ez[e]] + g->u[e];",
      [(alg.test_two_factor_weighted_rho_and_alpha_by_hand, {}), (alg.test_residual_definition_and_stop_rule, {})]),
+    ("stop rule on the primal residual alone",
+     "if (rpri <= tol_pri && rdual <= tol_dual) break;", "if (rpri <= tol_pri) break;",
+     [(alg.test_residual_definition_and_stop_rule, {})]),
+    ("stop rule on the dual residual alone",
+     "if (rpri <= tol_pri && rdual <= tol_dual) break;", "if (rdual <= tol_dual) break;",
+     [(alg.test_residual_definition_and_stop_rule, {})]),
     ("wall weights swapped",
      "double wc = 1.0 / rho[0], wr = 1.0 / rho[2];", "double wc = 1.0 / rho[2], wr = 1.0 / rho[0];",
      [(prox.test_pack_wall_matches_bruteforce, dict(seed=s)) for s in range(10)]),
