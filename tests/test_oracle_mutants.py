@@ -1,8 +1,9 @@
 """Planted mistakes in the oracle: each case builds a copy of the oracle with
 one plausible error (a wrong sign, swapped weights, a transposed operand, a
 dropped term) and runs the pins that cover that part against it; at least
-one of them must fail.  The mistakes exist only in temporary builds; the
-oracle itself is untouched."""
+one of them must fail.  The mistakes exist only in temporary builds (the C
+oracle) or in modified copies loaded for one test (the network's Python
+reference); the oracle itself is untouched."""
 import pytest
 
 from oracle import oracle as orc
@@ -125,4 +126,44 @@ def test_planted_mistake_fails_a_pin(tmp_path, name, old, new, pins):
                 pin(**kw)
             except Exception as e:   # an assertion, or a solver the mistake derailed
                 failed.append("%s(%s): %s" % (pin.__name__, kw, type(e).__name__))
+    assert failed, "no pin caught the planted mistake '%s'" % name
+
+
+# Planted mistakes in the warm-start network's FP64 reference
+# (oracle/mlp_oracle.py): each is loaded as a modified copy of the module in
+# place of the real one inside tests/test_oracle_mlp.py, whose pins must
+# then fail.
+MLP_MUTANTS = [
+    ("loss gradient without the factor 2", "dY = 2.0 * D / n", "dY = D / n",
+     ["test_gradients_match_finite_differences"]),
+    ("second hidden layer masked by the first layer's activations",
+     'dH2 = r((dYq @ f["W3q"]) * (f["H2"] > 0))', 'dH2 = r((dYq @ f["W3q"]) * (f["H1"] > 0))',
+     ["test_gradients_match_finite_differences"]),
+    ("W2 gradient against the wrong activations", 'gW2 = dH2.T @ f["H1"]', 'gW2 = dH2.T @ f["H2"]',
+     ["test_gradients_match_finite_differences"]),
+    ("Adam without bias correction", "mh = m / (1 - b1 ** step)", "mh = m",
+     ["test_adam_closed_form_first_step"]),
+    ("bfloat16 by truncation", "u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u = u & 0xFFFF0000",
+     ["test_bf16_rounding"]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
+def test_planted_mlp_mistake_fails_a_pin(monkeypatch, name, old, new, pins):
+    import types
+
+    from oracle import mlp_oracle
+    from tests import test_oracle_mlp as mlp_pins
+    with open(mlp_oracle.__file__) as fh:
+        src = fh.read()
+    assert src.count(old) == 1, "the planted line must match the module source exactly once"
+    mutant = types.ModuleType("mlp_oracle_mutant")
+    exec(compile(src.replace(old, new), "mlp_oracle_mutant", "exec"), mutant.__dict__)
+    monkeypatch.setattr(mlp_pins, "mo", mutant)
+    failed = []
+    for pin in pins:
+        try:
+            getattr(mlp_pins, pin)()
+        except Exception as e:   # an assertion, or arithmetic the mistake derailed
+            failed.append("%s: %s" % (pin, type(e).__name__))
     assert failed, "no pin caught the planted mistake '%s'" % name
