@@ -228,3 +228,91 @@ def test_register_prox_argument_checks(lib):
     assert lib.fga_add_factors(g, FGA_USER_TYPE0, 1, 1, ctypes.c_void_p(one.ctypes.data), None, 0, 0,
                                None) == FGA_EINVAL
     assert lib.fga_destroy(g) == 0
+
+
+def test_batch_network_and_handle_validation(lib):
+    """Entry points outside the graph object reject bad input on the host
+    with FGA_EINVAL and a message naming the call; NULL handles are
+    rejected, NULL destroys are no-ops, and a graph not yet finalized gives
+    FGA_ESTATE.  Every call here fails its checks before any device work."""
+    from paper_1603_02526_gb300._lib import FGA_EINVAL, FGA_ESTATE, fga_iter_opts, fga_iter_result
+    P = ctypes.c_void_p
+    ptr = lambda a: P(a.ctypes.data)
+    nx, nu, n = 3, 1, 2
+    T = np.array([5, 7], dtype=np.int32)
+    A = np.eye(nx)
+    B = np.ones((nx, nu))
+    q = np.ones(nx)
+    r = np.ones(nu)
+    out = P()
+
+    def batch(**kw):
+        a = dict(out=ctypes.byref(out), prec=1, n=n, T=ptr(T), nx=nx, nu=nu, nsys=1, sys=None, A=ptr(A),
+                 B=ptr(B), q=ptr(q), r=ptr(r), umax=1.0, rho=1.0, alpha=1.0)
+        a.update(kw)
+        return lib.fga_mpc_batch_create(a["out"], a["prec"], 0, None, a["n"], a["T"], a["nx"], a["nu"],
+                                        a["nsys"], a["sys"], a["A"], a["B"], a["q"], a["r"], a["umax"],
+                                        a["rho"], a["alpha"])
+
+    qneg = -np.ones(nx)
+    for kw in (dict(out=None), dict(prec=5), dict(nx=0), dict(nx=30, nu=5), dict(rho=0.0), dict(umax=-1.0),
+               dict(nsys=2, n=3), dict(q=ptr(qneg)), dict(T=None)):
+        assert batch(**kw) == FGA_EINVAL, kw
+        assert b"fga_mpc_batch_create" in lib.fga_last_error(), kw
+
+    m = P()
+    assert lib.fga_mlp_create(None, 12, 64, 64, 16, 64, 1, 0, None) == FGA_EINVAL
+    for shape in ((12, 60, 64, 16, 64), (12, 64, 64, 16, 4), (0, 64, 64, 16, 64), (12, 64, 64, 12, 64)):
+        assert lib.fga_mlp_create(ctypes.byref(m), *shape, 1, 0, None) == FGA_EINVAL, shape
+        assert b"fga_mlp_create" in lib.fga_last_error()
+
+    f = lib.fga_mpc_solve_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, ctypes.c_float, ctypes.c_float,
+                  ctypes.c_float, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, P, P, P, P]
+    buf = np.zeros(64, dtype=np.float32)
+    b = ptr(buf)
+
+    def noalloc(**kw):
+        a = dict(n=n, T=ptr(T), nx=nx, nu=nu, umax=1.0, rho=1.0, alpha=1.0, iters=100, tol=1e-4, ce=1, z=b)
+        a.update(kw)
+        return f(a["n"], a["T"], a["nx"], a["nu"], b, b, b, b, b, a["umax"], a["rho"], a["alpha"], a["iters"],
+                 a["tol"], a["ce"], a["z"], b, b, None)
+
+    T0 = np.array([5, 0], dtype=np.int32)
+    Tbig = np.array([5, 100001], dtype=np.int32)
+    for kw in (dict(n=0), dict(n=4097), dict(nx=33), dict(nx=0), dict(nu=0), dict(rho=0.0), dict(ce=0),
+               dict(iters=-1), dict(tol=-1.0), dict(z=None), dict(T=None), dict(T=ptr(T0)), dict(T=ptr(Tbig))):
+        assert noalloc(**kw) == FGA_EINVAL, kw
+        assert b"fga_mpc_solve_noalloc" in lib.fga_last_error(), kw
+
+    info = (ctypes.c_int64 * 8)()
+    d = ctypes.c_double()
+    opts, res = fga_iter_opts(), fga_iter_result()
+    assert lib.fga_residuals(None, ctypes.byref(d), ctypes.byref(d)) == FGA_EINVAL
+    assert lib.fga_read_edge_state(None, 0, None, 0) == FGA_EINVAL
+    assert lib.fga_launch_info(None, info, 8) == FGA_EINVAL
+    assert lib.fga_set_edge_rho_alpha(None, None, None) == FGA_EINVAL
+    assert lib.fga_set_stream(None, None) == FGA_EINVAL
+    assert lib.fga_horizon_solve(None, ctypes.byref(opts), ctypes.byref(res)) == FGA_EINVAL
+    assert lib.fga_horizon_read(None, None, None, None) == FGA_EINVAL
+    assert lib.fga_horizon_info(None, info, 8) == FGA_EINVAL
+    assert lib.fga_mpc_batch_info(None, info, 8) == FGA_EINVAL
+    assert lib.fga_mlp_num_params(None, info) == FGA_EINVAL
+    assert lib.fga_mpc_batch_destroy(None) == 0 and lib.fga_mlp_destroy(None) == 0
+
+    g = _new(lib)
+    assert lib.fga_add_variables(g, 2, 1, None) == 0
+    ids = np.array([[0], [1]], dtype=np.int64)
+    lohi = np.array([-1.0, 1.0])
+    assert lib.fga_add_factors(g, 8, 2, 1, P(ids.ctypes.data), P(lohi.ctypes.data), 2, 1, None) == 0
+    out2 = np.zeros(2)
+    assert lib.fga_read_edge_state(g, 0, P(out2.ctypes.data), 2) == FGA_ESTATE
+    assert lib.fga_launch_info(g, info, 8) == FGA_ESTATE
+    bad = np.array([1.0, 0.0])
+    assert lib.fga_set_edge_rho_alpha(g, P(bad.ctypes.data), None) == FGA_EINVAL
+    nan = np.array([1.0, np.nan])
+    assert lib.fga_set_edge_rho_alpha(g, None, P(nan.ctypes.data)) == FGA_EINVAL
+    good = np.array([1.0, 2.0])
+    assert lib.fga_set_edge_rho_alpha(g, P(good.ctypes.data), P(good.ctypes.data)) == 0
+    assert lib.fga_destroy(g) == 0
